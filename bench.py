@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the balanced k-means partitioner on GB300.
+
+One step = one gk_partition call on the device-resident workload: Hilbert bootstrap
+(bounding box, keys, radix sort, gather, initial centers), the balanced k-means loop
+(assignment passes with influence updates, center movement, erosion) and the scatter of
+block ids to input order.  Default workload: 3D Gaussian mixture, n = 1e7, k = 1024,
+eps = 0.03, FP64 points and FP64 assignment.
+
+Prints one JSON line (rank 0):
+  value      points processed per second by the balanced k-means iterations of the whole
+             job: sum over steps of n * (assignment passes) / sum of step times (bootstrap
+             and movement time included in the denominator)
+  e2e        the same through the C ABI with pinned host buffers (copies in the region)
+  roofline   the assignment kernel: algorithmic bytes per launch / mean launch time
+  cpu_baseline  the FP64 oracle's balance pass on a bounded sample, host cores
+
+--impl reference times the oracle (the slow FP64 CPU restatement) on the same metric.
+--gpus N > 1 runs N independent replicas (one per rank, weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "points/s per balanced k-means iter and partition time (s), FP32 vs FP64, 1 GB300"
+UNIT = "points/s"
+DEFAULT_WORKLOAD = "gmm3d_1e7_k1024_f64"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# --------------------------------------------------------------------------------------
+# CPU baseline: the oracle's balance pass (assign + block weights + influence update)
+# --------------------------------------------------------------------------------------
+def cpu_baseline(x, w, spec, seconds: float):
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    k = spec["k"]
+    m = int(min(len(x), max(4 * k, 2_000_000_000 // (k * 150))))
+    rng = np.random.default_rng(12345)
+    idx = np.sort(rng.choice(len(x), m, replace=False))
+    xs = np.ascontiguousarray(x[idx], dtype=np.float64)
+    ws = None if w is None else np.ascontiguousarray(w[idx], dtype=np.float64)
+    xs = xs[oracle.sort_keys(oracle.hilbert_keys(xs))]
+    C = oracle.sfc_centers(xs, k)
+    I = np.ones(k)
+    times = []
+    t_end = time.perf_counter() + seconds
+    while True:
+        t0 = time.perf_counter()
+        A, _, _ = oracle.assign(xs, C, I, threads=cores)
+        S, W = oracle.block_weights(A, ws, k)
+        bal, I, _ = oracle.balance_update(S, W, k, spec["d"], spec["eps"], I)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() > t_end and len(times) >= 2:
+            break
+    t = float(np.mean(times))
+    return {"value": m / t, "unit": UNIT, "cores": cores, "kind": "oracle", "ms_per_pass": 1e3 * t,
+            "sample": (f"{m} of the workload's points (uniform sample, curve-sorted), k={k}: "
+                       f"one FP64 balance pass (brute-force assignment over all k with "
+                       f"{cores} OpenMP threads, block weights, influence update), "
+                       f"mean of {len(times)} passes")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1805_01208_gb300 import synth
+    x, w, spec = synth.workload(args.workload, n=args.n)
+    cores = len(os.sched_getaffinity(0))
+    for _ in range(args.warmup):
+        cpu_baseline(x, w, spec, 0.0)
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps)))
+    vals = [cpu_baseline(x, w, spec, per_step) for _ in range(args.steps)]
+    value = float(np.mean([v["value"] for v in vals]))
+    ms = float(np.mean([v["ms_per_pass"] for v in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": _config(spec, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(spec, args):
+    return {"workload": args.workload, "n": spec["n"], "d": spec["d"], "k": spec["k"],
+            "eps": spec["eps"], "points": spec["dtype"], "assign": spec["assign"],
+            "weights": "uniform[1,10]" if spec["weighted"] else "unit",
+            "l2": "inputs larger than L2 and a 512 MB write between timed steps",
+            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single"}
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1805_01208_gb300 as gk
+    gk.build()
+    from paper_1805_01208_gb300 import synth
+
+    x, w, spec = synth.workload(args.workload, n=args.n)
+    if world > 1 and rank > 0:  # replicas: an independent instance per rank
+        x = synth.make_points(spec["shape"], spec["n"], spec["d"], spec["seed"] + 1000 * rank,
+                              spec["dtype"])
+    n, d, k, eps = len(x), spec["d"], spec["k"], spec["eps"]
+    xt = torch.from_numpy(x).to(dev)
+    wt = None if w is None else torch.from_numpy(w).to(dev)
+    opts = gk.default_options(assign_dtype=spec["assign"])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step(options):
+        return gk.partition(xt, k, eps, weights=wt, options=options)
+
+    for _ in range(args.warmup):
+        step(opts)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    times, results = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)  # evict L2 between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, _, res = step(opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        results.append(res)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    total_ms = float(sum(times))
+    points_passes = float(sum(n * r["balance_passes"] for r in results))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pp = torch.tensor([points_passes], device=dev, dtype=torch.float64)
+        dist.all_reduce(pp)
+        points_passes = float(pp.item())
+    value = points_passes / (total_ms * 1e-3)
+    ms_per_step = total_ms / args.steps
+    launches = int(sum(r["kernel_launches"] for r in results))
+
+    # ---- end to end through the C ABI with pinned host buffers -------------------------
+    e2e = _e2e(gk, x, w, spec, opts, stream, max(1, min(3, args.steps)))
+
+    # ---- roofline of the assignment kernel ---------------------------------------------
+    live_ms = sum(r["assign_live_ms"] for r in results)
+    live_n = sum(r["assign_live_launches"] for r in results)
+    timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1)
+    _, _, _, tres = step(timed)
+    ev_avg = tres["time_assign_ms"] / max(1, tres["assign_launches"])
+    es = 8 if spec["dtype"] == "f64" else 4
+    bytes_per_pt = 4 * d + 4 + (es if spec["weighted"] else 0)
+    bytes_per_launch = n * bytes_per_pt
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "assign_kernel",
+            "bytes_per_launch": bytes_per_launch, "launch_ms_events": ev_avg,
+            "launch_ms_live_graph": live_ms / max(1, live_n), "peak_source": peak_kind,
+            "other_kernels_ms_per_pass": {
+                "filter": tres["time_filter_ms"] / max(1, tres["filter_launches"]),
+                "balance": tres["time_balance_ms"] / max(1, tres["balance_launches"]),
+                "move_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])}}
+    _attach_traffic(roof, args.workload)
+
+    # ---- FP32 form on the same data ------------------------------------------------------
+    fp32 = None
+    if not args.no_fp32_compare and spec["assign"] == "f64":
+        o32 = gk.default_options(assign_dtype="f32")
+        step(o32)
+        t32, r32 = [], []
+        for _ in range(max(1, min(2, args.steps))):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, _, res = step(o32)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t32.append(e0.elapsed_time(e1))
+            r32.append(res)
+        v32 = sum(n * r["balance_passes"] for r in r32) / (sum(t32) * 1e-3)
+        fp64_pass = live_ms / max(1, live_n)
+        fp32_pass = sum(r["assign_live_ms"] for r in r32) / max(1, sum(r["assign_live_launches"] for r in r32))
+        fp32 = {"value": v32, "ms_per_step": float(np.mean(t32)),
+                "balance_passes": r32[-1]["balance_passes"], "balanced": r32[-1]["balanced"],
+                "assign_ms_per_pass": fp32_pass, "speedup_per_pass_vs_fp64": fp64_pass / fp32_pass,
+                "speedup_partition_vs_fp64": ms_per_step / float(np.mean(t32))}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(x, w, spec, args.cpu_seconds)
+
+    last = results[-1]
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": spec["assign"], "data": "synthetic", "config": _config(spec, args),
+                "partition_time_s": ms_per_step / 1e3,
+                "balance_passes_per_step": last["balance_passes"],
+                "iterations_per_step": last["iterations"], "balanced": last["balanced"],
+                "max_imbalance": last["max_imbalance"], "avg_candidates": last["avg_candidates"],
+                "rechecked_points_per_step": last["rechecked_points"],
+                "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
+                "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
+                "fp32_form": fp32, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _e2e(gk, x, w, spec, opts, stream, steps):
+    """Same metric through gk_partition with pinned host input and output buffers."""
+    import torch
+    n, d, k = len(x), spec["d"], spec["k"]
+    xh = torch.from_numpy(x).pin_memory()
+    wh = None if w is None else torch.from_numpy(w).pin_memory()
+    bh = torch.empty(n, dtype=torch.int32).pin_memory()
+    ch = torch.empty((k, d), dtype=torch.float64).pin_memory()
+    ih = torch.empty(k, dtype=torch.float64).pin_memory()
+    code = gk.GK_F64 if spec["dtype"] == "f64" else gk.GK_F32
+    L = gk.lib()
+    sptr = ctypes.c_void_p(stream.cuda_stream)
+
+    def call():
+        res = gk.Result()
+        st = L.gk_partition(ctypes.c_void_p(xh.data_ptr()), code,
+                            None if wh is None else ctypes.c_void_p(wh.data_ptr()), n, d, k,
+                            spec["eps"], ctypes.byref(opts), ctypes.c_void_p(bh.data_ptr()),
+                            ctypes.c_void_p(ch.data_ptr()), ctypes.c_void_p(ih.data_ptr()),
+                            ctypes.byref(res), sptr)
+        assert st in (gk.GK_OK, gk.GK_ERR_NOT_BALANCED), gk.status_string(st)
+        return res
+
+    call()
+    torch.cuda.synchronize()
+    tot, pp = 0.0, 0.0
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+        pp += n * res.balance_passes
+    es = 8 if spec["dtype"] == "f64" else 4
+    h2d = n * d * es + (n * es if w is not None else 0)
+    d2h = n * 4 + k * d * 8 + k * 8
+    return {"value": pp / (tot * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": tot / steps}
+
+
+def _attach_traffic(roof, workload):
+    """DRAM traffic per launch from the committed ncu summary of this kernel, if any."""
+    path = os.path.join(ROOT, "profiles", f"assign_kernel_{workload}.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.strip().startswith("dram_bytes_per_launch:"):
+                    val = line.split(":", 1)[1].strip().split()[0]
+                    roof["traffic"] = None if val == "null" else float(val)
+                    roof["traffic_source"] = os.path.relpath(path, ROOT)
+    except OSError:
+        pass
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * gk.h -- C ABI of the GB300 (sm_103a) balanced k-means geometric partitioner.
+ *
+ * The library implements the data-parallel path of "Balanced k-means for
+ * Parallel Geometric Partitioning": the Hilbert space-filling-curve bootstrap
+ * (Section 4.1; Algorithm 2, the sfcIndex / sortGlobal / initial-center steps)
+ * and the balanced k-means iteration (Section 4.2, Eq. 1-3; Algorithm 1
+ * AssignAndBalance; Algorithm 2 BalancedKMeans), as hand-written CUDA kernels
+ * for one GPU.
+ *
+ * Conventions for every entry point:
+ *   - coords: n x d row-major (point p's coordinates at coords[p*d .. p*d+d-1]),
+ *     element type given by dtype (GK_F32 or GK_F64), d in {2, 3}.
+ *   - weights: n values of the same dtype as coords, or NULL for unit weights;
+ *     every weight must be finite and > 0 (Section 4: w maps points to R+).
+ *   - Every pointer may address host memory or device memory of the current
+ *     device; the library looks at each one and stages host buffers through
+ *     its workspace (host<->device copies then happen inside the call).
+ *   - The caller owns every pointer it passes.  The library keeps a device
+ *     workspace that grows on demand and is reused across calls; gk_release()
+ *     frees it.
+ *   - stream: a cudaStream_t (passed as void*; NULL = legacy default stream).
+ *     Work is enqueued on it, and every entry point synchronises it before
+ *     returning, so outputs and the returned status are final on return.
+ *   - Errors: invalid arguments are reported as GK_ERR_INVALID_ARG before any
+ *     kernel launch; a failing CUDA call as GK_ERR_CUDA; an allocation failure
+ *     as GK_ERR_OOM.  Outputs are unspecified after an error, except
+ *     GK_ERR_NOT_BALANCED, which still returns a valid assignment.
+ *   - Not thread-safe: calls must not overlap (one workspace per process).
+ */
+#ifndef GK_H
+#define GK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GK_ABI_VERSION 1
+
+typedef enum gk_status {
+    GK_OK = 0,
+    GK_ERR_INVALID_ARG = 1,
+    GK_ERR_CUDA = 2,
+    GK_ERR_OOM = 3,
+    GK_ERR_NOT_BALANCED = 4, /* assignment returned, but a block exceeds (1+eps)*ceil(W/k) */
+    GK_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+} gk_status;
+
+typedef enum gk_dtype { GK_F32 = 0, GK_F64 = 1 } gk_dtype;
+
+/* Tuning parameters of Algorithms 1 and 2 (the paper leaves their values open). */
+typedef struct gk_options {
+    int32_t max_iter;           /* movement phases of Algorithm 2 (default 50)             */
+    int32_t max_balance_iter;   /* assignment passes per phase, Algorithm 1 (default 50)   */
+    int32_t final_balance_iter; /* extra passes with centers fixed if still unbalanced
+                                   after the last phase (default 500)                     */
+    int32_t erosion;            /* 1: influence erosion of Eq. 2-3 after each move (default) */
+    double delta_threshold;     /* stop when every center moved less than this (input
+                                   units); < 0 selects 1e-4 * largest bounding-box extent */
+    int32_t assign_dtype;       /* GK_F64 (default): the assignment is the FP64 argmin of
+                                   the effective distance (FP32 search certified by an
+                                   error bound, FP64 re-decision of the rest).  GK_F32:
+                                   plain FP32 argmin on box-normalised coordinates.       */
+    int32_t use_graph;          /* 1 (default): the iteration loop runs as one CUDA graph
+                                   with conditional while-nodes; 0: host-driven loop       */
+    int32_t timing;             /* 1: with use_graph = 0, time every kernel of the loop with
+                                   CUDA events (fills the time_*_ms fields of gk_result)  */
+    int32_t reserved[5];        /* must be zero                                           */
+} gk_options;
+
+/* Outcome and counters of one call. */
+typedef struct gk_result {
+    int32_t status;             /* same value as returned                                  */
+    int32_t iterations;         /* movement phases executed                                */
+    int32_t balance_passes;     /* assignment passes executed (all phases)                 */
+    int32_t converged;          /* 1 if max center movement < threshold ended the loop     */
+    int32_t balanced;           /* 1 if the returned assignment meets the balance bound    */
+    int32_t reserved0;
+    double max_imbalance;       /* max_c S_c / ceil(W/k) - 1 of the returned assignment    */
+    double max_delta;           /* largest center movement of the last movement phase      */
+    double delta_threshold;     /* absolute threshold used                                 */
+    double avg_candidates;      /* mean candidate centers evaluated per point and pass     */
+    int64_t rechecked_points;   /* point-passes re-decided in FP64 (GK_F64 assignment)     */
+    int64_t kernel_launches;    /* kernels executed by this call (graph nodes included)    */
+    double time_bootstrap_ms;   /* device time: bounding box, keys, sort, gather, centers  */
+    double time_kmeans_ms;      /* device time: the iteration loop                          */
+    double time_total_ms;       /* device time of the whole call                           */
+    double time_filter_ms;      /* CUDA-event sums per kernel kind (gk_options.timing = 1) */
+    double time_assign_ms;
+    double time_balance_ms;
+    double time_move_ms;        /* centroid accumulation + finalize                        */
+    int64_t filter_launches;
+    int64_t assign_launches;
+    int64_t balance_launches;
+    int64_t move_launches;
+    double assign_live_ms;      /* device-clock (globaltimer) sum of the assignment kernel
+                                   launches, any mode (graph included)                    */
+    int64_t assign_live_launches;
+} gk_result;
+
+/* Fills *opt with the defaults listed above. */
+void gk_default_options(gk_options *opt);
+
+/* Human-readable name of a gk_status value (static string). */
+const char *gk_status_string(int32_t status);
+
+/* GK_ABI_VERSION of the loaded library. */
+int32_t gk_abi_version(void);
+
+/*
+ * Hilbert index of every point (Algorithm 2 "sfcIndex"; Section 4.1).
+ * Each coordinate is mapped to a 2^b cell grid (b = 32 for d = 2, 21 for
+ * d = 3) over the points' bounding box made isotropic with side 2^E, the
+ * smallest power of two not below the largest extent; cell =
+ * floor((x - lo) * 2^(b-E)) clamped to 2^b - 1, the subtraction done once in
+ * the input precision.  The key is the index of that cell on the Hilbert curve
+ * of J. Skilling ("Programming the Hilbert curve", 2004), most significant
+ * level first, axis 0 first inside a level.
+ *   keys_out: n uint64 (host or device), written in input order.
+ */
+gk_status gk_hilbert_keys(const void *coords, int32_t dtype, int64_t n, int32_t d,
+                          uint64_t *keys_out, void *stream);
+
+/*
+ * Space-filling-curve bootstrap (Algorithm 2, sfcIndex / sortGlobal / initial
+ * centers): keys as gk_hilbert_keys, a stable sort by key (equal keys keep input
+ * order), and the initial centers C[i] = sorted point i*n/k + n/(2k).
+ *   perm_out:    n int64, perm_out[i] = input index of the i-th point on the curve
+ *                (nullable).
+ *   centers_out: k x d FP64 in input units (nullable).
+ * Requires 1 <= k <= n.
+ */
+gk_status gk_sfc_init(const void *coords, int32_t dtype, int64_t n, int32_t d, int32_t k,
+                      int64_t *perm_out, double *centers_out, void *stream);
+
+/*
+ * One assignment pass (Section 4.2; the inner loop of Algorithm 1): every point
+ * goes to the center c minimising dist(p, C_c) / influence_c (ties: lowest c),
+ * and the block weights S_c = sum of w_p over the points of block c are formed.
+ *   centers:   k x d FP64 (input units);  influence: k FP64 > 0.
+ *   assign_dtype: GK_F64 (FP64 argmin) or GK_F32 (see gk_options).
+ *   block_out: n int32 in input order.  block_weights_out: k FP64 (nullable).
+ * Points are processed in the order given; it is fastest on curve-sorted points.
+ */
+gk_status gk_assign(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
+                    int32_t k, const double *centers, const double *influence,
+                    int32_t assign_dtype, int32_t *block_out, double *block_weights_out,
+                    void *stream);
+
+/*
+ * Center movement (Algorithm 2, the weighted means after AssignAndBalance):
+ * centers_out[c] = sum w_p x_p / sum w_p over the points with block[p] = c
+ * (an empty block keeps centers[c]); delta_out[c] = distance moved (nullable);
+ * *beta_out = mean over non-empty blocks of the diagonal of the block's
+ * bounding box, the block diameter used by the erosion of Eq. 2 (nullable).
+ *   block: n int32 in [0, k).  centers: k x d FP64.  centers_out: k x d FP64.
+ */
+gk_status gk_move_centers(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                          int32_t d, int32_t k, const int32_t *block, const double *centers,
+                          double *centers_out, double *delta_out, double *beta_out,
+                          void *stream);
+
+/*
+ * Balanced k-means from given centers and influence (Algorithm 2 from its main
+ * loop on, with Algorithm 1): repeated assignment passes with the influence
+ * update of Eq. 1 (influence *= clamp((W/k / S_c)^(1/d), 0.95, 1.05) while some
+ * block exceeds (1+eps)*ceil(W/k)), weighted-mean center movement, the erosion of
+ * Eq. 2-3, until the centers move less than the threshold or max_iter phases ran;
+ * then, if the assignment is still unbalanced, up to final_balance_iter passes
+ * with the centers fixed.
+ *   centers_inout:   k x d FP64; in: initial centers; out: the centers the
+ *                    returned assignment was computed with.
+ *   influence_inout: k FP64; in: initial influence (e.g. all 1); out: the
+ *                    influence the returned assignment was computed with.
+ *   block_out:       n int32 in input order.
+ *   opt: NULL = defaults.  result: nullable.
+ * Points are processed in the given order (curve-sorted points are fastest).
+ */
+gk_status gk_balanced_kmeans(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                             int32_t d, int32_t k, double eps, double *centers_inout,
+                             double *influence_inout, int32_t *block_out, const gk_options *opt,
+                             gk_result *result, void *stream);
+
+/*
+ * The whole partitioner (Algorithm 2): Hilbert bootstrap, balanced k-means on
+ * the curve-sorted points from the curve centers with influence 1, and one
+ * block id per input point.
+ *   block_out:     n int32 in input order.
+ *   centers_out:   k x d FP64 (nullable): centers of the returned assignment.
+ *   influence_out: k FP64 (nullable): influence of the returned assignment.
+ */
+gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                       int32_t d, int32_t k, double eps, const gk_options *opt,
+                       int32_t *block_out, double *centers_out, double *influence_out,
+                       gk_result *result, void *stream);
+
+/* Frees the device workspace and cached graphs of the current device. */
+void gk_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GK_H */

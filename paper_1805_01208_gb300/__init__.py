@@ -1,0 +1,291 @@
+"""GB300 (sm_103a) balanced k-means geometric partitioner.
+
+Thin Python binding of the C ABI in ``include/gk.h`` (``libgk.so``).  Every step of
+the computation runs in the library's CUDA kernels; this module only marshals
+arguments: it passes data pointers of torch tensors (device or host) or numpy arrays
+(host) and the current CUDA stream, and allocates outputs.  There is no CPU fallback:
+without the built library every call raises.
+
+Functions (same names as the C entry points, without the ``gk_`` prefix):
+``hilbert_keys``, ``sfc_init``, ``assign``, ``move_centers``, ``balanced_kmeans``,
+``partition``, ``release``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgk.so")
+
+GK_OK = 0
+GK_ERR_INVALID_ARG = 1
+GK_ERR_CUDA = 2
+GK_ERR_OOM = 3
+GK_ERR_NOT_BALANCED = 4
+GK_ERR_TIMEOUT = 5
+GK_F32 = 0
+GK_F64 = 1
+
+
+class GKError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("max_iter", ctypes.c_int32),
+        ("max_balance_iter", ctypes.c_int32),
+        ("final_balance_iter", ctypes.c_int32),
+        ("erosion", ctypes.c_int32),
+        ("delta_threshold", ctypes.c_double),
+        ("assign_dtype", ctypes.c_int32),
+        ("use_graph", ctypes.c_int32),
+        ("timing", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32),
+        ("iterations", ctypes.c_int32),
+        ("balance_passes", ctypes.c_int32),
+        ("converged", ctypes.c_int32),
+        ("balanced", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("max_imbalance", ctypes.c_double),
+        ("max_delta", ctypes.c_double),
+        ("delta_threshold", ctypes.c_double),
+        ("avg_candidates", ctypes.c_double),
+        ("rechecked_points", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+        ("time_bootstrap_ms", ctypes.c_double),
+        ("time_kmeans_ms", ctypes.c_double),
+        ("time_total_ms", ctypes.c_double),
+        ("time_filter_ms", ctypes.c_double),
+        ("time_assign_ms", ctypes.c_double),
+        ("time_balance_ms", ctypes.c_double),
+        ("time_move_ms", ctypes.c_double),
+        ("filter_launches", ctypes.c_int64),
+        ("assign_launches", ctypes.c_int64),
+        ("balance_launches", ctypes.c_int64),
+        ("move_launches", ctypes.c_int64),
+        ("assign_live_ms", ctypes.c_double),
+        ("assign_live_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved0"}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1805_01208_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.gk_default_options.argtypes = [P]
+        L.gk_status_string.argtypes = [i32]
+        L.gk_status_string.restype = ctypes.c_char_p
+        L.gk_abi_version.restype = i32
+        L.gk_hilbert_keys.argtypes = [P, i32, i64, i32, P, P]
+        L.gk_sfc_init.argtypes = [P, i32, i64, i32, i32, P, P, P]
+        L.gk_assign.argtypes = [P, i32, P, i64, i32, i32, P, P, i32, P, P, P]
+        L.gk_move_centers.argtypes = [P, i32, P, i64, i32, i32, P, P, P, P, P, P]
+        L.gk_balanced_kmeans.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P, P]
+        L.gk_partition.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P, P]
+        for name in ("gk_hilbert_keys", "gk_sfc_init", "gk_assign", "gk_move_centers",
+                     "gk_balanced_kmeans", "gk_partition"):
+            getattr(L, name).restype = i32
+        L.gk_release.argtypes = []
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().gk_status_string(status).decode()
+
+
+def default_options(**overrides) -> Options:
+    o = Options()
+    lib().gk_default_options(ctypes.byref(o))
+    for key, val in overrides.items():
+        if key == "assign_dtype" and isinstance(val, str):
+            val = GK_F64 if val == "f64" else GK_F32
+        setattr(o, key, val)
+    return o
+
+
+# ------------------------------------------------------------------------------------
+# argument marshalling
+# ------------------------------------------------------------------------------------
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _dtype_code(a) -> int:
+    if _is_torch(a):
+        import torch
+        if a.dtype == torch.float64:
+            return GK_F64
+        if a.dtype == torch.float32:
+            return GK_F32
+    else:
+        if a.dtype == np.float64:
+            return GK_F64
+        if a.dtype == np.float32:
+            return GK_F32
+    raise TypeError(f"coordinates must be float32 or float64, got {a.dtype}")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(a, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if _is_torch(a) and a.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _empty(like, shape, kind):
+    """Output buffer on the same side as `like` (torch device/host tensor or numpy)."""
+    if _is_torch(like):
+        import torch
+        dt = {"i32": torch.int32, "i64": torch.int64, "f64": torch.float64, "u64": torch.int64}[kind]
+        return torch.empty(shape, dtype=dt, device=like.device)
+    dt = {"i32": np.int32, "i64": np.int64, "f64": np.float64, "u64": np.uint64}[kind]
+    return np.empty(shape, dtype=dt)
+
+
+def _check(status, where, allow=()):
+    if status != GK_OK and status not in allow:
+        raise GKError(status, where)
+    return status
+
+
+def _shape(coords):
+    if len(coords.shape) != 2:
+        raise ValueError("coords must be (n, d)")
+    return int(coords.shape[0]), int(coords.shape[1])
+
+
+def _same_dtype(coords, weights):
+    if weights is not None and _dtype_code(weights) != _dtype_code(coords):
+        raise TypeError("weights must have the dtype of the coordinates")
+
+
+# ------------------------------------------------------------------------------------
+# entry points
+# ------------------------------------------------------------------------------------
+def hilbert_keys(coords, stream=None):
+    """uint64 Hilbert keys (returned as int64 tensors for torch inputs) in input order."""
+    n, d = _shape(coords)
+    keys = _empty(coords, (n,), "u64")
+    st = lib().gk_hilbert_keys(_ptr(coords), _dtype_code(coords), n, d, _ptr(keys),
+                               _stream(coords, stream))
+    _check(st, "gk_hilbert_keys")
+    return keys
+
+
+def sfc_init(coords, k: int, stream=None):
+    """(perm, centers): curve order (sorted position -> input index) and initial centers."""
+    n, d = _shape(coords)
+    perm = _empty(coords, (n,), "i64")
+    centers = _empty(coords, (k, d), "f64")
+    st = lib().gk_sfc_init(_ptr(coords), _dtype_code(coords), n, d, k, _ptr(perm), _ptr(centers),
+                           _stream(coords, stream))
+    _check(st, "gk_sfc_init")
+    return perm, centers
+
+
+def assign(coords, centers, influence, weights=None, assign_dtype: str = "f64", stream=None):
+    """One assignment pass: (block ids, block weights)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    k = int(centers.shape[0])
+    block = _empty(coords, (n,), "i32")
+    bw = _empty(coords, (k,), "f64")
+    st = lib().gk_assign(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k, _ptr(centers),
+                         _ptr(influence), GK_F64 if assign_dtype == "f64" else GK_F32,
+                         _ptr(block), _ptr(bw), _stream(coords, stream))
+    _check(st, "gk_assign")
+    return block, bw
+
+
+def move_centers(coords, block, centers, weights=None, stream=None):
+    """Weighted means of the blocks: (new centers, movement per center, beta)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    k = int(centers.shape[0])
+    out = _empty(coords, (k, d), "f64")
+    delta = _empty(coords, (k,), "f64")
+    beta = ctypes.c_double()
+    st = lib().gk_move_centers(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k,
+                               _ptr(block), _ptr(centers), _ptr(out), _ptr(delta),
+                               ctypes.byref(beta), _stream(coords, stream))
+    _check(st, "gk_move_centers")
+    return out, delta, beta.value
+
+
+def balanced_kmeans(coords, k: int, eps: float, centers, influence, weights=None,
+                    options: Options | None = None, stream=None):
+    """Balanced k-means from given centers/influence (updated in place to the state the
+    returned assignment was computed with).  Returns (block, result dict)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    block = _empty(coords, (n,), "i32")
+    res = Result()
+    opt = options if options is not None else default_options()
+    st = lib().gk_balanced_kmeans(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k, eps,
+                                  _ptr(centers), _ptr(influence), _ptr(block), ctypes.byref(opt),
+                                  ctypes.byref(res), _stream(coords, stream))
+    _check(st, "gk_balanced_kmeans", allow=(GK_ERR_NOT_BALANCED,))
+    return block, res.as_dict()
+
+
+def partition(coords, k: int, eps: float, weights=None, options: Options | None = None,
+              stream=None, want_state: bool = True):
+    """The whole partitioner.  Returns (block, centers, influence, result dict)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    block = _empty(coords, (n,), "i32")
+    centers = _empty(coords, (k, d), "f64") if want_state else None
+    infl = _empty(coords, (k,), "f64") if want_state else None
+    res = Result()
+    opt = options if options is not None else default_options()
+    st = lib().gk_partition(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k, eps,
+                            ctypes.byref(opt), _ptr(block), _ptr(centers), _ptr(infl),
+                            ctypes.byref(res), _stream(coords, stream))
+    _check(st, "gk_partition", allow=(GK_ERR_NOT_BALANCED,))
+    return block, centers, infl, res.as_dict()
+
+
+def release():
+    lib().gk_release()
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)

@@ -1,0 +1,669 @@
+// gk_api.cu -- the C ABI declared in include/gk.h: argument checks, host/device
+// pointer staging, the device workspace, and the order of kernel launches for the
+// space-filling-curve bootstrap and the balanced k-means loop (Algorithms 1 and 2).
+#include <math.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gk.h"
+#include "gk_common.cuh"
+#include "gk_internal.h"
+
+namespace gk {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// One device workspace per process (grown on demand, reused across calls) plus a
+// pinned host mirror of the control block and a cached loop graph.
+struct Workspace {
+    int device = -1;
+    char *dev = nullptr;
+    size_t dev_bytes = 0;
+    Ctl *host_ctl = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Prob graph_key;
+    bool has_graph = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+Workspace g_ws;
+
+void drop_graph() {
+    if (g_ws.exec) cudaGraphExecDestroy(g_ws.exec);
+    g_ws.exec = nullptr;
+    g_ws.has_graph = false;
+}
+
+void release_all() {
+    drop_graph();
+    if (g_ws.dev) cudaFree(g_ws.dev);
+    if (g_ws.host_ctl) cudaFreeHost(g_ws.host_ctl);
+    for (auto &e : g_ws.ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : g_ws.kev)
+        if (e) cudaEventDestroy(e);
+    g_ws = Workspace();
+}
+
+// Pointer kinds.
+enum PtrKind { kHost = 0, kDevice = 1, kForeign = 2 };
+PtrKind ptr_kind(const void *p, int device) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return kHost;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == device ? kDevice : kForeign;
+    return kHost;
+}
+
+struct Bufs {
+    // staging of host inputs / outputs
+    void *coords_stage = nullptr, *weights_stage = nullptr;
+    int *block_stage = nullptr;
+    long long *perm_stage = nullptr;
+    unsigned *hist = nullptr;
+};
+
+// Sizes of everything a problem needs; with base != nullptr also assigns pointers.
+size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool stage_weights,
+              bool stage_block, bool perm_out) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *ptr = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return ptr;
+    };
+    size_t es = p.dtype == 1 ? 8 : 4;
+    long long n = p.n, np = p.n_pad, k = p.k, d = p.d;
+    p.ctl = (Ctl *)take(sizeof(Ctl));
+    b.coords_stage = stage_coords ? take((size_t)n * d * es) : nullptr;
+    b.weights_stage = stage_weights ? take((size_t)n * es) : nullptr;
+    if (sort) {
+        p.keys[0] = (unsigned long long *)take((size_t)n * 8);
+        p.keys[1] = (unsigned long long *)take((size_t)n * 8);
+        p.perm[0] = (unsigned *)take((size_t)n * 4);
+        p.perm[1] = (unsigned *)take((size_t)n * 4);
+        b.hist = (unsigned *)take(radix_hist_entries(n) * 4);
+    } else {
+        p.keys[0] = p.keys[1] = nullptr;
+        p.perm[0] = p.perm[1] = nullptr;
+        b.hist = nullptr;
+    }
+    p.X32 = (float *)take((size_t)d * np * 4);
+    p.X64 = p.dtype == 1 ? (double *)take((size_t)d * np * 8) : nullptr;
+    p.Ws = p.weighted ? (void *)take((size_t)np * es) : nullptr;
+    p.A = (int *)take((size_t)np * 4);
+    p.tiles = (float4 *)take((size_t)p.ntiles * 32);
+    p.cand_cnt = (int *)take((size_t)p.ntiles * 4);
+    p.cand_list = (int *)take((size_t)p.ntiles * kCap * 4);
+    p.C = (double *)take((size_t)k * d * 8);
+    p.I = (double *)take((size_t)k * 8);
+    p.Iused = (double *)take((size_t)k * 8);
+    p.g64 = (double *)take((size_t)k * 8);
+    p.Cm = (double *)take((size_t)k * d * 8);
+    p.delta = (double *)take((size_t)k * 8);
+    p.S64 = (double *)take((size_t)k * 8);
+    p.Sfix = (unsigned long long *)take((size_t)k * 16);
+    p.SXfix = (unsigned long long *)take((size_t)k * d * 16);
+    p.BBlo = (unsigned long long *)take((size_t)k * d * 8);
+    p.BBhi = (unsigned long long *)take((size_t)k * d * 8);
+    p.cdata = (float4 *)take((size_t)k * 32);
+    b.block_stage = stage_block ? (int *)take((size_t)n * 4) : nullptr;
+    b.perm_stage = perm_out ? (long long *)take((size_t)n * 8) : nullptr;
+    return off;
+}
+
+gk_status ensure_workspace(size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GK_ERR_CUDA;
+    if (g_ws.device != dev && g_ws.device != -1) release_all();
+    g_ws.device = dev;
+    if (!g_ws.host_ctl) {
+        if (cudaMallocHost((void **)&g_ws.host_ctl, sizeof(Ctl)) != cudaSuccess) {
+            cudaGetLastError();
+            return GK_ERR_OOM;
+        }
+        for (auto &e : g_ws.ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return GK_ERR_CUDA;
+        for (auto &e : g_ws.kev)
+            if (cudaEventCreate(&e) != cudaSuccess) return GK_ERR_CUDA;
+    }
+    if (g_ws.dev_bytes >= bytes) return GK_OK;
+    drop_graph();
+    if (g_ws.dev) cudaFree(g_ws.dev);
+    g_ws.dev = nullptr;
+    g_ws.dev_bytes = 0;
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc((void **)&g_ws.dev, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc((void **)&g_ws.dev, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return GK_ERR_OOM;
+        }
+        want = bytes;
+    }
+    g_ws.dev_bytes = want;
+    return GK_OK;
+}
+
+#define GK_CUDA(x)                        \
+    do {                                  \
+        if ((x) != cudaSuccess) {         \
+            cudaGetLastError();           \
+            return GK_ERR_CUDA;           \
+        }                                 \
+    } while (0)
+
+int exponent_above(double v) {  // smallest e with |v| < 2^e (v finite)
+    if (v == 0.0) return 0;
+    int e;
+    frexp(fabs(v), &e);
+    return e;
+}
+
+int grid_exponent(double s) {  // smallest E with 2^E >= s
+    if (!(s > 0.0)) return 0;
+    int e;
+    double f = frexp(s, &e);
+    return f == 0.5 ? e - 1 : e;
+}
+
+void options_or_default(const gk_options *opt, gk_options *o) {
+    if (opt)
+        *o = *opt;
+    else
+        gk_default_options(o);
+}
+
+gk_status check_common(const void *coords, int32_t dtype, int64_t n, int32_t d) {
+    if (!coords || (dtype != GK_F32 && dtype != GK_F64) || (d != 2 && d != 3) || n < 1 ||
+        n >= (1ll << 32) - 1024)
+        return GK_ERR_INVALID_ARG;
+    return GK_OK;
+}
+
+// State shared by the entry points of one call.
+struct Call {
+    cudaStream_t s;
+    Prob p;
+    Bufs b;
+    bool coords_host, weights_host;
+    gk_status init(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
+                   int32_t k, bool sort, bool block_host, bool perm_out) {
+        memset(&p, 0, sizeof(p));
+        p.n = n;
+        p.n_pad = (n + kTile - 1) / kTile * kTile;
+        p.d = d;
+        p.k = k;
+        p.dtype = dtype;
+        p.weighted = weights != nullptr;
+        p.ntiles = (int)(p.n_pad / kTile);
+        p.bits = d == 2 ? 32 : 21;
+        int dev = 0;
+        GK_CUDA(cudaGetDevice(&dev));
+        PtrKind kc = ptr_kind(coords, dev);
+        PtrKind kw = weights ? ptr_kind(weights, dev) : kHost;
+        if (kc == kForeign || kw == kForeign) return GK_ERR_INVALID_ARG;
+        size_t es = dtype == GK_F64 ? 8 : 4;
+        if (kc == kDevice && ((uintptr_t)coords % es)) return GK_ERR_INVALID_ARG;
+        if (weights && kw == kDevice && ((uintptr_t)weights % es)) return GK_ERR_INVALID_ARG;
+        coords_host = kc == kHost;
+        weights_host = weights && kw == kHost;
+        size_t need = layout(p, b, nullptr, sort, coords_host, weights_host, block_host, perm_out);
+        gk_status st = ensure_workspace(need);
+        if (st != GK_OK) return st;
+        layout(p, b, g_ws.dev, sort, coords_host, weights_host, block_host, perm_out);
+        p.coords = coords_host ? b.coords_stage : coords;
+        p.weights = weights ? (weights_host ? b.weights_stage : weights) : nullptr;
+        GK_CUDA(cudaEventRecord(g_ws.ev[0], s));
+        if (coords_host)
+            GK_CUDA(cudaMemcpyAsync(b.coords_stage, coords, (size_t)n * d * es,
+                                    cudaMemcpyHostToDevice, s));
+        if (weights_host)
+            GK_CUDA(cudaMemcpyAsync(b.weights_stage, weights, (size_t)n * es,
+                                    cudaMemcpyHostToDevice, s));
+        // control block and accumulators
+        Ctl c0;
+        memset(&c0, 0, sizeof(c0));
+        for (int j = 0; j < 3; ++j) {
+            c0.bb_lo[j] = ~0ull;
+            c0.bb_hi[j] = 0ull;
+        }
+        c0.w_lo = ~0ull;
+        c0.w_hi = 0ull;
+        *g_ws.host_ctl = c0;
+        GK_CUDA(cudaMemcpyAsync(p.ctl, g_ws.host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaMemsetAsync(p.Sfix, 0, (size_t)k * 16, s));
+        GK_CUDA(cudaMemsetAsync(p.SXfix, 0, (size_t)k * d * 16, s));
+        GK_CUDA(cudaMemsetAsync(p.BBlo, 0xff, (size_t)k * d * 8, s));
+        GK_CUDA(cudaMemsetAsync(p.BBhi, 0, (size_t)k * d * 8, s));
+        return GK_OK;
+    }
+    gk_status read_ctl() {
+        GK_CUDA(cudaMemcpyAsync(g_ws.host_ctl, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        return GK_OK;
+    }
+    // Bounding box -> frame, grid and fixed-point parameters (one readback).
+    gk_status geometry(double delta_threshold) {
+        GK_CUDA(launch_bbox(p, s));
+        gk_status st = read_ctl();
+        if (st != GK_OK) return st;
+        Ctl &c = *g_ws.host_ctl;
+        if (c.nonfinite || c.nonpositive_w) return GK_ERR_INVALID_ARG;
+        double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, ext = 0.0, xmax = 0.0;
+        for (int j = 0; j < p.d; ++j) {
+            lo[j] = okey_to_f64(c.bb_lo[j]);
+            hi[j] = okey_to_f64(c.bb_hi[j]);
+            ext = fmax(ext, hi[j] - lo[j]);
+            xmax = fmax(xmax, fmax(fabs(lo[j]), fabs(hi[j])));
+        }
+        int E = grid_exponent(ext);
+        p.grid_m = p.bits - E;
+        for (int j = 0; j < 3; ++j) p.origin[j] = lo[j];
+        if (p.dtype == GK_F64) {
+            p.scale = ldexp(1.0, -E);
+            p.R = 1.0f;
+        } else {  // FP32 inputs: the assignment frame is the raw coordinates
+            p.scale = 1.0;
+            for (int j = 0; j < 3; ++j) p.origin[j] = 0.0;
+            p.R = (float)xmax * (1.0f + 1e-6f);
+        }
+        // keep the quantisation origin (lo) separately: keys use lo in both cases
+        for (int j = 0; j < 3; ++j) key_origin[j] = lo[j];
+        double wmax = p.weighted ? okey_to_f64(c.w_hi) : 1.0;
+        p.Fw = p.weighted ? kFixBits - exponent_above(wmax) : 0;
+        p.Fx = kFixBits - exponent_above(p.weighted ? wmax * xmax * (1.0 + 1e-12) : xmax);
+        extent = ext;
+        thr = delta_threshold >= 0.0 ? delta_threshold : 1e-4 * ext;
+        return GK_OK;
+    }
+    double key_origin[3] = {0, 0, 0};
+    double extent = 0.0, thr = 0.0;
+    double t_filter = 0, t_assign = 0, t_balance = 0, t_move = 0;
+    long long n_pass = 0, n_move = 0;
+
+    Prob key_prob() const {  // frame for the Hilbert quantisation: origin = lo
+        Prob q = p;
+        for (int j = 0; j < 3; ++j) q.origin[j] = key_origin[j];
+        return q;
+    }
+};
+
+void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double t_loop,
+                 double t_tot, long long n, const Call &cl) {
+    if (!r) return;
+    memset(r, 0, sizeof(*r));
+    r->status = st;
+    r->iterations = c.iter;
+    r->balance_passes = c.passes;
+    r->converged = c.converged;
+    r->balanced = c.balanced;
+    r->max_imbalance = c.max_imbalance;
+    r->max_delta = c.max_delta;
+    r->delta_threshold = c.thr;
+    r->avg_candidates = c.passes > 0 ? (double)c.cand_sum / ((double)c.passes * (double)n) : 0.0;
+    r->rechecked_points = (int64_t)c.rechecks;
+    r->kernel_launches = (int64_t)c.launches;
+    r->time_bootstrap_ms = t_boot;
+    r->time_kmeans_ms = t_loop;
+    r->time_total_ms = t_tot;
+    r->time_filter_ms = cl.t_filter;
+    r->time_assign_ms = cl.t_assign;
+    r->time_balance_ms = cl.t_balance;
+    r->time_move_ms = cl.t_move;
+    r->filter_launches = cl.n_pass;
+    r->assign_launches = cl.n_pass;
+    r->balance_launches = cl.n_pass;
+    r->move_launches = cl.n_move;
+    r->assign_live_ms = (double)c.assign_ns * 1e-6;
+    r->assign_live_launches = (int64_t)c.assign_cnt;
+}
+
+gk_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (!dst) return GK_OK;
+    GK_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return GK_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
+// Runs the k-means loop on the prepared problem (C, I in the workspace).
+gk_status run_loop(Call &cl, const gk_options &o) {
+    Prob &p = cl.p;
+    cudaStream_t s = cl.s;
+    if (o.use_graph) {
+        Prob key = p;
+        key.coords = nullptr;
+        key.weights = nullptr;
+        if (!(g_ws.has_graph && memcmp(&key, &g_ws.graph_key, sizeof(Prob)) == 0)) {
+            drop_graph();
+            cudaGraphExec_t ex = nullptr;
+            int npp = 0;
+            if (build_loop_graph(key, &ex, &npp) != cudaSuccess) {
+                cudaGetLastError();
+                return GK_ERR_CUDA;
+            }
+            g_ws.exec = ex;
+            g_ws.graph_key = key;
+            g_ws.has_graph = true;
+        }
+        GK_CUDA(cudaGraphLaunch(g_ws.exec, s));
+        return GK_OK;
+    }
+    // host-driven loop: one readback of the loop condition per pass; with
+    // o.timing, CUDA events around every kernel (read after that readback)
+    cudaEvent_t *ev = g_ws.kev;
+    auto pass = [&](int mode) -> gk_status {
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[0], s));
+        GK_CUDA(launch_filter(p, s));
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[1], s));
+        GK_CUDA(launch_assign(p, s));
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[2], s));
+        GK_CUDA(launch_balance(p, mode, s));
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[3], s));
+        gk_status st = cl.read_ctl();
+        if (st == GK_OK && o.timing) {
+            cl.t_filter += elapsed(ev[0], ev[1]);
+            cl.t_assign += elapsed(ev[1], ev[2]);
+            cl.t_balance += elapsed(ev[2], ev[3]);
+            cl.n_pass += 1;
+        }
+        return st;
+    };
+    GK_CUDA(launch_init(p, s));
+    for (int it = 0; it < o.max_iter; ++it) {
+        for (int bp = 0; bp < o.max_balance_iter; ++bp) {
+            gk_status st = pass(0);
+            if (st != GK_OK) return st;
+            if (!g_ws.host_ctl->cont_balance) break;
+        }
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[0], s));
+        GK_CUDA(launch_move(p, 0, s));
+        if (o.timing) GK_CUDA(cudaEventRecord(ev[1], s));
+        gk_status st = cl.read_ctl();
+        if (st != GK_OK) return st;
+        if (o.timing) {
+            cl.t_move += elapsed(ev[0], ev[1]);
+            cl.n_move += 1;
+        }
+        if (!g_ws.host_ctl->cont_move) break;
+    }
+    GK_CUDA(launch_final_begin(p, s));
+    gk_status st = cl.read_ctl();
+    if (st != GK_OK) return st;
+    while (g_ws.host_ctl->cont_final) {
+        st = pass(1);
+        if (st != GK_OK) return st;
+    }
+    return GK_OK;
+}
+
+gk_status check_options(const gk_options &o) {
+    if (o.max_iter < 1 || o.max_balance_iter < 1 || o.final_balance_iter < 0 ||
+        (o.assign_dtype != GK_F32 && o.assign_dtype != GK_F64) || !(o.delta_threshold == o.delta_threshold))
+        return GK_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (o.reserved[i] != 0) return GK_ERR_INVALID_ARG;
+    return GK_OK;
+}
+
+// Shared body of gk_partition (sort = true) and gk_balanced_kmeans (sort = false).
+gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                        int32_t d, int32_t k, double eps, const gk_options *opt, bool sort,
+                        double *centers_io, double *influence_io, int32_t *block_out,
+                        double *centers_out, double *influence_out, gk_result *result,
+                        void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (k < 1 || k > n || !(eps >= 0.0) || !block_out) return GK_ERR_INVALID_ARG;
+    if (!sort && (!centers_io || !influence_io)) return GK_ERR_INVALID_ARG;
+    gk_options o;
+    options_or_default(opt, &o);
+    if ((st = check_options(o)) != GK_OK) return st;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    if (ptr_kind(block_out, dev) == kForeign) return GK_ERR_INVALID_ARG;
+    bool block_host = ptr_kind(block_out, dev) == kHost;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    st = cl.init(coords, dtype, weights, n, d, k, sort, block_host, false);
+    if (st != GK_OK) return st;
+    Prob &p = cl.p;
+    p.eps = eps;
+    p.assign_f64 = o.assign_dtype == GK_F64;
+    p.max_iter = o.max_iter;
+    p.max_balance_iter = o.max_balance_iter;
+    p.final_balance_iter = o.final_balance_iter;
+    p.erosion = o.erosion;
+    if ((st = cl.geometry(o.delta_threshold)) != GK_OK) return st;
+    GK_CUDA(cudaMemcpyAsync(&p.ctl->thr, &cl.thr, sizeof(double), cudaMemcpyHostToDevice, cl.s));
+    const unsigned *perm = nullptr;
+    if (sort) {
+        Prob kp = cl.key_prob();
+        GK_CUDA(launch_keys(kp, p.keys[0], p.perm[0], cl.s));
+        int sel = 0;
+        GK_CUDA(launch_radix_sort(p, d == 2 ? 64 : 63, cl.b.hist, &sel, cl.s));
+        perm = p.perm[sel];
+    }
+    GK_CUDA(launch_gather(p, perm, cl.s));
+    if (sort) {
+        GK_CUDA(launch_centers(p, cl.s));
+    } else {
+        GK_CUDA(cudaMemcpyAsync(p.C, centers_io, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
+        GK_CUDA(cudaMemcpyAsync(p.I, influence_io, (size_t)k * 8, cudaMemcpyDefault, cl.s));
+    }
+    GK_CUDA(cudaEventRecord(g_ws.ev[1], cl.s));
+    if ((st = run_loop(cl, o)) != GK_OK) return st;
+    GK_CUDA(cudaEventRecord(g_ws.ev[2], cl.s));
+    int *out = block_host ? cl.b.block_stage : block_out;
+    GK_CUDA(launch_scatter(p, perm, out, cl.s));
+    if (block_host) st = copy_out(block_out, out, (size_t)n * 4, cl.s);
+    if (st == GK_OK) st = copy_out(sort ? centers_out : centers_io, p.C, (size_t)k * d * 8, cl.s);
+    if (st == GK_OK) st = copy_out(sort ? influence_out : influence_io, p.Iused, (size_t)k * 8, cl.s);
+    if (st != GK_OK) return st;
+    GK_CUDA(cudaEventRecord(g_ws.ev[3], cl.s));
+    if ((st = cl.read_ctl()) != GK_OK) return st;
+    const Ctl &c = *g_ws.host_ctl;
+    gk_status res = GK_OK;
+    if (c.status != kOk)
+        res = GK_ERR_TIMEOUT;
+    else if (!c.balanced)
+        res = GK_ERR_NOT_BALANCED;
+    fill_result(result, c, res, elapsed(g_ws.ev[0], g_ws.ev[1]), elapsed(g_ws.ev[1], g_ws.ev[2]),
+                elapsed(g_ws.ev[0], g_ws.ev[3]), n, cl);
+    return res;
+}
+
+}  // namespace
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" {
+
+void gk_default_options(gk_options *opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->max_iter = 50;
+    opt->max_balance_iter = 50;
+    opt->final_balance_iter = 500;
+    opt->erosion = 1;
+    opt->delta_threshold = -1.0;
+    opt->assign_dtype = GK_F64;
+    opt->use_graph = 1;
+}
+
+const char *gk_status_string(int32_t status) {
+    switch (status) {
+        case GK_OK: return "GK_OK";
+        case GK_ERR_INVALID_ARG: return "GK_ERR_INVALID_ARG";
+        case GK_ERR_CUDA: return "GK_ERR_CUDA";
+        case GK_ERR_OOM: return "GK_ERR_OOM";
+        case GK_ERR_NOT_BALANCED: return "GK_ERR_NOT_BALANCED";
+        case GK_ERR_TIMEOUT: return "GK_ERR_TIMEOUT";
+        default: return "GK_UNKNOWN_STATUS";
+    }
+}
+
+int32_t gk_abi_version(void) { return GK_ABI_VERSION; }
+
+gk_status gk_hilbert_keys(const void *coords, int32_t dtype, int64_t n, int32_t d,
+                          uint64_t *keys_out, void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (!keys_out) return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    PtrKind kk = ptr_kind(keys_out, dev);
+    if (kk == kForeign || (kk == kDevice && ((uintptr_t)keys_out % 8))) return GK_ERR_INVALID_ARG;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    // sort buffers are used as the key staging area
+    st = cl.init(coords, dtype, nullptr, n, d, 1, true, false, false);
+    if (st != GK_OK) return st;
+    if ((st = cl.geometry(-1.0)) != GK_OK) return st;
+    Prob kp = cl.key_prob();
+    unsigned long long *dst = kk == kDevice ? (unsigned long long *)keys_out : cl.p.keys[0];
+    GK_CUDA(launch_keys(kp, dst, nullptr, cl.s));
+    if (kk != kDevice) st = copy_out(keys_out, dst, (size_t)n * 8, cl.s);
+    if (st != GK_OK) return st;
+    GK_CUDA(cudaStreamSynchronize(cl.s));
+    return GK_OK;
+}
+
+gk_status gk_sfc_init(const void *coords, int32_t dtype, int64_t n, int32_t d, int32_t k,
+                      int64_t *perm_out, double *centers_out, void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (k < 1 || k > n) return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    if ((perm_out && ptr_kind(perm_out, dev) == kForeign) ||
+        (centers_out && ptr_kind(centers_out, dev) == kForeign))
+        return GK_ERR_INVALID_ARG;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    st = cl.init(coords, dtype, nullptr, n, d, k, true, false, perm_out != nullptr);
+    if (st != GK_OK) return st;
+    if ((st = cl.geometry(-1.0)) != GK_OK) return st;
+    Prob &p = cl.p;
+    Prob kp = cl.key_prob();
+    GK_CUDA(launch_keys(kp, p.keys[0], p.perm[0], cl.s));
+    int sel = 0;
+    GK_CUDA(launch_radix_sort(p, d == 2 ? 64 : 63, cl.b.hist, &sel, cl.s));
+    GK_CUDA(launch_gather(p, p.perm[sel], cl.s));
+    GK_CUDA(launch_centers(p, cl.s));
+    if (perm_out) {
+        GK_CUDA(launch_perm_out(p, p.perm[sel], cl.b.perm_stage, cl.s));
+        st = copy_out(perm_out, cl.b.perm_stage, (size_t)n * 8, cl.s);
+    }
+    if (st == GK_OK) st = copy_out(centers_out, p.C, (size_t)k * d * 8, cl.s);
+    if (st != GK_OK) return st;
+    GK_CUDA(cudaStreamSynchronize(cl.s));
+    return GK_OK;
+}
+
+gk_status gk_assign(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
+                    int32_t k, const double *centers, const double *influence,
+                    int32_t assign_dtype, int32_t *block_out, double *block_weights_out,
+                    void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (k < 1 || !centers || !influence || !block_out ||
+        (assign_dtype != GK_F32 && assign_dtype != GK_F64))
+        return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    if (ptr_kind(block_out, dev) == kForeign || ptr_kind(centers, dev) == kForeign ||
+        ptr_kind(influence, dev) == kForeign ||
+        (block_weights_out && ptr_kind(block_weights_out, dev) == kForeign))
+        return GK_ERR_INVALID_ARG;
+    bool block_host = ptr_kind(block_out, dev) == kHost;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    st = cl.init(coords, dtype, weights, n, d, k, false, block_host, false);
+    if (st != GK_OK) return st;
+    Prob &p = cl.p;
+    p.assign_f64 = assign_dtype == GK_F64;
+    if ((st = cl.geometry(-1.0)) != GK_OK) return st;
+    GK_CUDA(launch_gather(p, nullptr, cl.s));
+    GK_CUDA(cudaMemcpyAsync(p.C, centers, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
+    GK_CUDA(cudaMemcpyAsync(p.I, influence, (size_t)k * 8, cudaMemcpyDefault, cl.s));
+    GK_CUDA(launch_load_state(p, cl.s));
+    GK_CUDA(launch_pass(p, 2, cl.s));
+    int *out = block_host ? cl.b.block_stage : block_out;
+    GK_CUDA(launch_scatter(p, nullptr, out, cl.s));
+    if (block_host) st = copy_out(block_out, out, (size_t)n * 4, cl.s);
+    if (st == GK_OK) st = copy_out(block_weights_out, p.S64, (size_t)k * 8, cl.s);
+    if (st != GK_OK) return st;
+    if ((st = cl.read_ctl()) != GK_OK) return st;
+    if (g_ws.host_ctl->status != kOk) return GK_ERR_TIMEOUT;
+    return GK_OK;
+}
+
+gk_status gk_move_centers(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                          int32_t d, int32_t k, const int32_t *block, const double *centers,
+                          double *centers_out, double *delta_out, double *beta_out,
+                          void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (k < 1 || !block || !centers || !centers_out) return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    if (ptr_kind(block, dev) == kForeign || ptr_kind(centers, dev) == kForeign ||
+        ptr_kind(centers_out, dev) == kForeign || (delta_out && ptr_kind(delta_out, dev) == kForeign))
+        return GK_ERR_INVALID_ARG;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    st = cl.init(coords, dtype, weights, n, d, k, false, false, false);
+    if (st != GK_OK) return st;
+    Prob &p = cl.p;
+    if ((st = cl.geometry(-1.0)) != GK_OK) return st;
+    GK_CUDA(launch_gather(p, nullptr, cl.s));
+    GK_CUDA(cudaMemcpyAsync(p.A, block, (size_t)n * 4, cudaMemcpyDefault, cl.s));
+    GK_CUDA(cudaMemcpyAsync(p.C, centers, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
+    GK_CUDA(launch_block_weights(p, cl.s));
+    GK_CUDA(launch_move(p, 1, cl.s));
+    st = copy_out(centers_out, p.Cm, (size_t)k * d * 8, cl.s);
+    if (st == GK_OK) st = copy_out(delta_out, p.delta, (size_t)k * 8, cl.s);
+    if (st != GK_OK) return st;
+    if ((st = cl.read_ctl()) != GK_OK) return st;
+    if (g_ws.host_ctl->bad_block) return GK_ERR_INVALID_ARG;
+    if (beta_out) *beta_out = g_ws.host_ctl->beta;
+    return GK_OK;
+}
+
+gk_status gk_balanced_kmeans(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                             int32_t d, int32_t k, double eps, double *centers_inout,
+                             double *influence_inout, int32_t *block_out, const gk_options *opt,
+                             gk_result *result, void *stream) {
+    return kmeans_common(coords, dtype, weights, n, d, k, eps, opt, false, centers_inout,
+                         influence_inout, block_out, nullptr, nullptr, result, stream);
+}
+
+gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                       int32_t d, int32_t k, double eps, const gk_options *opt,
+                       int32_t *block_out, double *centers_out, double *influence_out,
+                       gk_result *result, void *stream) {
+    return kmeans_common(coords, dtype, weights, n, d, k, eps, opt, true, nullptr, nullptr,
+                         block_out, centers_out, influence_out, result, stream);
+}
+
+void gk_release(void) { release_all(); }
+
+}  // extern "C"

@@ -1,0 +1,528 @@
+// gk_bootstrap.cu -- space-filling-curve bootstrap (Algorithm 2: sfcIndex, sortGlobal,
+// redistribution, initial centers) and the final scatter to input order.
+//
+//   bbox_kernel        bounding box, weight range, finiteness (Section 4.4 "bb")
+//   keys_kernel        grid quantisation + Hilbert index (Algorithm 2 sfcIndex)
+//   radix_*            stable LSD radix sort of (key, index) (Algorithm 2 sortGlobal)
+//   gather_kernel      curve-sorted SoA copies + total weight (Algorithm 2 redistribution)
+//   tile_box_kernel    per-tile bounding boxes for the candidate filter (Section 4.4)
+//   centers_kernel     C[i] = sorted point i*n/k + n/(2k), influence 1 (Algorithm 2)
+//   scatter_kernel     block ids back to input order
+#include "gk_common.cuh"
+#include "gk_internal.h"
+
+namespace gk {
+
+// ------------------------------------------------------------------------------
+// Bounding box.  Per-thread extremes in the input precision, CTA reduction, then
+// one ordered-key atomic per CTA and axis.
+// ------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v);
+template <>
+__device__ __forceinline__ bool finite_val<float>(float v) {
+    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+}
+template <>
+__device__ __forceinline__ bool finite_val<double>(double v) {
+    return (((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
+template <typename T>
+__global__ void bbox_kernel(Prob p) {
+    count_launch(p.ctl);
+    const T *x = (const T *)p.coords;
+    const T *w = (const T *)p.weights;
+    T lo[3], hi[3];
+    T wlo = (T)INFINITY, whi = (T)-INFINITY;
+    for (int j = 0; j < 3; ++j) {
+        lo[j] = (T)INFINITY;
+        hi[j] = (T)-INFINITY;
+    }
+    int bad = 0, nonpos = 0;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        for (int j = 0; j < p.d; ++j) {
+            T v = x[i * p.d + j];
+            bad |= !finite_val<T>(v);
+            lo[j] = v < lo[j] ? v : lo[j];
+            hi[j] = v > hi[j] ? v : hi[j];
+        }
+        if (w) {
+            T v = w[i];
+            bad |= !finite_val<T>(v);
+            nonpos |= !(v > (T)0);
+            wlo = v < wlo ? v : wlo;
+            whi = v > whi ? v : whi;
+        }
+    }
+    __shared__ double s_lo[3][32], s_hi[3][32], s_wlo[32], s_whi[32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = 0; j < 3; ++j) {
+        double a = (double)lo[j], b = (double)hi[j];
+        for (int o = 16; o; o >>= 1) {
+            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) {
+            s_lo[j][warp] = a;
+            s_hi[j][warp] = b;
+        }
+    }
+    double a = (double)wlo, b = (double)whi;
+    for (int o = 16; o; o >>= 1) {
+        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (lane == 0) {
+        s_wlo[warp] = a;
+        s_whi[warp] = b;
+    }
+    bad = __syncthreads_or(bad);
+    nonpos = __syncthreads_or(nonpos);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < p.d; ++j) {
+            double l = s_lo[j][0], h = s_hi[j][0];
+            for (int q = 1; q < nw; ++q) {
+                l = fmin(l, s_lo[j][q]);
+                h = fmax(h, s_hi[j][q]);
+            }
+            atomicMin(&p.ctl->bb_lo[j], okey_f64(l));
+            atomicMax(&p.ctl->bb_hi[j], okey_f64(h));
+        }
+        if (w) {
+            double l = s_wlo[0], h = s_whi[0];
+            for (int q = 1; q < nw; ++q) {
+                l = fmin(l, s_wlo[q]);
+                h = fmax(h, s_whi[q]);
+            }
+            atomicMin(&p.ctl->w_lo, okey_f64(l));
+            atomicMax(&p.ctl->w_hi, okey_f64(h));
+        }
+        if (bad) atomicOr(&p.ctl->nonfinite, 1);
+        if (nonpos) atomicOr(&p.ctl->nonpositive_w, 1);
+    }
+}
+
+// ------------------------------------------------------------------------------
+// Hilbert keys.  Cell = floor(fl(x - lo) * 2^m) clamped to 2^b - 1, computed from
+// the bits of the (non-negative) difference; then J. Skilling's transform
+// ("Programming the Hilbert curve", 2004): undo the excess work level by level,
+// Gray-encode, and interleave the transposed bits (axis 0 most significant).
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned quant_bits_f64(double v, int m, int b) {
+    unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long top = (1ull << b) - 1ull;
+    if (ex == 0) return 0u;  // zero (v >= 0; subnormals floor to 0 for b <= 32)
+    unsigned long long mant = (bits & 0xfffffffffffffull) | 0x10000000000000ull;
+    int sh = ex - 1075 + m;  // v * 2^m = mant * 2^sh
+    unsigned long long q;
+    if (sh >= 0)
+        q = sh > 11 ? ~0ull : (mant << sh);
+    else
+        q = sh > -64 ? (mant >> (-sh)) : 0ull;
+    return (unsigned)(q > top ? top : q);
+}
+__device__ __forceinline__ unsigned quant_bits_f32(float v, int m, int b) {
+    unsigned bits = __float_as_uint(v);
+    int ex = (int)((bits >> 23) & 0xff);
+    unsigned long long top = (1ull << b) - 1ull;
+    if (ex == 0) return 0u;
+    unsigned long long mant = (unsigned long long)((bits & 0x7fffffu) | 0x800000u);
+    int sh = ex - 150 + m;
+    unsigned long long q;
+    if (sh >= 0)
+        q = sh > 40 ? ~0ull : (mant << sh);
+    else
+        q = sh > -64 ? (mant >> (-sh)) : 0ull;
+    return (unsigned)(q > top ? top : q);
+}
+
+__host__ __device__ __forceinline__ unsigned long long spread2(unsigned v) {
+    unsigned long long x = v;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffull;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffull;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0full;
+    x = (x | (x << 2)) & 0x3333333333333333ull;
+    x = (x | (x << 1)) & 0x5555555555555555ull;
+    return x;
+}
+__host__ __device__ __forceinline__ unsigned long long spread3(unsigned v) {
+    unsigned long long x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ unsigned long long skilling_key(unsigned X[D], int b) {
+    // inverse undo, coarse level first
+    for (int lev = b - 1; lev >= 1; --lev) {
+        unsigned Q = 1u << lev, P = Q - 1u;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            if (X[i] & Q) {
+                X[0] ^= P;
+            } else {
+                unsigned t = (X[0] ^ X[i]) & P;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    // Gray encode
+#pragma unroll
+    for (int i = 1; i < D; ++i) X[i] ^= X[i - 1];
+    unsigned y = X[D - 1] >> 1;  // bit l of t = xor of the bits of X[D-1] above l
+    y ^= y >> 1;
+    y ^= y >> 2;
+    y ^= y >> 4;
+    y ^= y >> 8;
+    y ^= y >> 16;
+#pragma unroll
+    for (int i = 0; i < D; ++i) X[i] ^= y;
+    if (D == 2) return (spread2(X[0]) << 1) | spread2(X[1]);
+    return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
+}
+
+template <typename T, int D>
+__global__ void keys_kernel(Prob p, unsigned long long *keys_out, unsigned *perm_out) {
+    count_launch(p.ctl);
+    const T *x = (const T *)p.coords;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n) return;
+    unsigned q[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        if (sizeof(T) == 8) {
+            double v = __dsub_rn((double)x[i * D + j], p.origin[j]);
+            q[j] = quant_bits_f64(v, p.grid_m, p.bits);
+        } else {
+            float v = __fsub_rn((float)x[i * D + j], (float)p.origin[j]);
+            q[j] = quant_bits_f32(v, p.grid_m, p.bits);
+        }
+    }
+    keys_out[i] = skilling_key<D>(q, p.bits);
+    if (perm_out) perm_out[i] = (unsigned)i;
+}
+
+// ------------------------------------------------------------------------------
+// LSD radix sort of (uint64 key, uint32 value), 8-bit digits, stable.
+// The array is cut into G contiguous segments of whole tiles (2048 items); each
+// CTA owns one segment.  Per pass: upsweep (segment digit counts), one-CTA scan of
+// the digit-major count table, downsweep (tiles of a segment in order; stable
+// ranks inside a tile from per-warp match_any counting).
+// ------------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void radix_upsweep(const unsigned long long *keys, long long n, int shift,
+                              int tiles_per_seg, int G, unsigned *hist, Ctl *ctl) {
+    count_launch(ctl);
+    __shared__ unsigned cnt[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    long long beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
+    long long end = beg + (long long)tiles_per_seg * kSortTile;
+    if (end > n) end = n;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * G + blockIdx.x] = cnt[i];
+}
+
+// Exclusive scan of m counts with one CTA of 1024 threads.
+__global__ void radix_scan(unsigned *hist, int m, Ctl *ctl) {
+    count_launch(ctl);
+    __shared__ unsigned part[1024];
+    int t = threadIdx.x;
+    int per = (m + 1023) / 1024;
+    int b = t * per, e = min(m, b + per);
+    unsigned s = 0;
+    for (int i = b; i < e; ++i) s += hist[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        unsigned v = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - s;  // exclusive prefix of this thread's chunk
+    for (int i = b; i < e; ++i) {
+        unsigned c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
+                unsigned long long *keys_out, unsigned *vals_out, long long n, int shift,
+                int tiles_per_seg, int G, const unsigned *offs, Ctl *ctl) {
+    count_launch(ctl);
+    __shared__ unsigned run_off[256];
+    __shared__ unsigned whist[kSortWarps][256];
+    __shared__ unsigned wofs[kSortWarps][256];
+    __shared__ unsigned tcnt[256];
+    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < 256; i += kSortThreads) run_off[i] = offs[(long long)i * G + blockIdx.x];
+    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&whist[0][0])[i] = 0;
+    __syncthreads();
+    unsigned lt_mask = (1u << lane) - 1u;
+    long long seg_beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
+    for (int t = 0; t < tiles_per_seg; ++t) {
+        long long tile_beg = seg_beg + (long long)t * kSortTile;
+        if (tile_beg >= n) break;
+        unsigned long long k[kSortItems];
+        unsigned v[kSortItems], dig[kSortItems], loc[kSortItems];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            long long i = tile_beg + warp * (32 * kSortItems) + r * 32 + lane;
+            bool ok = i < n;
+            k[r] = ok ? keys_in[i] : 0ull;
+            v[r] = ok ? vals_in[i] : 0u;
+            dig[r] = ok ? ((unsigned)(k[r] >> shift) & 255u) : 256u;
+            unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            unsigned base = ok ? whist[warp][dig[r]] : 0u;
+            loc[r] = base + __popc(peers & lt_mask);
+            __syncwarp();
+            if (ok && (peers & lt_mask) == 0u) whist[warp][dig[r]] = base + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int dgt = tid; dgt < 256; dgt += kSortThreads) {
+            unsigned acc = 0;
+            for (int w = 0; w < kSortWarps; ++w) {
+                wofs[w][dgt] = acc;
+                acc += whist[w][dgt];
+            }
+            tcnt[dgt] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            if (dig[r] < 256u) {
+                unsigned dst = run_off[dig[r]] + wofs[warp][dig[r]] + loc[r];
+                if (dst < (unsigned long long)n) {  // always true when counts are consistent
+                    keys_out[dst] = k[r];
+                    vals_out[dst] = v[r];
+                }
+            }
+        }
+        __syncthreads();
+        for (int dgt = tid; dgt < 256; dgt += kSortThreads) {
+            run_off[dgt] += tcnt[dgt];
+            for (int w = 0; w < kSortWarps; ++w) whist[w][dgt] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------
+// Gather into curve order: SoA frame coordinates (FP32), raw FP64 coordinates,
+// sorted weights, and the total weight as a 128-bit fixed-point sum.
+// ------------------------------------------------------------------------------
+template <typename T>
+__global__ void gather_kernel(Prob p, const unsigned *perm) {
+    count_launch(p.ctl);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const T *x = (const T *)p.coords;
+    const T *w = (const T *)p.weights;
+    unsigned long long wfix = 0;
+    if (i < p.n_pad) {
+        long long src = i < p.n ? (perm ? (long long)perm[i] : i) : 0;
+        bool ok = i < p.n && src < p.n;  // a permutation entry is always < n
+        for (int j = 0; j < p.d; ++j) {
+            T v = ok ? x[src * p.d + j] : (T)0;
+            if (sizeof(T) == 8) {
+                double dv = (double)v;
+                p.X64[j * p.n_pad + i] = dv;
+                double f = ok ? __dmul_rn(__dsub_rn(dv, p.origin[j]), p.scale) : 0.0;
+                p.X32[j * p.n_pad + i] = __double2float_rn(f);
+            } else {
+                p.X32[j * p.n_pad + i] = (float)v;
+            }
+        }
+        if (p.weighted) {
+            T wv = ok ? w[src] : (T)0;
+            ((T *)p.Ws)[i] = wv;
+            if (ok) wfix = (unsigned long long)(sizeof(T) == 8 ? fix_f64((double)wv, p.Fw)
+                                                                : fix_f32((float)wv, p.Fw));
+        }
+    }
+    if (p.weighted) {
+        for (int o = 16; o; o >>= 1) wfix += __shfl_xor_sync(0xffffffffu, wfix, o);
+        if ((threadIdx.x & 31) == 0 && wfix) atomic_add_u128(&p.ctl->wsum_lo, wfix);
+    }
+}
+
+// Per tile: origin = centre of the bounding box of its frame coordinates, half
+// extents and radius rounded upwards so that every point of the tile lies inside.
+__global__ void tile_box_kernel(Prob p) {
+    count_launch(p.ctl);
+    int t = blockIdx.x;
+    long long i = (long long)t * kTile + threadIdx.x;
+    bool ok = i < p.n;
+    float lo[3], hi[3];
+    for (int j = 0; j < 3; ++j) {
+        float v = (ok && j < p.d) ? p.X32[j * p.n_pad + i] : 0.0f;
+        lo[j] = ok ? v : INFINITY;
+        hi[j] = ok ? v : -INFINITY;
+    }
+    __shared__ float s[6][kTile / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j < 3; ++j) {
+        for (int o = 16; o; o >>= 1) {
+            lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
+            hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
+        }
+        if (lane == 0) {
+            s[j][warp] = lo[j];
+            s[3 + j][warp] = hi[j];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float o[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
+        float r2 = 0.0f;
+        for (int j = 0; j < p.d; ++j) {
+            float l = s[j][0], u = s[3 + j][0];
+            for (int q = 1; q < kTile / 32; ++q) {
+                l = fminf(l, s[j][q]);
+                u = fmaxf(u, s[3 + j][q]);
+            }
+            o[j] = 0.5f * l + 0.5f * u;
+            h[j] = fmaxf(__fsub_ru(u, o[j]), __fsub_ru(o[j], l));
+            r2 = __fadd_ru(r2, __fmul_ru(h[j], h[j]));
+        }
+        p.tiles[2 * t] = make_float4(o[0], o[1], o[2], __fsqrt_ru(r2));
+        p.tiles[2 * t + 1] = make_float4(h[0], h[1], h[2], 0.0f);
+    }
+}
+
+// Initial centers on the curve (raw coordinates, FP64) and influence 1.
+__global__ void centers_kernel(Prob p) {
+    count_launch(p.ctl);
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.k) return;
+    long long idx = (long long)c * p.n / p.k + p.n / (2ll * p.k);
+    for (int j = 0; j < p.d; ++j)
+        p.C[c * p.d + j] = p.dtype == 1 ? p.X64[j * p.n_pad + idx] : (double)p.X32[j * p.n_pad + idx];
+    p.I[c] = 1.0;
+}
+
+__global__ void scatter_kernel(const int *A_sorted, const unsigned *perm, long long n, int *out,
+                               Ctl *ctl) {
+    count_launch(ctl);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        long long j = perm ? (long long)perm[i] : i;
+        if (j < n) out[j] = A_sorted[i];
+    }
+}
+
+__global__ void perm_to_i64_kernel(const unsigned *perm, long long n, long long *out, Ctl *ctl) {
+    count_launch(ctl);
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = perm[i];
+}
+
+// ------------------------------------------------------------------------------
+// Host launchers.
+// ------------------------------------------------------------------------------
+static int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+cudaError_t launch_bbox(const Prob &p, cudaStream_t s) {
+    int grid = 152 * 4;
+    long long need = (p.n + 255) / 256;
+    if (need < grid) grid = (int)need;
+    if (grid < 1) grid = 1;
+    if (p.dtype == 1)
+        bbox_kernel<double><<<grid, 256, 0, s>>>(p);
+    else
+        bbox_kernel<float><<<grid, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_keys(const Prob &p, unsigned long long *keys, unsigned *perm, cudaStream_t s) {
+    int grid = blocks_for(p.n, 256);
+    if (p.dtype == 1) {
+        if (p.d == 2)
+            keys_kernel<double, 2><<<grid, 256, 0, s>>>(p, keys, perm);
+        else
+            keys_kernel<double, 3><<<grid, 256, 0, s>>>(p, keys, perm);
+    } else {
+        if (p.d == 2)
+            keys_kernel<float, 2><<<grid, 256, 0, s>>>(p, keys, perm);
+        else
+            keys_kernel<float, 3><<<grid, 256, 0, s>>>(p, keys, perm);
+    }
+    return cudaGetLastError();
+}
+
+size_t radix_hist_entries(long long n) {
+    long long ntiles = (n + kSortTile - 1) / kSortTile;
+    long long tps = (ntiles + 1215) / 1216;
+    if (tps < 1) tps = 1;
+    long long G = (ntiles + tps - 1) / tps;
+    if (G < 1) G = 1;
+    return (size_t)(256 * G);
+}
+
+// Sorts keys[0]/perm[0] (n items) in place through the alternate buffers; returns
+// in *sel the index of the buffer pair holding the result.
+cudaError_t launch_radix_sort(const Prob &p, int key_bits, unsigned *hist, int *sel,
+                              cudaStream_t s) {
+    long long n = p.n;
+    long long ntiles = (n + kSortTile - 1) / kSortTile;
+    int tps = (int)((ntiles + 1215) / 1216);
+    if (tps < 1) tps = 1;
+    int G = (int)((ntiles + tps - 1) / tps);
+    if (G < 1) G = 1;
+    int cur = 0;
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        radix_upsweep<<<G, 256, 0, s>>>(p.keys[cur], n, shift, tps, G, hist, p.ctl);
+        radix_scan<<<1, 1024, 0, s>>>(hist, 256 * G, p.ctl);
+        radix_downsweep<<<G, kSortThreads, 0, s>>>(p.keys[cur], p.perm[cur], p.keys[cur ^ 1],
+                                                    p.perm[cur ^ 1], n, shift, tps, G, hist, p.ctl);
+        cur ^= 1;
+    }
+    *sel = cur;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
+    int grid = blocks_for(p.n_pad, 256);
+    if (p.dtype == 1)
+        gather_kernel<double><<<grid, 256, 0, s>>>(p, perm);
+    else
+        gather_kernel<float><<<grid, 256, 0, s>>>(p, perm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tile_box_kernel<<<p.ntiles, kTile, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centers(const Prob &p, cudaStream_t s) {
+    centers_kernel<<<blocks_for(p.k, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const Prob &p, const unsigned *perm, int *out, cudaStream_t s) {
+    scatter_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(p.A, perm, p.n, out, p.ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perm_out(const Prob &p, const unsigned *perm, long long *out, cudaStream_t s) {
+    perm_to_i64_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(perm, p.n, out, p.ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace gk

@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/gk.h declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libgk():
+    from paper_1805_01208_gb300.build import build
+    path = build()
+    return ctypes.CDLL(path)
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "gk.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gk_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
+                 "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
+                 "gk_status_string", "gk_abi_version"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(libgk):
+    missing = [name for name in _declared() if not hasattr(libgk, name)]
+    assert not missing, missing
+
+
+def test_host_only_helpers(libgk):
+    import paper_1805_01208_gb300 as gk
+    assert gk.lib().gk_abi_version() == 1
+    o = gk.default_options()
+    assert (o.max_iter, o.max_balance_iter, o.final_balance_iter, o.erosion) == (50, 50, 500, 1)
+    assert o.delta_threshold < 0 and o.assign_dtype == gk.GK_F64 and o.use_graph == 1
+    assert gk.status_string(gk.GK_ERR_NOT_BALANCED) == "GK_ERR_NOT_BALANCED"
+    assert gk.status_string(99) == "GK_UNKNOWN_STATUS"
+
+
+def test_struct_layouts_match_header():
+    import paper_1805_01208_gb300 as gk
+    # gk_options: 4 int32, double, 3 int32, 5 int32 reserved (8-byte aligned double)
+    assert ctypes.sizeof(gk.Options) == 4 * 4 + 8 + 3 * 4 + 5 * 4
+    assert ctypes.sizeof(gk.Result) == 6 * 4 + 4 * 8 + 2 * 8 + 3 * 8 + 4 * 8 + 4 * 8 + 8 + 8
+
+
+def test_library_is_built_for_sm103a(libgk):
+    from paper_1805_01208_gb300.build import ARCH
+    assert "arch=compute_103a,code=sm_103a" in ARCH
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_1805_01208_gb300 as gk
+    monkeypatch.setattr(gk, "_lib", None)
+    monkeypatch.setattr(gk, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        gk.lib()
