@@ -101,20 +101,24 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.Ws = p.weighted ? (void *)take((size_t)np * es) : nullptr;
     p.A = (int *)take((size_t)np * 4);
     p.tiles = (float4 *)take((size_t)p.ntiles * 32);
-    p.cand_cnt = (int *)take((size_t)p.ntiles * 4);
-    p.cand_list = (int *)take((size_t)p.ntiles * kCap * 4);
+    p.supers = (float4 *)take((size_t)p.nsupers * 32);
+    p.tcnt = (int *)take((size_t)p.ntiles * 4);
+    p.tcoef = (float4 *)take((size_t)p.ntiles * kCap * 16);
+    p.tga = (float *)take((size_t)p.ntiles * kCap * 4);
+    p.tcid = (int *)take((size_t)p.ntiles * kCap * 4);
     p.C = (double *)take((size_t)k * d * 8);
-    p.I = (double *)take((size_t)k * 8);
-    p.Iused = (double *)take((size_t)k * 8);
-    p.g64 = (double *)take((size_t)k * 8);
     p.Cm = (double *)take((size_t)k * d * 8);
     p.delta = (double *)take((size_t)k * 8);
     p.S64 = (double *)take((size_t)k * 8);
+    p.Iin = (double *)take((size_t)k * 8);
+    p.I2 = (double *)take((size_t)2 * k * 8);
+    p.g64_2 = (double *)take((size_t)2 * k * 8);
+    p.part = (double *)take((size_t)(k + 127) / 128 * 8);
     p.Sfix = (unsigned long long *)take((size_t)k * 16);
     p.SXfix = (unsigned long long *)take((size_t)k * d * 16);
     p.BBlo = (unsigned long long *)take((size_t)k * d * 8);
     p.BBhi = (unsigned long long *)take((size_t)k * d * 8);
-    p.cdata = (float4 *)take((size_t)k * 32);
+    p.cdata2 = (float4 *)take((size_t)2 * k * 32);
     b.block_stage = stage_block ? (int *)take((size_t)n * 4) : nullptr;
     b.perm_stage = perm_out ? (long long *)take((size_t)n * 8) : nullptr;
     return off;
@@ -205,6 +209,7 @@ struct Call {
         p.dtype = dtype;
         p.weighted = weights != nullptr;
         p.ntiles = (int)(p.n_pad / kTile);
+        p.nsupers = (p.ntiles + kSuperTiles - 1) / kSuperTiles;
         p.bits = d == 2 ? 32 : 21;
         int dev = 0;
         GK_CUDA(cudaGetDevice(&dev));
@@ -309,7 +314,9 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     r->max_imbalance = c.max_imbalance;
     r->max_delta = c.max_delta;
     r->delta_threshold = c.thr;
-    r->avg_candidates = c.passes > 0 ? (double)c.cand_sum / ((double)c.passes * (double)n) : 0.0;
+    unsigned long long cand = 0;
+    for (int i = 0; i < kStripes; ++i) cand += c.cand_stripes[i];
+    r->avg_candidates = c.passes > 0 ? (double)cand / ((double)c.passes * (double)n) : 0.0;
     r->rechecked_points = (int64_t)c.rechecks;
     r->kernel_launches = (int64_t)c.launches;
     r->time_bootstrap_ms = t_boot;
@@ -465,7 +472,7 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
         GK_CUDA(launch_centers(p, cl.s));
     } else {
         GK_CUDA(cudaMemcpyAsync(p.C, centers_io, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
-        GK_CUDA(cudaMemcpyAsync(p.I, influence_io, (size_t)k * 8, cudaMemcpyDefault, cl.s));
+        GK_CUDA(cudaMemcpyAsync(p.Iin, influence_io, (size_t)k * 8, cudaMemcpyDefault, cl.s));
     }
     GK_CUDA(cudaEventRecord(g_ws.ev[1], cl.s));
     if ((st = run_loop(cl, o)) != GK_OK) return st;
@@ -474,7 +481,8 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     GK_CUDA(launch_scatter(p, perm, out, cl.s));
     if (block_host) st = copy_out(block_out, out, (size_t)n * 4, cl.s);
     if (st == GK_OK) st = copy_out(sort ? centers_out : centers_io, p.C, (size_t)k * d * 8, cl.s);
-    if (st == GK_OK) st = copy_out(sort ? influence_out : influence_io, p.Iused, (size_t)k * 8, cl.s);
+    GK_CUDA(launch_export(p, cl.s));
+    if (st == GK_OK) st = copy_out(sort ? influence_out : influence_io, p.Iin, (size_t)k * 8, cl.s);
     if (st != GK_OK) return st;
     GK_CUDA(cudaEventRecord(g_ws.ev[3], cl.s));
     if ((st = cl.read_ctl()) != GK_OK) return st;
@@ -603,7 +611,7 @@ gk_status gk_assign(const void *coords, int32_t dtype, const void *weights, int6
     if ((st = cl.geometry(-1.0)) != GK_OK) return st;
     GK_CUDA(launch_gather(p, nullptr, cl.s));
     GK_CUDA(cudaMemcpyAsync(p.C, centers, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
-    GK_CUDA(cudaMemcpyAsync(p.I, influence, (size_t)k * 8, cudaMemcpyDefault, cl.s));
+    GK_CUDA(cudaMemcpyAsync(p.Iin, influence, (size_t)k * 8, cudaMemcpyDefault, cl.s));
     GK_CUDA(launch_load_state(p, cl.s));
     GK_CUDA(launch_pass(p, 2, cl.s));
     int *out = block_host ? cl.b.block_stage : block_out;

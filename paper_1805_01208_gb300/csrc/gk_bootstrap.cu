@@ -415,7 +415,33 @@ __global__ void centers_kernel(Prob p) {
     long long idx = (long long)c * p.n / p.k + p.n / (2ll * p.k);
     for (int j = 0; j < p.d; ++j)
         p.C[c * p.d + j] = p.dtype == 1 ? p.X64[j * p.n_pad + idx] : (double)p.X32[j * p.n_pad + idx];
-    p.I[c] = 1.0;
+    p.Iin[c] = 1.0;
+}
+
+// Supertile boxes from the boxes of their tiles (rounded outwards).
+__global__ void super_box_kernel(Prob p) {
+    count_launch(p.ctl);
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= p.nsupers) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int t0 = s * kSuperTiles, t1 = min(p.ntiles, t0 + kSuperTiles);
+    for (int t = t0; t < t1; ++t) {
+        float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
+        float o[3] = {a.x, a.y, a.z}, h[3] = {b.x, b.y, b.z};
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = fminf(lo[j], __fsub_rd(o[j], h[j]));
+            hi[j] = fmaxf(hi[j], __fadd_ru(o[j], h[j]));
+        }
+    }
+    float o[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
+    float r2 = 0.0f;
+    for (int j = 0; j < p.d; ++j) {
+        o[j] = 0.5f * lo[j] + 0.5f * hi[j];
+        h[j] = fmaxf(__fsub_ru(hi[j], o[j]), __fsub_ru(o[j], lo[j]));
+        r2 = __fadd_ru(r2, __fmul_ru(h[j], h[j]));
+    }
+    p.supers[2 * s] = make_float4(o[0], o[1], o[2], __fsqrt_ru(r2));
+    p.supers[2 * s + 1] = make_float4(h[0], h[1], h[2], 0.0f);
 }
 
 __global__ void scatter_kernel(const int *A_sorted, const unsigned *perm, long long n, int *out,
@@ -507,6 +533,9 @@ cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     tile_box_kernel<<<p.ntiles, kTile, 0, s>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,18 +1,22 @@
 // gk_common.cuh -- shared device-side definitions of the balanced k-means library.
 //
 // Data layout in device memory (one problem at a time, inside the workspace):
-//   X32   d planes of n_pad FP32: curve-sorted coordinates in the assignment frame
-//         (FP64 inputs: (x - lo) * 2^-E rounded to FP32, E = grid exponent of the
-//         bounding box; FP32 inputs: the raw coordinates).
-//   X64   d planes of n_pad FP64: curve-sorted raw coordinates (FP64 inputs only).
-//   Ws    n_pad sorted weights in the input dtype (weighted problems only).
-//   A     n_pad int32 block ids in sorted order.
-//   tiles 2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -}.
-//   cands per tile: count (int32; -1 = overflow, scan all centers) + kCap ids.
-//   per center: C (k x d FP64, input units), I, I_used, g64 = 1/I^2, moved centers,
-//         delta, 128-bit fixed-point block weights, 128-bit fixed-point coordinate
-//         sums, ordered-key bounding boxes, and cdata = 2 float4 per center
-//         {frame center hi xyz, g = 1/I^2 as FP32}, {frame center lo xyz, 0}.
+//   X32    d planes of n_pad FP32: curve-sorted coordinates in the assignment frame
+//          (FP64 inputs: (x - lo) * 2^-E rounded to FP32, E = grid exponent of the
+//          bounding box; FP32 inputs: the raw coordinates).  Padding entries are 0.
+//   X64    d planes of n_pad FP64: curve-sorted raw coordinates (FP64 inputs only).
+//   Ws     n_pad sorted weights in the input dtype (weighted problems only).
+//   A      n_pad int32 block ids in sorted order.
+//   tiles  2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -};
+//   supers the same per supertile of kSuperTiles tiles.
+//   per tile candidate table (written by the filter every pass): count (int32, -1 =
+//          overflow: scan all centers) and kCap entries of coefficients
+//          {-2 g q.xyz, g |q|^2} (float4), g (float) and center id (int32), q = frame
+//          center relative to the tile origin, g = scaled 1/I^2.
+//   per center: C, Cm (k x d FP64, input units), delta, S64, Iin (k FP64), influence and
+//          1/I^2 double-buffered (I2, g64_2: 2 x k FP64), cdata2 (2 x 2 float4 per center:
+//          {frame center hi xyz, g32}, {frame center lo xyz, 0}), 128-bit fixed-point
+//          block weights and coordinate sums, ordered-key bounding boxes.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,19 +24,21 @@
 
 namespace gk {
 
-constexpr int kTile = 256;          // points per tile (one CTA of the assign kernel)
-constexpr int kCap = 256;           // candidate centers stored per tile
-constexpr int kFilterWarps = 8;     // tiles per CTA of the filter kernel
+constexpr int kTile = 256;          // points per tile (one warp of the assign kernel)
+constexpr int kSuperTiles = 16;     // tiles per supertile (one CTA of the filter kernel)
+constexpr int kCap = 64;            // candidate centers stored per tile
+constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
 constexpr int kCenterChunk = 1024;  // centers staged in shared memory per bulk copy
-constexpr int kFixBits = 55;        // |fixed-point value| < 2^55 per point
+constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
+constexpr int kStripes = 64;        // striped counters for per-pass statistics
 constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers
 
 // Error codes mirrored from gk.h (device code does not include the C header).
 constexpr int kOk = 0;
 constexpr int kErrTimeout = 5;
 
-// Device-resident control block: geometry found by the bounding-box kernel,
-// loop state and counters.  Written by kernels, read back by the host.
+// Device-resident control block: geometry found by the bounding-box kernel, loop
+// state and counters.  Written by kernels, read back by the host.
 struct Ctl {
     unsigned long long bb_lo[3], bb_hi[3];  // ordered keys of the coordinate extremes
     unsigned long long w_lo, w_hi;          // ordered keys of the weight extremes
@@ -49,12 +55,17 @@ struct Ctl {
     int cont_move;                          // outer while-loop condition
     int cont_final;                         // final balance loop condition
     int final_passes;
+    int isel;                               // current buffer of I2 / g64_2 / cdata2
+    int iused_sel;                          // buffer the last assignment was computed with
+    int gshift;                             // g32 = g * 2^-gshift
+    unsigned int done_count;                // last-block-done counter (reset by the last block)
+    int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
     double max_delta;
     double thr;                             // absolute movement threshold
     double W, target, ceil_avg, bound;      // total weight, W/k, ceil(W/k), (1+eps)ceil(W/k)
     double beta;
-    unsigned long long cand_sum;            // sum over points and passes of candidates
+    unsigned long long maxS_key, maxg_key, maxd_key;  // ordered keys of per-pass maxima
     unsigned long long rechecks;            // FP64 re-decisions
     unsigned long long overflow_tiles;      // tiles whose candidate list overflowed
     unsigned long long wsum_lo, wsum_hi;    // total weight, 128-bit fixed point
@@ -62,6 +73,7 @@ struct Ctl {
     unsigned long long t_assign0;           // globaltimer at the start of the last assign launch
     unsigned long long assign_ns;           // sum of assign launch durations (globaltimer)
     unsigned long long assign_cnt;          // assign launches measured
+    unsigned long long cand_stripes[kStripes];  // sum over tiles and passes of candidates x points
 };
 
 // Problem descriptor passed by value to every kernel.
@@ -69,7 +81,7 @@ struct Prob {
     long long n;
     long long n_pad;
     int d, k, dtype, weighted, assign_f64;
-    int ntiles;
+    int ntiles, nsupers;
     int bits, grid_m;           // Hilbert bits per axis and the scaling exponent b - E
     int Fw, Fx;                 // fixed-point exponents of weights and coordinate sums
     double origin[3];           // frame: (x - origin) * scale
@@ -88,15 +100,18 @@ struct Prob {
     double *X64;
     void *Ws;
     int *A;
-    float4 *tiles;
-    int *cand_cnt;
-    int *cand_list;
+    float4 *tiles, *supers;
+    // per-tile candidate tables
+    int *tcnt;
+    float4 *tcoef;
+    float *tga;
+    int *tcid;
     // per-center state
-    double *C, *I, *Iused, *g64, *Cm, *delta, *S64;
+    double *C, *Cm, *delta, *S64, *Iin, *I2, *g64_2, *part;
     unsigned long long *Sfix;   // 2 per block (lo, hi)
     unsigned long long *SXfix;  // 2 per (block, axis)
-    unsigned long long *BBlo, *BBhi;  // per (block, axis) ordered keys
-    float4 *cdata;              // 2 per block
+    unsigned long long *BBlo, *BBhi;  // per (block, axis) ordered keys (input precision)
+    float4 *cdata2;             // 2 buffers x 2 float4 per block
     Ctl *ctl;
 };
 
@@ -122,6 +137,14 @@ __host__ __device__ inline double okey_to_f64(unsigned long long k) {
     return v;
 #endif
 }
+__device__ __forceinline__ unsigned okey_f32(float v) {
+    unsigned b = __float_as_uint(v);
+    return (b >> 31) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float okey_to_f32(unsigned k) {
+    unsigned b = (k >> 31) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
 
 // ------------------------------------------------------------------------------
 // Fixed point: trunc(v * 2^F) as a signed 64-bit integer, from the bits of v.
@@ -145,6 +168,18 @@ __device__ __forceinline__ long long fix_f32(float v, int F) {
     unsigned long long mag = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
     return (b >> 31) ? -(long long)mag : (long long)mag;
 }
+// trunc(w * x * 2^F) for FP32 w > 0 and x, from the exact 48-bit product of the
+// mantissas (integer arithmetic only).
+__device__ __forceinline__ long long fix_prod_f32(float w, float x, int F) {
+    unsigned bw = __float_as_uint(w), bx = __float_as_uint(x);
+    int ew = (int)((bw >> 23) & 0xff), ex = (int)((bx >> 23) & 0xff);
+    if (ew == 0 || ex == 0) return 0;
+    unsigned long long m = (unsigned long long)((bw & 0x7fffffu) | 0x800000u) *
+                           (unsigned long long)((bx & 0x7fffffu) | 0x800000u);
+    int sh = ew + ex - 300 + F;
+    unsigned long long mag = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    return (bx >> 31) ? -(long long)mag : (long long)mag;
+}
 
 // 128-bit two's-complement accumulation of a signed 64-bit value into (lo, hi).
 __device__ __forceinline__ void atomic_add_i128(unsigned long long *lohi, long long v) {
@@ -162,10 +197,6 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *lohi, unsign
 __device__ __forceinline__ double i128_to_f64(unsigned long long lo, unsigned long long hi, int F) {
     double v = (double)(long long)hi * 18446744073709551616.0 + (double)lo;
     return ldexp(v, -F);
-}
-
-__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int src) {
-    return __shfl_sync(0xffffffffu, v, src);
 }
 
 // ------------------------------------------------------------------------------
@@ -221,6 +252,23 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ __forceinline__ void count_launch(Ctl *ctl) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->launches, 1ull);
+}
+
+// Last-block-done: every thread of every CTA calls this once; it returns true (in
+// all threads) in the CTA that finished last, to which the global writes of all
+// CTAs are then visible.  That CTA resets the counter.
+__device__ __forceinline__ bool last_block(Ctl *ctl) {
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(&ctl->done_count, 1u);
+        s_last = prev == gridDim.x - 1;
+        if (s_last) ctl->done_count = 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last;
 }
 
 }  // namespace gk

@@ -1,52 +1,100 @@
 // gk_kmeans.cu -- the balanced k-means iteration (Algorithm 1 AssignAndBalance and the
 // movement / erosion steps of Algorithm 2; Section 4.2 Eq. 1-3; Section 4.4).
 //
-//   filter_kernel     per-tile candidate centers from the tile's bounding box
-//                     (Section 4.4; lower bound minDist/influence against the
-//                     smallest upper bound maxDist/influence over all centers)
+//   init_a/init_b     influence state, center data, totals, loop state
+//   filter_kernel     candidate centers per tile from bounding boxes (Section 4.4):
+//                     a supertile against all centers, then each tile against the
+//                     supertile's list; writes each tile's coefficient table
 //   assign_kernel     effective-distance argmin over the tile's candidates + block
 //                     weight histogram (Algorithm 1 inner loop, localBlockSizes)
 //   balance_kernel    global block weights, balance test, influence update (Eq. 1)
 //   centroid_kernel   weighted coordinate sums and block bounding boxes (Algorithm 2)
-//   finalize_kernel   new centers, movement, average block diameter, erosion (Eq. 2-3),
-//                     convergence test
+//   finalize_a/b      new centers, movement, average block diameter, convergence test,
+//                     erosion (Eq. 2-3)
 //
-// Effective distances are compared squared: dist^2 / influence^2 orders the
-// centers exactly as dist / influence does.
+// Effective distances are compared squared: dist^2 / influence^2 orders the centers
+// exactly as dist / influence does.  The k-sized FP64 work (cbrt, divisions, exp, log)
+// is spread over ceil(k/128) CTAs; the CTA that finishes last takes the global
+// decisions (no grid-wide waiting).  The influence is double-buffered: a pass writes
+// the updated influence into the other buffer and the decision flips the buffer index.
 #include "gk_common.cuh"
 #include "gk_internal.h"
 
 namespace gk {
 
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
+constexpr int kKThreads = 128;                // threads per CTA of the k-sized kernels
+constexpr int kFilterThreads = kSuperTiles * 32;
+constexpr int kAssignWarps = 8;
 
-// Frame coordinates of center c split into an FP32 pair (hi + lo) and g = 1/I^2.
-__device__ __forceinline__ void write_cdata(const Prob &p, int c) {
-    double I = p.I[c];
-    double g = 1.0 / (I * I);
-    p.g64[c] = g;
-    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+__device__ __forceinline__ int exponent_above(double v) {  // smallest e with |v| < 2^e
+    if (v == 0.0) return 0;
+    int e;
+    frexp(fabs(v), &e);
+    return e;
+}
+
+// Frame coordinates of center c (FP64) split into an FP32 pair hi + lo.
+__device__ __forceinline__ void frame_center(const Prob &p, int c, float hi[3], float lo[3]) {
+    for (int j = 0; j < 3; ++j) {
+        hi[j] = 0.f;
+        lo[j] = 0.f;
+    }
     for (int j = 0; j < p.d; ++j) {
         double f = (p.C[c * p.d + j] - p.origin[j]) * p.scale;
         hi[j] = __double2float_rn(f);
         lo[j] = __double2float_rn(f - (double)hi[j]);
     }
-    p.cdata[2 * c] = make_float4(hi[0], hi[1], hi[2], __double2float_rn(g));
-    p.cdata[2 * c + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+}
+
+__device__ __forceinline__ float scaled_g32(double g, int gshift) {
+    return __double2float_rn(ldexp(g, -gshift));
+}
+
+template <typename T>
+__device__ __forceinline__ T block_reduce_max(T v, T *red) {  // all threads get the result
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off; off >>= 1) {
+        T o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o > v ? o : v;
+    }
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    T m = red[0];
+    for (int i = 1; i < nw; ++i) m = red[i] > m ? red[i] : m;
+    return m;
 }
 
 // ------------------------------------------------------------------------------
-// Loop control.
+// Initial state (two kernels over ceil(k/128) CTAs).
 // ------------------------------------------------------------------------------
-__global__ void init_kernel(Prob p, cudaGraphConditionalHandle h_move,
-                            cudaGraphConditionalHandle h_bal) {
+__global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphConditionalHandle h_move,
+                                                           cudaGraphConditionalHandle h_bal) {
     count_launch(p.ctl);
-    for (int c = threadIdx.x; c < p.k; c += blockDim.x) {
-        write_cdata(p, c);
-        p.Iused[c] = p.I[c];
+    __shared__ double red[32];
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double g = 0.0;
+    if (c < p.k) {
+        double I = p.Iin[c];
+        g = 1.0 / (I * I);
+        p.I2[c] = I;
+        p.g64_2[c] = g;
+        float hi[3], lo[3];
+        frame_center(p, c, hi, lo);
+        for (int b = 0; b < 2; ++b) {
+            float4 *cd = p.cdata2 + (size_t)b * 2 * p.k;
+            cd[2 * c] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+            cd[2 * c + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        }
     }
-    if (threadIdx.x == 0) {
+    double m = block_reduce_max(g, red);
+    if (threadIdx.x == 0) atomicMax(&p.ctl->maxg_key, okey_f64(m));
+    if (last_block(p.ctl) && threadIdx.x == 0) {
         Ctl *ctl = p.ctl;
+        double gmax = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
+        ctl->maxg_key = 0ull;
+        ctl->gshift = exponent_above(gmax);
         if (p.weighted)
             ctl->W = i128_to_f64(ctl->wsum_lo, ctl->wsum_hi, p.Fw);
         else
@@ -54,6 +102,8 @@ __global__ void init_kernel(Prob p, cudaGraphConditionalHandle h_move,
         ctl->target = ctl->W / (double)p.k;
         ctl->ceil_avg = ceil(ctl->W / (double)p.k);
         ctl->bound = (1.0 + p.eps) * ctl->ceil_avg;
+        ctl->isel = 0;
+        ctl->iused_sel = 0;
         ctl->balanced = 0;
         ctl->converged = 0;
         ctl->pass_in_phase = 0;
@@ -64,9 +114,18 @@ __global__ void init_kernel(Prob p, cudaGraphConditionalHandle h_move,
         ctl->cont_move = 1;
         ctl->cont_final = 0;
         ctl->max_delta = 0.0;
+        ctl->maxS_key = 0ull;
+        ctl->maxd_key = 0ull;
+        ctl->nonempty = 0;
         if (h_move) cudaGraphSetConditional(h_move, 1u);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
+}
+
+__global__ void __launch_bounds__(kKThreads) init_b_kernel(Prob p) {
+    count_launch(p.ctl);
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < p.k) p.cdata2[2 * c].w = scaled_g32(p.g64_2[c], p.ctl->gshift);
 }
 
 __global__ void final_begin_kernel(Prob p, cudaGraphConditionalHandle h_fin) {
@@ -77,16 +136,24 @@ __global__ void final_begin_kernel(Prob p, cudaGraphConditionalHandle h_fin) {
     if (h_fin) cudaGraphSetConditional(h_fin, (unsigned)cont);
 }
 
+// Influence the last assignment was computed with -> Iin (output staging).
+__global__ void export_kernel(Prob p) {
+    count_launch(p.ctl);
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < p.k) p.Iin[c] = p.I2[(size_t)p.ctl->iused_sel * p.k + c];
+}
+
 // ------------------------------------------------------------------------------
-// Candidate filter (Section 4.4).  One warp per tile; all centers pass through
-// shared memory in chunks brought in by bulk copies.  For the tile's box B and
-// center c (frame coordinates, relative to the tile origin):
+// Candidate filter (Section 4.4).  For a box B (origin o, half extents h) and a
+// center c (frame coordinates, q = c - o):
 //   UB_c = g_c * maxDist(B, c)^2,  LB_c = g_c * minDist(B, c)^2,  tau = min_c UB_c.
-// Every point of B has effective distance <= tau to the best center, so c can
-// only win if LB_c <= tau.  The box is widened by 4 u R and tau by 64 u so that
-// FP32 rounding of points, centers and this arithmetic never drops the FP64
-// winner.  Candidates are written in ascending center order; more than kCap
-// marks the tile for a scan over all centers.
+// Every point of B has effective distance <= tau to its best center, so c can only
+// win if LB_c <= tau.  Boxes are widened by 4 u R and tau by 64 u so that FP32
+// rounding of points, centers and this arithmetic never drops the FP64 winner;
+// comparisons are written so that a NaN keeps the center.  Level 1: the supertile
+// box against all centers (staged in shared memory by bulk copies).  Level 2: each
+// warp takes one tile of the supertile against the level-1 list and writes the
+// tile's coefficient table in ascending center order.
 // ------------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void box_bounds(const float4 &ch, const float4 &cl, const float o[3],
@@ -107,61 +174,69 @@ __device__ __forceinline__ void box_bounds(const float4 &ch, const float4 &cl, c
 }
 
 template <int D>
-__global__ void __launch_bounds__(kFilterWarps * 32) filter_kernel(Prob p) {
+__global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     count_launch(p.ctl);
     __shared__ __align__(128) float4 sc[2 * kCenterChunk];
+    __shared__ int slist[kSuperCap];
+    __shared__ float s_red[kSuperTiles];
+    __shared__ int s_wcnt[kSuperTiles];
     __shared__ __align__(8) unsigned long long bar;
-    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int t = blockIdx.x * kFilterWarps + warp;
-    bool active = t < p.ntiles;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s = blockIdx.x;
+    const int sel = p.ctl->isel;
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float infl = 4.0f * kU * p.R;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
-    float o[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
-    if (active) {
-        float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
-        float infl = 4.0f * kU * p.R;
-        o[0] = a.x;
-        o[1] = a.y;
-        o[2] = a.z;
-        h[0] = __fadd_ru(b.x, infl);
-        h[1] = __fadd_ru(b.y, infl);
-        h[2] = __fadd_ru(b.z, infl);
+    float so[3], sh[3];
+    {
+        float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
+        so[0] = a.x;
+        so[1] = a.y;
+        so[2] = a.z;
+        sh[0] = __fadd_ru(b.x, infl);
+        sh[1] = __fadd_ru(b.y, infl);
+        sh[2] = __fadd_ru(b.z, infl);
     }
     const int nch = (p.k + kCenterChunk - 1) / kCenterChunk;
     unsigned phase = 0;
-    bool failed = false;
     auto stage = [&](int ch) -> bool {
         int cb = ch * kCenterChunk;
         int m = min(kCenterChunk, p.k - cb);
         if (tid == 0) {
             fence_proxy_async();
             mbar_expect_tx(&bar, (unsigned)(m * 32));
-            bulk_g2s(sc, p.cdata + 2 * (long long)cb, (unsigned)(m * 32), &bar);
+            bulk_g2s(sc, cd + 2 * (size_t)cb, (unsigned)(m * 32), &bar);
         }
         bool ok = mbar_wait_bounded(&bar, phase);
         phase ^= 1u;
         return !__syncthreads_or(!ok);
     };
+    bool failed = false;
+    // level 1, sweep 1: tau of the supertile
     float tau = INFINITY;
-    for (int ch = 0; ch < nch && !failed; ++ch) {
+    for (int ch = 0; ch < nch; ++ch) {
         if (!stage(ch)) {
             failed = true;
             break;
         }
         int m = min(kCenterChunk, p.k - ch * kCenterChunk);
-        if (active) {
-            for (int c = lane; c < m; c += 32) {
-                float lb, ub;
-                box_bounds<D>(sc[2 * c], sc[2 * c + 1], o, h, lb, ub);
-                tau = fminf(tau, ub);
-            }
+        for (int c = tid; c < m; c += kFilterThreads) {
+            float lb, ub;
+            box_bounds<D>(sc[2 * c], sc[2 * c + 1], so, sh, lb, ub);
+            tau = fminf(tau, ub);
         }
         __syncthreads();
     }
     for (int off = 16; off; off >>= 1) tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, off));
-    tau = __fmul_ru(tau, 1.0f + 64.0f * kU);
-    int cnt = 0;
-    unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) s_red[warp] = tau;
+    __syncthreads();
+    tau = s_red[0];
+    for (int w = 1; w < kSuperTiles; ++w) tau = fminf(tau, s_red[w]);
+    const float tauS = __fmul_ru(tau, 1.0f + 64.0f * kU);
+    // level 1, sweep 2: ascending list of the supertile's candidates
+    int count = 0;
+    const unsigned lt = (1u << lane) - 1u;
     for (int ch = 0; ch < nch && !failed; ++ch) {
         if (nch > 1 && !stage(ch)) {
             failed = true;
@@ -169,174 +244,346 @@ __global__ void __launch_bounds__(kFilterWarps * 32) filter_kernel(Prob p) {
         }
         int cb = ch * kCenterChunk;
         int m = min(kCenterChunk, p.k - cb);
-        if (active) {
-            for (int base = 0; base < m; base += 32) {
-                int c = base + lane;
-                bool keep = false;
-                if (c < m) {
-                    float lb, ub;
-                    box_bounds<D>(sc[2 * c], sc[2 * c + 1], o, h, lb, ub);
-                    keep = lb <= tau;
-                }
-                unsigned bal = __ballot_sync(0xffffffffu, keep);
-                int pos = cnt + __popc(bal & lt);
-                if (keep && pos < kCap) p.cand_list[(long long)t * kCap + pos] = cb + c;
-                cnt += __popc(bal);
+        for (int base = 0; base < m; base += kFilterThreads) {
+            int c = base + tid;
+            bool keep = false;
+            if (c < m) {
+                float lb, ub;
+                box_bounds<D>(sc[2 * c], sc[2 * c + 1], so, sh, lb, ub);
+                keep = !(lb > tauS);
             }
+            unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < kSuperTiles; ++w) {
+                int v = s_wcnt[w];
+                before += w < warp ? v : 0;
+                total += v;
+            }
+            int pos = count + before + __popc(bal & lt);
+            if (keep && pos < kSuperCap) slist[pos] = cb + c;
+            count += total;
+            __syncthreads();
         }
-        __syncthreads();
     }
+    const int t = s * kSuperTiles + warp;
     if (failed) {
         // A bulk copy did not complete in time: record it, let the assignment scan
         // every center for these tiles, and wait (bounded) for the copy in flight.
         if (tid == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
-        if (active && lane == 0) p.cand_cnt[t] = -1;
+        if (t < p.ntiles && lane == 0) p.tcnt[t] = -1;
         mbar_wait_bounded(&bar, phase ^ 1u);
         return;
     }
-    if (active && lane == 0) {
-        p.cand_cnt[t] = cnt > kCap ? -1 : cnt;
-        if (cnt > kCap) atomicAdd(&p.ctl->overflow_tiles, 1ull);
+    const bool all = count > kSuperCap;
+    const int L = all ? p.k : count;
+    const bool in_smem = nch == 1;
+    if (t >= p.ntiles) return;
+    float o[3], h[3];
+    {
+        float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
+        o[0] = a.x;
+        o[1] = a.y;
+        o[2] = a.z;
+        h[0] = __fadd_ru(b.x, infl);
+        h[1] = __fadd_ru(b.y, infl);
+        h[2] = __fadd_ru(b.z, infl);
+    }
+    auto center = [&](int i, int &c, float4 &ch, float4 &cl) {
+        c = all ? i : slist[i];
+        if (in_smem) {
+            ch = sc[2 * c];
+            cl = sc[2 * c + 1];
+        } else {
+            ch = cd[2 * c];
+            cl = cd[2 * c + 1];
+        }
+    };
+    float tt = INFINITY;
+    for (int i = lane; i < L; i += 32) {
+        int c;
+        float4 ch, cl;
+        center(i, c, ch, cl);
+        float lb, ub;
+        box_bounds<D>(ch, cl, o, h, lb, ub);
+        tt = fminf(tt, ub);
+    }
+    for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
+    const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
+    int cnt = 0;
+    const size_t row = (size_t)t * kCap;
+    for (int base = 0; base < L; base += 32) {
+        int i = base + lane;
+        bool keep = false;
+        int c = 0;
+        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+        if (i < L) {
+            center(i, c, ch, cl);
+            float lb, ub;
+            box_bounds<D>(ch, cl, o, h, lb, ub);
+            keep = !(lb > tauT);
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, keep);
+        int pos = cnt + __popc(bal & lt);
+        if (keep && pos < kCap) {
+            float q0 = (ch.x - o[0]) + cl.x;
+            float q1 = (ch.y - o[1]) + cl.y;
+            float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+            float g = ch.w;
+            float qq = fmaf(q2, q2, fmaf(q1, q1, q0 * q0));
+            p.tcoef[row + pos] = make_float4(-2.0f * g * q0, -2.0f * g * q1, -2.0f * g * q2, g * qq);
+            p.tga[row + pos] = g;
+            p.tcid[row + pos] = c;
+        }
+        cnt += __popc(bal);
+    }
+    if (lane == 0) {
+        bool over = cnt > kCap;
+        p.tcnt[t] = over ? -1 : cnt;
+        if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
+        long long nv = p.n - (long long)t * kTile;
+        nv = nv > kTile ? kTile : nv;
+        unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
+        atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
+    }
+}
+
+// ------------------------------------------------------------------------------
+// Warp segmented reduction of per-lane (id, value) runs whose ids are laid out in
+// lane order; the last lane of each segment adds the segment's sum to acc[2*id].
+// Lanes with id < 0 contribute nothing.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ void seg_flush_u64(int id, unsigned long long v, unsigned long long *acc,
+                                              bool wide) {
+    const int lane = threadIdx.x & 31;
+    int prev = __shfl_up_sync(0xffffffffu, id, 1);
+    bool head = lane == 0 || id != prev;
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane - off >= start) v += y;
+    }
+    bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (end && id >= 0) {
+        if (wide)
+            atomic_add_u128(&acc[2 * id], v);
+        else
+            atomicAdd(&acc[2 * id], v);
     }
 }
 
 // ------------------------------------------------------------------------------
 // Assignment + block-weight histogram (Section 4.2; Algorithm 1 inner loop).
 //
+// One warp per tile of 256 curve-consecutive points; lane l owns points 8l..8l+7.
 // In tile-local frame coordinates x' = x - o the squared effective distance to a
-// candidate with frame center q (relative to o) and g = 1/I^2 is
-//     E = g |x'|^2 - 2 g q.x' + g |q|^2 = fma chain over per-candidate coefficients.
-// FP64 mode: the FP32 winner b is accepted when the FP32 gap to the runner-up
-// exceeds twice a rigorous bound on |E_fp32 - E_exact| (coordinate rounding,
-// coefficient rounding, fma-chain rounding; evaluated with the tile radius and the
-// largest g among the candidates, doubled for safety).  Other points are decided
-// again in FP64 from the raw coordinates over all candidates.  The result is the
-// FP64 argmin up to ties closer than FP64 rounding.
+// candidate with frame center q (relative to o) and g = scaled 1/I^2 is
+//     E = g |x'|^2 - 2 g q.x' + g |q|^2  (a chain of four fma per point; two points
+//     per packed fma.rn.f32x2).
+// FP64 mode: the FP32 winner b is kept when the FP32 gap to the runner-up exceeds
+// twice a rigorous bound B on |E_fp32 - E_exact| (coordinate rounding, coefficient
+// rounding, fma-chain rounding; evaluated with the tile radius and the largest g of
+// the tile's candidates, doubled for safety); a point with a single candidate is
+// decided by the filter alone.  Every other point is decided again in FP64 from the
+// raw coordinates over all of the tile's candidates.  The result is the FP64 argmin
+// up to ties closer than FP64 rounding, ties going to the lowest center index.
 // ------------------------------------------------------------------------------
+template <bool F64MODE>
+__device__ __forceinline__ void argmin_update(float E, int c, float &E1, float &E2, int &best) {
+    if (F64MODE) E2 = fminf(E2, fmaxf(E, E1));
+    bool lt = E < E1;
+    best = lt ? c : best;
+    E1 = lt ? E : E1;
+}
+
 template <int D, bool F64MODE>
-__global__ void __launch_bounds__(kTile) assign_kernel(Prob p) {
+__global__ void __launch_bounds__(kAssignWarps * 32) assign_kernel(Prob p) {
     count_launch(p.ctl);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_assign0 = globaltimer_ns();
-    __shared__ __align__(16) float4 coef[kCap];
-    __shared__ float ga[kCap];
-    __shared__ int cid[kCap];
-    __shared__ float s_gmax[kTile / 32];
-    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int t = blockIdx.x;
-    long long i = (long long)t * kTile + tid;
-    bool valid = i < p.n;
-    float4 ob = p.tiles[2 * t];
-    float o[3] = {ob.x, ob.y, ob.z};
-    int cnt = p.cand_cnt[t];
-    bool all = cnt < 0;
-    int ncand = all ? p.k : cnt;
-    float xp[3] = {0.f, 0.f, 0.f};
+    __shared__ __align__(16) float4 s_coef[kAssignWarps][kCap];
+    __shared__ float s_ga[kAssignWarps][kCap];
+    __shared__ int s_cid[kAssignWarps][kCap];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * kAssignWarps + w;
+    if (t >= p.ntiles) return;
+    const int sel = p.ctl->isel;
+    const float4 ob = p.tiles[2 * t];
+    const float o[3] = {ob.x, ob.y, ob.z};
+    const int cnt = p.tcnt[t];
+    const bool all = cnt < 0;
+    const long long i0 = (long long)t * kTile + lane * 8;
+    long long nv = p.n - i0;
+    const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+
+    // 8 consecutive points per lane (n_pad is a multiple of kTile: loads stay in bounds)
+    float2 xp[3][4];
 #pragma unroll
-    for (int j = 0; j < D; ++j) xp[j] = valid ? (p.X32[j * p.n_pad + i] - o[j]) : 0.0f;
-    float xx = 0.f;
+    for (int j = 0; j < D; ++j) {
+        const float4 *src = reinterpret_cast<const float4 *>(p.X32 + (size_t)j * p.n_pad + i0);
+        float4 a = src[0], b = src[1];
+        xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
+        xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
+        xp[j][2] = make_float2(b.x - o[j], b.y - o[j]);
+        xp[j][3] = make_float2(b.z - o[j], b.w - o[j]);
+    }
+    float2 xx[4];
 #pragma unroll
-    for (int j = 0; j < D; ++j) xx = fmaf(xp[j], xp[j], xx);
-    float E1 = INFINITY, E2 = INFINITY;
-    int best = 0;
-    float gl = 0.f;
-    for (int base = 0; base < ncand; base += kCap) {
-        int m = min(kCap, ncand - base);
-        __syncthreads();
-        if (tid < m) {
-            int c = all ? base + tid : p.cand_list[(long long)t * kCap + base + tid];
-            float4 ch = p.cdata[2 * c], cl = p.cdata[2 * c + 1];
-            float q0 = (ch.x - o[0]) + cl.x;
-            float q1 = (ch.y - o[1]) + cl.y;
-            float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-            float g = ch.w;
-            float qq = fmaf(q2, q2, fmaf(q1, q1, q0 * q0));
-            coef[tid] = make_float4(-2.0f * g * q0, -2.0f * g * q1, -2.0f * g * q2, g * qq);
-            ga[tid] = g;
-            cid[tid] = c;
+    for (int q = 0; q < 4; ++q) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
+        xx[q] = acc;
+    }
+    float E1[8], E2[8];
+    int best[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        E1[q] = INFINITY;
+        E2[q] = INFINITY;
+        best[q] = 0;
+    }
+    float gl = 0.0f;
+    auto consume = [&](int m) {
+        for (int jj = 0; jj < m; ++jj) {
+            const float4 cf = s_coef[w][jj];
+            const float a = s_ga[w][jj];
+            const int c = s_cid[w][jj];
+            const float2 a2 = make_float2(a, a), bx = make_float2(cf.x, cf.x),
+                         by = make_float2(cf.y, cf.y), bz = make_float2(cf.z, cf.z),
+                         e2 = make_float2(cf.w, cf.w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 acc = e2;
+                if (D == 3) acc = __ffma2_rn(bz, xp[2][q], acc);
+                acc = __ffma2_rn(by, xp[1][q], acc);
+                acc = __ffma2_rn(bx, xp[0][q], acc);
+                acc = __ffma2_rn(a2, xx[q], acc);
+                argmin_update<F64MODE>(acc.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
+                argmin_update<F64MODE>(acc.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
+            }
+        }
+    };
+    if (!all) {
+        const size_t row = (size_t)t * kCap;
+        for (int j = lane; j < cnt; j += 32) {
+            s_coef[w][j] = p.tcoef[row + j];
+            float g = p.tga[row + j];
+            s_ga[w][j] = g;
+            s_cid[w][j] = p.tcid[row + j];
             gl = fmaxf(gl, g);
         }
-        __syncthreads();
-#pragma unroll 4
-        for (int jj = 0; jj < m; ++jj) {
-            float4 cf = coef[jj];
-            float acc = D == 3 ? fmaf(cf.z, xp[2], cf.w) : cf.w;
-            acc = fmaf(cf.y, xp[1], acc);
-            acc = fmaf(cf.x, xp[0], acc);
-            float E = fmaf(ga[jj], xx, acc);
-            if (E < E1) {
-                if (F64MODE) E2 = E1;
-                E1 = E;
-                best = cid[jj];
-            } else if (F64MODE) {
-                E2 = fminf(E2, E);
+        __syncwarp();
+        consume(cnt);
+    } else {
+        const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+        for (int base = 0; base < p.k; base += 32) {
+            int m = min(32, p.k - base);
+            __syncwarp();
+            if (lane < m) {
+                int c = base + lane;
+                float4 ch = cd[2 * c], cl = cd[2 * c + 1];
+                float q0 = (ch.x - o[0]) + cl.x;
+                float q1 = (ch.y - o[1]) + cl.y;
+                float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+                float g = ch.w;
+                float qq = fmaf(q2, q2, fmaf(q1, q1, q0 * q0));
+                s_coef[w][lane] = make_float4(-2.0f * g * q0, -2.0f * g * q1, -2.0f * g * q2, g * qq);
+                s_ga[w][lane] = g;
+                s_cid[w][lane] = c;
+                gl = fmaxf(gl, g);
             }
+            __syncwarp();
+            consume(m);
         }
     }
     if (F64MODE) {
         for (int off = 16; off; off >>= 1) gl = fmaxf(gl, __shfl_xor_sync(0xffffffffu, gl, off));
-        if (lane == 0) s_gmax[warp] = gl;
-        __syncthreads();
-        float gmax = s_gmax[0];
-        for (int w = 1; w < kTile / 32; ++w) gmax = fmaxf(gmax, s_gmax[w]);
-        // error bound B(E) = beta0 + beta1 sqrt(E) + beta2 E (see comment above)
-        float R = p.R;
-        float rp = ob.w + 2.0f * 1.7320508f * kU * R;
-        float ex = sqrtf((float)D) * kU * (R + rp);
-        float sg = sqrtf(gmax);
-        float c2 = (2.0f * D + 10.0f) * kU;
-        float beta2 = c2;
-        float beta1 = c2 * 4.0f * sg * rp + 2.0f * sg * ex;
-        float beta0 = c2 * 4.0f * gmax * rp * rp + gmax * ex * ex;
-        float Estar = 2.0f * E2 + 2.0f * (beta0 + 2.0f * beta1 * beta1);
-        float B = 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
-        bool recheck = valid && !((E2 - E1) > 2.0f * B);  // E2 = inf -> certified
-        if (recheck) {
-            double x64[3];
-            for (int j = 0; j < D; ++j)
-                x64[j] = p.dtype == 1 ? p.X64[j * p.n_pad + i] : (double)p.X32[j * p.n_pad + i];
-            double bestE = INFINITY;
-            int b = 0;
-            for (int jj = 0; jj < ncand; ++jj) {
-                int c = all ? jj : p.cand_list[(long long)t * kCap + jj];
-                double s = 0.0;
-                for (int j = 0; j < D; ++j) {
-                    double df = x64[j] - p.C[c * D + j];
-                    s += df * df;
+        // error bound B(E) = beta0 + beta1 sqrt(E) + beta2 E (see the comment above)
+        const float R = p.R;
+        const float rp = ob.w + 2.0f * 1.7320508f * kU * R;
+        const float ex = sqrtf((float)D) * kU * (R + rp);
+        const float sg = sqrtf(gl);
+        const float c2 = (2.0f * D + 10.0f) * kU;
+        const float beta2 = c2;
+        const float beta1 = c2 * 4.0f * sg * rp + 2.0f * sg * ex;
+        const float beta0 = c2 * 4.0f * gl * rp * rp + gl * ex * ex;
+        unsigned flag = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float Estar = 2.0f * E2[q] + 2.0f * (beta0 + 2.0f * beta1 * beta1);
+            float B = 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
+            bool single = E2[q] == INFINITY && E1[q] < INFINITY;
+            bool ok = single || (E2[q] - E1[q]) > 2.0f * B;
+            if (q < nval && !ok) flag |= 1u << q;
+        }
+        if (flag) {
+            const double *g64 = p.g64_2 + (size_t)sel * p.k;
+            const int ncand = all ? p.k : cnt;
+            for (int q = 0; q < 8; ++q) {
+                if (!((flag >> q) & 1u)) continue;
+                double x64[3] = {0.0, 0.0, 0.0};
+                for (int j = 0; j < D; ++j)
+                    x64[j] = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + i0 + q]
+                                          : (double)p.X32[(size_t)j * p.n_pad + i0 + q];
+                double bestE = INFINITY;
+                int b = 0;
+                for (int jj = 0; jj < ncand; ++jj) {
+                    int c = all ? jj : s_cid[w][jj];
+                    double s2 = 0.0;
+                    for (int j = 0; j < D; ++j) {
+                        double df = x64[j] - p.C[c * D + j];
+                        s2 += df * df;
+                    }
+                    double E = s2 * g64[c];
+                    if (E < bestE) {
+                        bestE = E;
+                        b = c;
+                    }
                 }
-                double E = s * p.g64[c];
-                if (E < bestE) {
-                    bestE = E;
-                    b = c;
-                }
+                best[q] = b;
             }
-            best = b;
         }
-        int nre = __syncthreads_count(recheck);
-        if (tid == 0 && nre) atomicAdd(&p.ctl->rechecks, (unsigned long long)nre);
+        unsigned nre = __popc(flag);
+        for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
+        if (lane == 0 && nre) atomicAdd(&p.ctl->rechecks, (unsigned long long)nre);
     }
-    if (valid) p.A[i] = best;
-    // block weights: warp aggregation, then one atomic per distinct block and warp
-    if (!p.weighted) {
-        int key = valid ? best : -1;
-        unsigned peers = __match_any_sync(0xffffffffu, key);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0u)
-            atomicAdd(&p.Sfix[2 * best], (unsigned long long)__popc(peers));
+    // block ids
+    if (nval == 8) {
+        int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+        dst[0] = make_int4(best[0], best[1], best[2], best[3]);
+        dst[1] = make_int4(best[4], best[5], best[6], best[7]);
     } else {
-        unsigned long long v = 0;
-        if (valid)
-            v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i], p.Fw)
-                                                  : fix_f32(((const float *)p.Ws)[i], p.Fw));
-        int b0 = __shfl_sync(0xffffffffu, valid ? best : -1, 0);
-        bool uniform = __all_sync(0xffffffffu, valid && best == b0);
-        if (uniform) {
-            for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) atomic_add_u128(&p.Sfix[2 * b0], v);
-        } else if (valid) {
-            atomic_add_u128(&p.Sfix[2 * best], v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nval) p.A[i0 + q] = best[q];
+    }
+    // block weights: runs inside the lane, then a segmented reduction over lanes
+    int cur = -1;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q < nval) {
+            unsigned long long v = 1ull;
+            if (p.weighted)
+                v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
+                                                      : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
+            if (best[q] != cur) {
+                if (cur >= 0) {
+                    if (p.weighted)
+                        atomic_add_u128(&p.Sfix[2 * cur], acc);
+                    else
+                        atomicAdd(&p.Sfix[2 * cur], acc);
+                }
+                cur = best[q];
+                acc = 0;
+            }
+            acc += v;
         }
     }
-    int nvalid = __syncthreads_count(valid);
-    if (tid == 0) atomicAdd(&p.ctl->cand_sum, (unsigned long long)ncand * (unsigned long long)nvalid);
+    seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
 }
 
 // ------------------------------------------------------------------------------
@@ -357,72 +604,76 @@ __global__ void block_weights_kernel(Prob p) {
 
 // ------------------------------------------------------------------------------
 // Balance test and influence update (Section 2 bound; Section 4.2 Eq. 1 as read:
-// I_c <- I_c * clamp((W/k / S_c)^(1/d), 0.95, 1.05)).  mode 0: main loop, 1: final
-// passes with centers fixed, 2: block weights only (standalone assignment).
-// One CTA.
+// I_c <- I_c * clamp((W/k / S_c)^(1/d), 0.95, 1.05)).  Every CTA converts its block
+// weights, resets the accumulators and writes the tentatively updated influence into
+// the other buffer; the last CTA takes the decision: balanced keeps the buffer,
+// unbalanced flips it.  mode 0: main loop, 1: final passes with the centers fixed,
+// 2: block weights only (standalone assignment).
 // ------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) balance_kernel(Prob p, int mode,
-                                                       cudaGraphConditionalHandle h) {
+__global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
+                                                            cudaGraphConditionalHandle h) {
     count_launch(p.ctl);
     __shared__ double red[32];
-    __shared__ int s_bal;
     Ctl *ctl = p.ctl;
-    int tid = threadIdx.x;
-    if (tid == 0) {  // the assignment kernel ran just before on this stream
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the assignment kernel ran just before
         ctl->assign_ns += globaltimer_ns() - ctl->t_assign0;
         ctl->assign_cnt += 1;
     }
-    double mx = 0.0;
-    for (int c = tid; c < p.k; c += blockDim.x) {
+    const int sel = ctl->isel, nsel = sel ^ 1;
+    const int gshift = ctl->gshift;
+    const double target = ctl->target;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double S = 0.0, gnew = 0.0;
+    if (c < p.k) {
         unsigned long long lo = p.Sfix[2 * c], hi = p.Sfix[2 * c + 1];
-        double S = p.weighted ? i128_to_f64(lo, hi, p.Fw) : (double)lo;
+        S = p.weighted ? i128_to_f64(lo, hi, p.Fw) : (double)lo;
         p.S64[c] = S;
         p.Sfix[2 * c] = 0ull;
         p.Sfix[2 * c + 1] = 0ull;
-        mx = fmax(mx, S);
-    }
-    for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((tid & 31) == 0) red[tid >> 5] = mx;
-    __syncthreads();
-    if (tid == 0) {
-        double m = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-        int bal = m <= ctl->bound;
-        s_bal = bal;
-        ctl->max_imbalance = m / ctl->ceil_avg - 1.0;
         if (mode != 2) {
-            ctl->balanced = bal;
-            ctl->passes += 1;
-            if (mode == 0)
-                ctl->pass_in_phase += 1;
-            else
-                ctl->final_passes += 1;
-        }
-    }
-    __syncthreads();
-    if (mode == 2) return;
-    int bal = s_bal;
-    for (int c = tid; c < p.k; c += blockDim.x) {
-        double I = p.I[c];
-        p.Iused[c] = I;
-        if (!bal) {
-            double S = p.S64[c];
+            double I = p.I2[(size_t)sel * p.k + c];
             double f;
             if (S > 0.0) {
-                double gamma = ctl->target / S;
+                double gamma = target / S;
                 f = p.d == 2 ? sqrt(gamma) : cbrt(gamma);
             } else {
                 f = INFINITY;
             }
             f = fmin(fmax(f, 0.95), 1.05);
-            I = I * f;
-            p.I[c] = I;
-            double g = 1.0 / (I * I);
-            p.g64[c] = g;
-            p.cdata[2 * c].w = __double2float_rn(g);
+            double In = I * f;
+            gnew = 1.0 / (In * In);
+            p.I2[(size_t)nsel * p.k + c] = In;
+            p.g64_2[(size_t)nsel * p.k + c] = gnew;
+            float4 hc = p.cdata2[(size_t)sel * 2 * p.k + 2 * c];
+            hc.w = scaled_g32(gnew, gshift);
+            p.cdata2[(size_t)nsel * 2 * p.k + 2 * c] = hc;
         }
     }
-    if (tid == 0) {
+    double mS = block_reduce_max(S, red);
+    double mg = block_reduce_max(gnew, red);
+    if (threadIdx.x == 0) {
+        atomicMax(&ctl->maxS_key, okey_f64(mS));
+        if (mode != 2) atomicMax(&ctl->maxg_key, okey_f64(mg));
+    }
+    if (last_block(ctl) && threadIdx.x == 0) {
+        double maxS = okey_to_f64(atomicOr(&ctl->maxS_key, 0ull));
+        double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
+        ctl->maxS_key = 0ull;
+        ctl->maxg_key = 0ull;
+        int bal = maxS <= ctl->bound;
+        ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
+        if (mode == 2) return;
+        ctl->balanced = bal;
+        ctl->passes += 1;
+        ctl->iused_sel = sel;
+        if (mode == 0)
+            ctl->pass_in_phase += 1;
+        else
+            ctl->final_passes += 1;
+        if (!bal) {
+            ctl->isel = nsel;
+            ctl->gshift = exponent_above(maxg);
+        }
         int cont;
         if (mode == 0)
             cont = !bal && ctl->pass_in_phase < p.max_balance_iter;
@@ -438,114 +689,154 @@ __global__ void __launch_bounds__(1024) balance_kernel(Prob p, int mode,
 }
 
 // ------------------------------------------------------------------------------
-// Center movement, part 1: 128-bit fixed-point sums of w*x per block and axis and
-// the block bounding boxes (ordered-key min/max).  Exact and order-independent.
+// Center movement, part 1: exact 128-bit fixed-point sums of w*x per block and axis
+// and the block bounding boxes (ordered keys, input precision).  One warp per 256
+// curve-consecutive points; runs inside a lane, then a segmented reduction over lanes.
 // ------------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(256) centroid_kernel(Prob p) {
+template <typename T>
+struct KeyOf;
+template <>
+struct KeyOf<float> {
+    __device__ static unsigned long long key(float v) { return okey_f32(v); }
+};
+template <>
+struct KeyOf<double> {
+    __device__ static unsigned long long key(double v) { return okey_f64(v); }
+};
+
+template <typename T, int D>
+__global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     count_launch(p.ctl);
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int lane = threadIdx.x & 31;
-    int b = i < p.n ? p.A[i] : -1;
-    bool valid = i < p.n && (unsigned)b < (unsigned)p.k;
-    if (!valid) b = -1;
-    long long v[D];
-    unsigned long long kl[D], kh[D];
-    double w = 1.0;
-    if (valid && p.weighted)
-        w = p.dtype == 1 ? ((const double *)p.Ws)[i] : (double)((const float *)p.Ws)[i];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = blockIdx.x * kAssignWarps + w;
+    if (t >= p.ntiles) return;
+    const long long i0 = (long long)t * kTile + lane * 8;
+    long long nv = p.n - i0;
+    const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
+    int cur = -1;
+    long long sum[D];
+    unsigned long long kmin[D], kmax[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        double x = 0.0;
-        long long fv = 0;
-        if (valid) {
-            if (p.dtype == 1) {
-                x = p.X64[j * p.n_pad + i];
-                fv = p.weighted ? fix_f64(w * x, p.Fx) : fix_f64(x, p.Fx);
-            } else {
-                float xf = p.X32[j * p.n_pad + i];
-                x = (double)xf;
-                fv = p.weighted ? fix_f64(w * x, p.Fx) : fix_f32(xf, p.Fx);
-            }
-        }
-        v[j] = fv;
-        kl[j] = valid ? okey_f64(x) : ~0ull;
-        kh[j] = valid ? okey_f64(x) : 0ull;
+        sum[j] = 0;
+        kmin[j] = ~0ull;
+        kmax[j] = 0ull;
     }
-    int b0 = __shfl_sync(0xffffffffu, b, 0);
-    bool uniform = __all_sync(0xffffffffu, valid && b == b0);
-    if (uniform) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            for (int off = 16; off; off >>= 1) {
-                v[j] += (long long)__shfl_xor_sync(0xffffffffu, (unsigned long long)v[j], off);
-                unsigned long long a = __shfl_xor_sync(0xffffffffu, kl[j], off);
-                unsigned long long c = __shfl_xor_sync(0xffffffffu, kh[j], off);
-                kl[j] = a < kl[j] ? a : kl[j];
-                kh[j] = c > kh[j] ? c : kh[j];
-            }
+    int bad = 0;
+    for (int q = 0; q < nval; ++q) {
+        int b = p.A[i0 + q];
+        if ((unsigned)b >= (unsigned)p.k) {
+            bad = 1;
+            continue;
         }
-        if (lane == 0) {
+        if (b != cur) {
+            if (cur >= 0) {
+                for (int j = 0; j < D; ++j) {
+                    atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
+                    atomicMin(&p.BBlo[cur * D + j], kmin[j]);
+                    atomicMax(&p.BBhi[cur * D + j], kmax[j]);
+                }
+            }
+            cur = b;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                atomic_add_i128(&p.SXfix[2 * (b0 * D + j)], v[j]);
-                atomicMin(&p.BBlo[b0 * D + j], kl[j]);
-                atomicMax(&p.BBhi[b0 * D + j], kh[j]);
+                sum[j] = 0;
+                kmin[j] = ~0ull;
+                kmax[j] = 0ull;
             }
         }
-    } else if (valid) {
+        T wv = p.weighted ? ((const T *)p.Ws)[i0 + q] : (T)1;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            atomic_add_i128(&p.SXfix[2 * (b * D + j)], v[j]);
-            atomicMin(&p.BBlo[b * D + j], kl[j]);
-            atomicMax(&p.BBhi[b * D + j], kh[j]);
+            T x = X[(size_t)j * p.n_pad + i0 + q];
+            long long v;
+            if (sizeof(T) == 8)
+                v = p.weighted ? fix_f64((double)wv * (double)x, p.Fx) : fix_f64((double)x, p.Fx);
+            else
+                v = p.weighted ? fix_prod_f32((float)wv, (float)x, p.Fx) : fix_f32((float)x, p.Fx);
+            sum[j] += v;
+            unsigned long long kk = KeyOf<T>::key(x);
+            kmin[j] = kk < kmin[j] ? kk : kmin[j];
+            kmax[j] = kk > kmax[j] ? kk : kmax[j];
+        }
+    }
+    if (bad) atomicOr(&p.ctl->bad_block, 1);
+    // segmented reduction of the lanes' last runs
+    int prev = __shfl_up_sync(0xffffffffu, cur, 1);
+    bool head = lane == 0 || cur != prev;
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        bool take = lane - off >= start;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            long long s2 = __shfl_up_sync(0xffffffffu, sum[j], off);
+            unsigned long long a = __shfl_up_sync(0xffffffffu, kmin[j], off);
+            unsigned long long b = __shfl_up_sync(0xffffffffu, kmax[j], off);
+            if (take) {
+                sum[j] += s2;
+                kmin[j] = a < kmin[j] ? a : kmin[j];
+                kmax[j] = b > kmax[j] ? b : kmax[j];
+            }
+        }
+    }
+    bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (end && cur >= 0) {
+        for (int j = 0; j < D; ++j) {
+            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
+            atomicMin(&p.BBlo[cur * D + j], kmin[j]);
+            atomicMax(&p.BBhi[cur * D + j], kmax[j]);
         }
     }
 }
 
 // ------------------------------------------------------------------------------
-// Center movement, part 2 (one CTA): C' = sum(w x) / sum(w) (empty block: C' = C),
-// delta_c = |C'_c - C_c|, beta = mean diagonal of the non-empty blocks' boxes,
-// convergence test, and -- when the loop continues -- C <- C' and the erosion
-// I <- exp((1 - alpha) log I), alpha = 2 / (1 + exp(min(-delta/beta, 0))) - 1
-// (Eq. 2-3).  mode 0: inside the loop; 1: standalone (outputs only).
+// Center movement, part 2 (ceil(k/128) CTAs): C' = sum(w x) / sum(w) (empty block:
+// C' = C), delta_c = |C'_c - C_c|, and per-CTA partial sums of the block diagonals;
+// the last CTA forms beta (the mean diagonal of the non-empty blocks, summed in CTA
+// order), the convergence test and the loop decision.  mode 1: standalone.
 // ------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) finalize_kernel(Prob p, int mode,
-                                                        cudaGraphConditionalHandle h_move,
-                                                        cudaGraphConditionalHandle h_bal) {
+__device__ __forceinline__ double bb_value(const Prob &p, unsigned long long key) {
+    return p.dtype == 1 ? okey_to_f64(key) : (double)okey_to_f32((unsigned)key);
+}
+
+__global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
+                                                               cudaGraphConditionalHandle h_move,
+                                                               cudaGraphConditionalHandle h_bal) {
     count_launch(p.ctl);
-    __shared__ double r_max[32], r_sum[32];
+    __shared__ double r_sum[32];
+    __shared__ double red[32];
     __shared__ int r_cnt[32];
-    __shared__ int s_move;
-    __shared__ double s_beta;
     Ctl *ctl = p.ctl;
-    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double mx = 0.0, sdiag = 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int c = blockIdx.x * blockDim.x + tid;
+    double dl = 0.0, sdiag = 0.0;
     int cnt = 0;
-    for (int c = tid; c < p.k; c += blockDim.x) {
+    if (c < p.k) {
         double S = p.S64[c];
         double dd = 0.0;
         if (S > 0.0) {
             double diag = 0.0;
             for (int j = 0; j < p.d; ++j) {
-                long long q = 2ll * (c * p.d + j);
+                size_t q = 2 * ((size_t)c * p.d + j);
                 double cm = i128_to_f64(p.SXfix[q], p.SXfix[q + 1], p.Fx) / S;
                 double m = cm - p.C[c * p.d + j];
                 dd += m * m;
                 p.Cm[c * p.d + j] = cm;
-                double e = okey_to_f64(p.BBhi[c * p.d + j]) - okey_to_f64(p.BBlo[c * p.d + j]);
+                double e = bb_value(p, p.BBhi[c * p.d + j]) - bb_value(p, p.BBlo[c * p.d + j]);
                 diag += e * e;
             }
-            sdiag += sqrt(diag);
-            cnt += 1;
+            sdiag = sqrt(diag);
+            cnt = 1;
         } else {
             for (int j = 0; j < p.d; ++j) p.Cm[c * p.d + j] = p.C[c * p.d + j];
         }
-        double dl = sqrt(dd);
+        dl = sqrt(dd);
         p.delta[c] = dl;
-        mx = fmax(mx, dl);
         for (int j = 0; j < p.d; ++j) {
-            long long q = 2ll * (c * p.d + j);
+            size_t q = 2 * ((size_t)c * p.d + j);
             p.SXfix[q] = 0ull;
             p.SXfix[q + 1] = 0ull;
             p.BBlo[c * p.d + j] = ~0ull;
@@ -553,87 +844,87 @@ __global__ void __launch_bounds__(1024) finalize_kernel(Prob p, int mode,
         }
     }
     for (int off = 16; off; off >>= 1) {
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
         sdiag += __shfl_xor_sync(0xffffffffu, sdiag, off);
         cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
     }
     if (lane == 0) {
-        r_max[warp] = mx;
         r_sum[warp] = sdiag;
         r_cnt[warp] = cnt;
     }
-    __syncthreads();
+    double mx = block_reduce_max(dl, red);
     if (tid == 0) {
-        double m = r_max[0], s = r_sum[0];
-        int n = r_cnt[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            m = fmax(m, r_max[w]);
+        double s = 0.0;
+        int n = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             s += r_sum[w];
             n += r_cnt[w];
         }
-        double beta = n > 0 ? s / (double)n : 0.0;
-        s_beta = beta;
-        ctl->beta = beta;
+        p.part[blockIdx.x] = s;
+        if (n) atomicAdd(&ctl->nonempty, n);
+        atomicMax(&ctl->maxd_key, okey_f64(mx));
+    }
+    if (last_block(ctl) && tid == 0) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&p.part[b]);
+        int n = atomicAdd(&ctl->nonempty, 0);
+        double m = okey_to_f64(atomicOr(&ctl->maxd_key, 0ull));
+        ctl->nonempty = 0;
+        ctl->maxd_key = 0ull;
+        ctl->beta = n > 0 ? s / (double)n : 0.0;
         ctl->max_delta = m;
-        int move = 0;
-        if (mode == 0) {
-            ctl->iter += 1;
-            int conv = m < ctl->thr;
-            ctl->converged = conv;
-            move = !conv && ctl->iter < p.max_iter && ctl->status == kOk;
-        }
-        s_move = move;
-    }
-    __syncthreads();
-    if (mode != 0) return;
-    if (s_move) {
-        double beta = s_beta;
-        for (int c = tid; c < p.k; c += blockDim.x) {
-            for (int j = 0; j < p.d; ++j) p.C[c * p.d + j] = p.Cm[c * p.d + j];
-            if (p.erosion) {
-                double dl = p.delta[c];
-                double alpha;
-                if (beta > 0.0) {
-                    double tt = fmin(-dl / beta, 0.0);
-                    alpha = 2.0 / (1.0 + exp(tt)) - 1.0;
-                } else {
-                    alpha = dl > 0.0 ? 1.0 : 0.0;
-                }
-                p.I[c] = exp((1.0 - alpha) * log(p.I[c]));
-            }
-            write_cdata(p, c);
-        }
-    }
-    if (tid == 0) {
-        ctl->cont_move = s_move;
+        if (mode != 0) return;
+        ctl->iter += 1;
+        int conv = m < ctl->thr;
+        ctl->converged = conv;
+        int move = !conv && ctl->iter < p.max_iter && ctl->status == kOk;
+        ctl->cont_move = move;
         ctl->pass_in_phase = 0;
         ctl->cont_balance = 1;
-        if (h_move) cudaGraphSetConditional(h_move, (unsigned)s_move);
+        if (h_move) cudaGraphSetConditional(h_move, (unsigned)move);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
 }
 
-// Copies C and I into the workspace state and prepares the center data (standalone
-// assignment / movement steps).
-__global__ void load_state_kernel(Prob p) {
+// Center movement, part 3: when the loop continues, C <- C' and the erosion
+// I <- exp((1 - alpha) log I), alpha = 2 / (1 + exp(min(-delta/beta, 0))) - 1 (Eq. 2-3).
+__global__ void __launch_bounds__(kKThreads) finalize_b_kernel(Prob p) {
     count_launch(p.ctl);
-    for (int c = threadIdx.x; c < p.k; c += blockDim.x) {
-        write_cdata(p, c);
-        p.Iused[c] = p.I[c];
+    const Ctl *ctl = p.ctl;
+    if (!ctl->cont_move) return;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.k) return;
+    const int sel = ctl->isel;
+    const double beta = ctl->beta;
+    for (int j = 0; j < p.d; ++j) p.C[c * p.d + j] = p.Cm[c * p.d + j];
+    double *Ip = p.I2 + (size_t)sel * p.k;
+    double I = Ip[c];
+    if (p.erosion) {
+        double dl = p.delta[c];
+        double alpha;
+        if (beta > 0.0) {
+            double tt = fmin(-dl / beta, 0.0);
+            alpha = 2.0 / (1.0 + exp(tt)) - 1.0;
+        } else {
+            alpha = dl > 0.0 ? 1.0 : 0.0;
+        }
+        I = exp((1.0 - alpha) * log(I));
+        Ip[c] = I;
+    }
+    double g = 1.0 / (I * I);
+    p.g64_2[(size_t)sel * p.k + c] = g;
+    float hi[3], lo[3];
+    frame_center(p, c, hi, lo);
+    for (int b = 0; b < 2; ++b) {
+        float4 *cd = p.cdata2 + (size_t)b * 2 * p.k;
+        cd[2 * c] = make_float4(hi[0], hi[1], hi[2], b == sel ? scaled_g32(g, ctl->gshift) : 0.0f);
+        cd[2 * c + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     }
 }
 
 // ------------------------------------------------------------------------------
 // Host launchers.
 // ------------------------------------------------------------------------------
-cudaError_t launch_init(const Prob &p, cudaStream_t s) {
-    init_kernel<<<1, 1024, 0, s>>>(p, 0, 0);
-    return cudaGetLastError();
-}
-cudaError_t launch_load_state(const Prob &p, cudaStream_t s) {
-    load_state_kernel<<<1, 1024, 0, s>>>(p);
-    return cudaGetLastError();
-}
+static int kgrid(const Prob &p) { return (p.k + kKThreads - 1) / kKThreads; }
 
 static void *filter_fn(int d) {
     return d == 2 ? (void *)filter_kernel<2> : (void *)filter_kernel<3>;
@@ -642,21 +933,30 @@ static void *assign_fn(int d, int f64) {
     if (d == 2) return f64 ? (void *)assign_kernel<2, true> : (void *)assign_kernel<2, false>;
     return f64 ? (void *)assign_kernel<3, true> : (void *)assign_kernel<3, false>;
 }
-static void *centroid_fn(int d) {
-    return d == 2 ? (void *)centroid_kernel<2> : (void *)centroid_kernel<3>;
+static void *centroid_fn(int d, int dtype) {
+    if (dtype == 1) return d == 2 ? (void *)centroid_kernel<double, 2> : (void *)centroid_kernel<double, 3>;
+    return d == 2 ? (void *)centroid_kernel<float, 2> : (void *)centroid_kernel<float, 3>;
 }
+static int tile_warp_grid(const Prob &p) { return (p.ntiles + kAssignWarps - 1) / kAssignWarps; }
+
+cudaError_t launch_init(const Prob &p, cudaStream_t s) {
+    init_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, 0, 0);
+    init_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+cudaError_t launch_load_state(const Prob &p, cudaStream_t s) { return launch_init(p, s); }
 
 cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    int fgrid = (p.ntiles + kFilterWarps - 1) / kFilterWarps;
-    return cudaLaunchKernel(filter_fn(p.d), dim3(fgrid), dim3(kFilterWarps * 32), args1, 0, s);
+    return cudaLaunchKernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), args1, 0, s);
 }
 cudaError_t launch_assign(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    return cudaLaunchKernel(assign_fn(p.d, p.assign_f64), dim3(p.ntiles), dim3(kTile), args1, 0, s);
+    return cudaLaunchKernel(assign_fn(p.d, p.assign_f64), dim3(tile_warp_grid(p)),
+                            dim3(kAssignWarps * 32), args1, 0, s);
 }
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s) {
-    balance_kernel<<<1, 1024, 0, s>>>(p, mode, 0);
+    balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0);
     return cudaGetLastError();
 }
 cudaError_t launch_pass(const Prob &p, int mode, cudaStream_t s) {
@@ -670,16 +970,17 @@ cudaError_t launch_block_weights(const Prob &p, cudaStream_t s) {
     block_weights_kernel<<<(int)((p.n + 255) / 256), 256, 0, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    balance_kernel<<<1, 1024, 0, s>>>(p, 2, 0);
+    balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, 2, 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    cudaError_t e = cudaLaunchKernel(centroid_fn(p.d), dim3((unsigned)((p.n + 255) / 256)),
-                                     dim3(256), args1, 0, s);
+    cudaError_t e = cudaLaunchKernel(centroid_fn(p.d, p.dtype), dim3(tile_warp_grid(p)),
+                                     dim3(kAssignWarps * 32), args1, 0, s);
     if (e != cudaSuccess) return e;
-    finalize_kernel<<<1, 1024, 0, s>>>(p, mode, 0, 0);
+    finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
+    if (mode == 0) finalize_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -688,11 +989,16 @@ cudaError_t launch_final_begin(const Prob &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_export(const Prob &p, cudaStream_t s) {
+    export_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------
 // The whole loop as one CUDA graph:
-//   init -> while(h_move){ while(h_bal){ filter -> assign -> balance(0) } ->
-//           centroid -> finalize } -> final_begin -> while(h_fin){ filter -> assign ->
-//           balance(1) }
+//   init_a -> init_b -> while(h_move){ while(h_bal){ filter -> assign -> balance(0) }
+//   -> centroid -> finalize_a -> finalize_b } -> final_begin -> while(h_fin){ filter ->
+//   assign -> balance(1) }
 // ------------------------------------------------------------------------------
 namespace {
 struct NodeAdder {
@@ -740,7 +1046,6 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
         cudaGraphDestroy(g);
         return e;
     }
-    int fgrid = (p.ntiles + kFilterWarps - 1) / kFilterWarps;
     int mode0 = 0, mode1 = 1;
     void *a_init[] = {&p, &h_move, &h_bal};
     void *a_p[] = {&p};
@@ -748,31 +1053,34 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     void *a_bal1[] = {&p, &mode1, &h_fin};
     void *a_fin[] = {&p, &mode0, &h_move, &h_bal};
     void *a_fb[] = {&p, &h_fin};
+    const dim3 kg(kgrid(p)), kb(kKThreads), tg(tile_warp_grid(p)), tb(kAssignWarps * 32);
 
     NodeAdder top{g};
-    top.kernel((void *)init_kernel, dim3(1), dim3(1024), a_init);
+    top.kernel((void *)init_a_kernel, kg, kb, a_init);
+    top.kernel((void *)init_b_kernel, kg, kb, a_p);
     cudaGraph_t body_move = top.loop(h_move);
     if (body_move) {
         NodeAdder mv{body_move};
         cudaGraph_t body_bal = mv.loop(h_bal);
         if (body_bal) {
             NodeAdder bl{body_bal};
-            bl.kernel(filter_fn(p.d), dim3(fgrid), dim3(kFilterWarps * 32), a_p);
-            bl.kernel(assign_fn(p.d, p.assign_f64), dim3(p.ntiles), dim3(kTile), a_p);
-            bl.kernel((void *)balance_kernel, dim3(1), dim3(1024), a_bal0);
+            bl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
+            bl.kernel(assign_fn(p.d, p.assign_f64), tg, tb, a_p);
+            bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
             if (bl.err != cudaSuccess) mv.err = bl.err;
         }
-        mv.kernel(centroid_fn(p.d), dim3((unsigned)((p.n + 255) / 256)), dim3(256), a_p);
-        mv.kernel((void *)finalize_kernel, dim3(1), dim3(1024), a_fin);
+        mv.kernel(centroid_fn(p.d, p.dtype), tg, tb, a_p);
+        mv.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
+        mv.kernel((void *)finalize_b_kernel, kg, kb, a_p);
         if (mv.err != cudaSuccess) top.err = mv.err;
     }
     top.kernel((void *)final_begin_kernel, dim3(1), dim3(32), a_fb);
     cudaGraph_t body_fin = top.loop(h_fin);
     if (body_fin) {
         NodeAdder fl{body_fin};
-        fl.kernel(filter_fn(p.d), dim3(fgrid), dim3(kFilterWarps * 32), a_p);
-        fl.kernel(assign_fn(p.d, p.assign_f64), dim3(p.ntiles), dim3(kTile), a_p);
-        fl.kernel((void *)balance_kernel, dim3(1), dim3(1024), a_bal1);
+        fl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
+        fl.kernel(assign_fn(p.d, p.assign_f64), tg, tb, a_p);
+        fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (fl.err != cudaSuccess) top.err = fl.err;
     }
     e = top.err;
