@@ -199,6 +199,33 @@ gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, i
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);
 
+/* Largest k accepted by gk_move_centers_noalloc. */
+#define GK_NOALLOC_MAX_K 4096
+
+/*
+ * gk_move_centers without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory while
+ * they run -- processes whose device memory belongs to their own pool or allocator
+ * (a library cudaMalloc could fail there or fragment it) and latency-critical loops
+ * that cannot afford the device synchronisation a cudaMalloc/cudaFree may cause.
+ * It calls no allocation routine of CUDA or of any other library.
+ *
+ * Same results as gk_move_centers (exact fixed-point sums, the same diagonal mean).
+ * Its scratch is one fixed array of about 450 KB in the library's device memory,
+ * held by every GPU that loads the library until the process exits; hence the limit
+ * 1 <= k <= GK_NOALLOC_MAX_K (larger k: GK_ERR_INVALID_ARG).  The first call on a
+ * device looks up the array's device address (set-up); make that first call before
+ * any stream capture.  Every call reuses the array and clears it first; calls whose
+ * GPU work overlaps (other streams, other host threads) race on it.
+ *   coords, weights (nullable), block, centers, centers_out, delta_out (nullable):
+ *   device memory of the current device; beta_out (nullable): host or device.
+ *   Block ids outside [0, k) give GK_ERR_INVALID_ARG.
+ */
+gk_status gk_move_centers_noalloc(const void *coords, int32_t dtype, const void *weights,
+                                  int64_t n, int32_t d, int32_t k, const int32_t *block,
+                                  const double *centers, double *centers_out, double *delta_out,
+                                  double *beta_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,7 +91,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1805_01208_gb300.build.build()")
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1805_01208_gb300.build()")
         L = ctypes.CDLL(LIB_PATH)
         P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         L.gk_default_options.argtypes = [P]
@@ -107,6 +107,8 @@ def lib():
         for name in ("gk_hilbert_keys", "gk_sfc_init", "gk_assign", "gk_move_centers",
                      "gk_balanced_kmeans", "gk_partition"):
             getattr(L, name).restype = i32
+        L.gk_move_centers_noalloc.argtypes = [P, i32, P, i64, i32, i32, P, P, P, P, P, P]
+        L.gk_move_centers_noalloc.restype = i32
         L.gk_release.argtypes = []
         _lib = L
     return _lib
@@ -249,6 +251,22 @@ def move_centers(coords, block, centers, weights=None, stream=None):
     return out, delta, beta.value
 
 
+def move_centers_noalloc(coords, block, centers, weights=None, out=None, delta=None, stream=None):
+    """move_centers with no allocation inside the library (device tensors only, k <= 4096).
+    `out` / `delta` may be preallocated device tensors."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    k = int(centers.shape[0])
+    out = _empty(coords, (k, d), "f64") if out is None else out
+    delta = _empty(coords, (k,), "f64") if delta is None else delta
+    beta = ctypes.c_double()
+    st = lib().gk_move_centers_noalloc(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k,
+                                       _ptr(block), _ptr(centers), _ptr(out), _ptr(delta),
+                                       ctypes.byref(beta), _stream(coords, stream))
+    _check(st, "gk_move_centers_noalloc")
+    return out, delta, beta.value
+
+
 def balanced_kmeans(coords, k: int, eps: float, centers, influence, weights=None,
                     options: Options | None = None, stream=None):
     """Balanced k-means from given centers/influence (updated in place to the state the
@@ -287,5 +305,5 @@ def release():
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .nvcc_build import build as _build
     return _build(force=force)

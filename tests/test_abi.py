@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def libgk():
-    from paper_1805_01208_gb300.build import build
+    from paper_1805_01208_gb300.nvcc_build import build
     path = build()
     return ctypes.CDLL(path)
 
@@ -53,7 +53,7 @@ def test_struct_layouts_match_header():
 
 
 def test_library_is_built_for_sm103a(libgk):
-    from paper_1805_01208_gb300.build import ARCH
+    from paper_1805_01208_gb300.nvcc_build import ARCH
     assert "arch=compute_103a,code=sm_103a" in ARCH
 
 
