@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--assign", default=None, choices=["f32", "f64"],
+                    help="override the workload's assignment precision")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -210,6 +212,8 @@ def main():
     from paper_1805_01208_gb300 import synth
 
     x, w, spec = synth.workload(args.workload, n=args.n)
+    if args.assign:
+        spec["assign"] = args.assign
     if world > 1 and rank > 0:  # replicas: an independent instance per rank
         x = synth.make_points(spec["shape"], spec["n"], spec["d"], spec["seed"] + 1000 * rank,
                               spec["dtype"])

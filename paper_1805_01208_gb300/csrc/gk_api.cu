@@ -102,10 +102,8 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.A = (int *)take((size_t)np * 4);
     p.tiles = (float4 *)take((size_t)p.ntiles * 32);
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
-    p.tcnt = (int *)take((size_t)p.ntiles * 4);
-    p.tcoef = (float4 *)take((size_t)p.ntiles * kCap * 16);
-    p.tga = (float *)take((size_t)p.ntiles * kCap * 4);
-    p.tcid = (int *)take((size_t)p.ntiles * kCap * 4);
+    p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
+    p.heavy = (int *)take((size_t)p.ntiles * 4);
     p.C = (double *)take((size_t)k * d * 8);
     p.Cm = (double *)take((size_t)k * d * 8);
     p.delta = (double *)take((size_t)k * 8);
@@ -113,7 +111,7 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.Iin = (double *)take((size_t)k * 8);
     p.I2 = (double *)take((size_t)2 * k * 8);
     p.g64_2 = (double *)take((size_t)2 * k * 8);
-    p.part = (double *)take((size_t)(k + 127) / 128 * 8);
+    p.part = (double *)take((size_t)(k + kKThreads - 1) / kKThreads * 8);
     p.Sfix = (unsigned long long *)take((size_t)k * 16);
     p.SXfix = (unsigned long long *)take((size_t)k * d * 16);
     p.BBlo = (unsigned long long *)take((size_t)k * d * 8);
@@ -213,6 +211,7 @@ struct Call {
         p.bits = d == 2 ? 32 : 21;
         int dev = 0;
         GK_CUDA(cudaGetDevice(&dev));
+        GK_CUDA(cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev));
         PtrKind kc = ptr_kind(coords, dev);
         PtrKind kw = weights ? ptr_kind(weights, dev) : kHost;
         if (kc == kForeign || kw == kForeign) return GK_ERR_INVALID_ARG;

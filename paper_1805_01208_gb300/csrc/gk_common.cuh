@@ -9,10 +9,11 @@
 //   A      n_pad int32 block ids in sorted order.
 //   tiles  2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -};
 //   supers the same per supertile of kSuperTiles tiles.
-//   per tile candidate table (written by the filter every pass): count (int32, -1 =
-//          overflow: scan all centers) and kCap entries of coefficients
-//          {-2 g q.xyz, g |q|^2} (float4), g (float) and center id (int32), q = frame
-//          center relative to the tile origin, g = scaled 1/I^2.
+//   per tile record (written by the filter every pass, kRecF4 float4): header
+//          {count (int32; -1 = overflow: scan all centers), 0, 0, 0}, {tile origin xyz,
+//          tile radius}, then kCap candidates of 2 float4: {-2 g q.xyz, g |q|^2},
+//          {g, center id (int32 bits), 0, 0}; q = frame center relative to the tile
+//          origin, g = scaled 1/I^2, ascending center order.
 //   per center: C, Cm (k x d FP64, input units), delta, S64, Iin (k FP64), influence and
 //          1/I^2 double-buffered (I2, g64_2: 2 x k FP64), cdata2 (2 x 2 float4 per center:
 //          {frame center hi xyz, g32}, {frame center lo xyz, 0}), 128-bit fixed-point
@@ -26,7 +27,11 @@ namespace gk {
 
 constexpr int kTile = 256;          // points per tile (one warp of the assign kernel)
 constexpr int kSuperTiles = 16;     // tiles per supertile (one CTA of the filter kernel)
-constexpr int kCap = 64;            // candidate centers stored per tile
+constexpr int kCap = 128;           // candidate centers stored per tile
+constexpr int kFastCands = 32;      // candidates brought in with the tile's bulk copy
+constexpr int kRecF4 = 2 + 2 * kCap;  // float4 per tile record (header + candidates)
+constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // bytes of one bulk copy
+constexpr int kKThreads = 32;       // threads per CTA of the k-sized kernels
 constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
 constexpr int kCenterChunk = 1024;  // centers staged in shared memory per bulk copy
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
@@ -59,6 +64,8 @@ struct Ctl {
     int iused_sel;                          // buffer the last assignment was computed with
     int gshift;                             // g32 = g * 2^-gshift
     unsigned int done_count;                // last-block-done counter (reset by the last block)
+    unsigned int tile_ctr;                  // next tile of the assignment pass (reset by the filter)
+    unsigned int heavy_cnt;                 // tiles in the heavy list (reset before each filter)
     int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
     double max_delta;
@@ -101,11 +108,10 @@ struct Prob {
     void *Ws;
     int *A;
     float4 *tiles, *supers;
-    // per-tile candidate tables
-    int *tcnt;
-    float4 *tcoef;
-    float *tga;
-    int *tcid;
+    // per-tile candidate records; tiles that need more than the inline candidates
+    float4 *trec;
+    int *heavy;
+    int nsm;                    // streaming multiprocessors of the device
     // per-center state
     double *C, *Cm, *delta, *S64, *Iin, *I2, *g64_2, *part;
     unsigned long long *Sfix;   // 2 per block (lo, hi)
@@ -230,6 +236,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     for (long long it = 0; it < kSpinLimit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+__device__ __forceinline__ void fence_mbarrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

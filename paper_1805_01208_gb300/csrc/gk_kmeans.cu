@@ -14,7 +14,7 @@
 //
 // Effective distances are compared squared: dist^2 / influence^2 orders the centers
 // exactly as dist / influence does.  The k-sized FP64 work (cbrt, divisions, exp, log)
-// is spread over ceil(k/128) CTAs; the CTA that finishes last takes the global
+// is spread over ceil(k/32) CTAs; the CTA that finishes last takes the global
 // decisions (no grid-wide waiting).  The influence is double-buffered: a pass writes
 // the updated influence into the other buffer and the decision flips the buffer index.
 #include "gk_common.cuh"
@@ -23,7 +23,6 @@
 namespace gk {
 
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
-constexpr int kKThreads = 128;                // threads per CTA of the k-sized kernels
 constexpr int kFilterThreads = kSuperTiles * 32;
 constexpr int kAssignWarps = 8;
 
@@ -67,7 +66,7 @@ __device__ __forceinline__ T block_reduce_max(T v, T *red) {  // all threads get
 }
 
 // ------------------------------------------------------------------------------
-// Initial state (two kernels over ceil(k/128) CTAs).
+// Initial state (two kernels over ceil(k/32) CTAs).
 // ------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphConditionalHandle h_move,
                                                            cudaGraphConditionalHandle h_bal) {
@@ -117,6 +116,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->maxS_key = 0ull;
         ctl->maxd_key = 0ull;
         ctl->nonempty = 0;
+        ctl->heavy_cnt = 0u;
         if (h_move) cudaGraphSetConditional(h_move, 1u);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     __shared__ __align__(128) float4 sc[2 * kCenterChunk];
     __shared__ int slist[kSuperCap];
     __shared__ float s_red[kSuperTiles];
+    __shared__ float s_gred[kSuperTiles];
     __shared__ int s_wcnt[kSuperTiles];
     __shared__ __align__(8) unsigned long long bar;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -186,7 +187,11 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     const int sel = p.ctl->isel;
     const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
     const float infl = 4.0f * kU * p.R;
-    if (tid == 0) mbar_init(&bar, 1);
+    if (s == 0 && tid == 0) p.ctl->tile_ctr = 0u;  // tile queue of the assignment that follows
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbarrier_init();
+    }
     __syncthreads();
     float so[3], sh[3];
     {
@@ -213,8 +218,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         return !__syncthreads_or(!ok);
     };
     bool failed = false;
-    // level 1, sweep 1: tau of the supertile
-    float tau = INFINITY;
+    // level 1, sweep 1: tau of the supertile (and the largest g of all centers)
+    float tau = INFINITY, gall = 0.0f;
     for (int ch = 0; ch < nch; ++ch) {
         if (!stage(ch)) {
             failed = true;
@@ -225,14 +230,25 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
             float lb, ub;
             box_bounds<D>(sc[2 * c], sc[2 * c + 1], so, sh, lb, ub);
             tau = fminf(tau, ub);
+            gall = fmaxf(gall, sc[2 * c].w);
         }
         __syncthreads();
     }
-    for (int off = 16; off; off >>= 1) tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, off));
-    if (lane == 0) s_red[warp] = tau;
+    for (int off = 16; off; off >>= 1) {
+        tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, off));
+        gall = fmaxf(gall, __shfl_xor_sync(0xffffffffu, gall, off));
+    }
+    if (lane == 0) {
+        s_red[warp] = tau;
+        s_gred[warp] = gall;
+    }
     __syncthreads();
     tau = s_red[0];
-    for (int w = 1; w < kSuperTiles; ++w) tau = fminf(tau, s_red[w]);
+    gall = s_gred[0];
+    for (int w = 1; w < kSuperTiles; ++w) {
+        tau = fminf(tau, s_red[w]);
+        gall = fmaxf(gall, s_gred[w]);
+    }
     const float tauS = __fmul_ru(tau, 1.0f + 64.0f * kU);
     // level 1, sweep 2: ascending list of the supertile's candidates
     int count = 0;
@@ -272,7 +288,11 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         // A bulk copy did not complete in time: record it, let the assignment scan
         // every center for these tiles, and wait (bounded) for the copy in flight.
         if (tid == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
-        if (t < p.ntiles && lane == 0) p.tcnt[t] = -1;
+        if (t < p.ntiles && lane == 0) {
+            p.trec[(size_t)t * kRecF4] = make_float4(__int_as_float(-1), INFINITY, 0.f, 0.f);
+            p.trec[(size_t)t * kRecF4 + 1] = p.tiles[2 * t];
+            p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
+        }
         mbar_wait_bounded(&bar, phase ^ 1u);
         return;
     }
@@ -312,7 +332,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
     const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
     int cnt = 0;
-    const size_t row = (size_t)t * kCap;
+    float gkept = 0.0f;
+    float4 *rec = p.trec + (size_t)t * kRecF4;
     for (int base = 0; base < L; base += 32) {
         int i = base + lane;
         bool keep = false;
@@ -330,17 +351,19 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
             float q0 = (ch.x - o[0]) + cl.x;
             float q1 = (ch.y - o[1]) + cl.y;
             float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-            float g = ch.w;
-            float qq = fmaf(q2, q2, fmaf(q1, q1, q0 * q0));
-            p.tcoef[row + pos] = make_float4(-2.0f * g * q0, -2.0f * g * q1, -2.0f * g * q2, g * qq);
-            p.tga[row + pos] = g;
-            p.tcid[row + pos] = c;
+            rec[2 + 2 * pos] = make_float4(q0, q1, q2, ch.w);
+            rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
         }
+        if (keep) gkept = fmaxf(gkept, ch.w);
         cnt += __popc(bal);
     }
+    for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
     if (lane == 0) {
         bool over = cnt > kCap;
-        p.tcnt[t] = over ? -1 : cnt;
+        // header: count (-1: scan all centers) and the largest g the tile can meet
+        rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
+        rec[1] = p.tiles[2 * t];
+        if (over || cnt > kFastCands) p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
         if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
         long long nv = p.n - (long long)t * kTile;
         nv = nv > kTile ? kTile : nv;
@@ -379,17 +402,17 @@ __device__ __forceinline__ void seg_flush_u64(int id, unsigned long long v, unsi
 // Assignment + block-weight histogram (Section 4.2; Algorithm 1 inner loop).
 //
 // One warp per tile of 256 curve-consecutive points; lane l owns points 8l..8l+7.
-// In tile-local frame coordinates x' = x - o the squared effective distance to a
-// candidate with frame center q (relative to o) and g = scaled 1/I^2 is
-//     E = g |x'|^2 - 2 g q.x' + g |q|^2  (a chain of four fma per point; two points
-//     per packed fma.rn.f32x2).
+// With tile-local frame coordinates x' = x - o and the candidate's frame center
+// relative to the tile origin q, the squared effective distance is
+//     E = g |x' - q|^2   (g = scaled 1/I^2; two points per packed f32x2 operation).
 // FP64 mode: the FP32 winner b is kept when the FP32 gap to the runner-up exceeds
-// twice a rigorous bound B on |E_fp32 - E_exact| (coordinate rounding, coefficient
-// rounding, fma-chain rounding; evaluated with the tile radius and the largest g of
-// the tile's candidates, doubled for safety); a point with a single candidate is
-// decided by the filter alone.  Every other point is decided again in FP64 from the
-// raw coordinates over all of the tile's candidates.  The result is the FP64 argmin
-// up to ties closer than FP64 rounding, ties going to the lowest center index.
+// twice a rigorous bound B on |E_fp32 - E_exact| (rounding of the stored point, of
+// the tile-local differences and of the hi/lo center, and of the squares, the sum
+// and g; per point, with the largest g of the tile's candidates; doubled for safety);
+// a point with a single candidate is decided by the filter alone.  Every other point
+// is decided again in FP64 from the raw coordinates, over the candidates whose FP32
+// value lies within the margin.  The result is the FP64 argmin up to ties closer than
+// FP64 rounding, ties going to the lowest center index.
 // ------------------------------------------------------------------------------
 template <bool F64MODE>
 __device__ __forceinline__ void argmin_update(float E, int c, float &E1, float &E2, int &best) {
@@ -399,191 +422,441 @@ __device__ __forceinline__ void argmin_update(float E, int c, float &E1, float &
     E1 = lt ? E : E1;
 }
 
+// Persistent warps: warp gw of TW takes tiles gw, gw + TW, ...  Each warp owns two
+// shared-memory stages; one lane issues the bulk copies (tile record with its first
+// kFastCands candidates, and the d coordinate planes of the tile) for the tile after
+// next as soon as a stage is consumed, so the loads of two tiles are always in flight.
+constexpr int kAWarps = 4;
+constexpr int kAMinBlocks = 5;
+struct AStage {
+    float4 rec[2 + 2 * kFastCands];
+    float x[3][kTile];
+};
+
 template <int D, bool F64MODE>
-__global__ void __launch_bounds__(kAssignWarps * 32) assign_kernel(Prob p) {
+__global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob p) {
     count_launch(p.ctl);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_assign0 = globaltimer_ns();
-    __shared__ __align__(16) float4 s_coef[kAssignWarps][kCap];
-    __shared__ float s_ga[kAssignWarps][kCap];
-    __shared__ int s_cid[kAssignWarps][kCap];
+    __shared__ __align__(128) AStage st[kAWarps][2];
+    __shared__ __align__(8) unsigned long long bar[kAWarps][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int t = blockIdx.x * kAssignWarps + w;
-    if (t >= p.ntiles) return;
+    if (lane == 0) {
+        mbar_init(&bar[w][0], 1);
+        mbar_init(&bar[w][1], 1);
+        fence_mbarrier_init();
+    }
+    __syncwarp();
     const int sel = p.ctl->isel;
-    const float4 ob = p.tiles[2 * t];
-    const float o[3] = {ob.x, ob.y, ob.z};
-    const int cnt = p.tcnt[t];
-    const bool all = cnt < 0;
-    const long long i0 = (long long)t * kTile + lane * 8;
-    long long nv = p.n - i0;
-    const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-
-    // 8 consecutive points per lane (n_pad is a multiple of kTile: loads stay in bounds)
-    float2 xp[3][4];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        const float4 *src = reinterpret_cast<const float4 *>(p.X32 + (size_t)j * p.n_pad + i0);
-        float4 a = src[0], b = src[1];
-        xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
-        xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
-        xp[j][2] = make_float2(b.x - o[j], b.y - o[j]);
-        xp[j][3] = make_float2(b.z - o[j], b.w - o[j]);
-    }
-    float2 xx[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
-        xx[q] = acc;
-    }
-    float E1[8], E2[8];
-    int best[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        E1[q] = INFINITY;
-        E2[q] = INFINITY;
-        best[q] = 0;
-    }
-    float gl = 0.0f;
-    auto consume = [&](int m) {
-        for (int jj = 0; jj < m; ++jj) {
-            const float4 cf = s_coef[w][jj];
-            const float a = s_ga[w][jj];
-            const int c = s_cid[w][jj];
-            const float2 a2 = make_float2(a, a), bx = make_float2(cf.x, cf.x),
-                         by = make_float2(cf.y, cf.y), bz = make_float2(cf.z, cf.z),
-                         e2 = make_float2(cf.w, cf.w);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float2 acc = e2;
-                if (D == 3) acc = __ffma2_rn(bz, xp[2][q], acc);
-                acc = __ffma2_rn(by, xp[1][q], acc);
-                acc = __ffma2_rn(bx, xp[0][q], acc);
-                acc = __ffma2_rn(a2, xx[q], acc);
-                argmin_update<F64MODE>(acc.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
-                argmin_update<F64MODE>(acc.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
-            }
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4);
+    auto issue = [&](int t, int b) {
+        if (lane == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[w][b], bytes);
+            bulk_g2s(st[w][b].rec, p.trec + (size_t)t * kRecF4, kRecFastBytes, &bar[w][b]);
+            for (int j = 0; j < D; ++j)
+                bulk_g2s(st[w][b].x[j], p.X32 + (size_t)j * p.n_pad + (size_t)t * kTile, kTile * 4,
+                         &bar[w][b]);
         }
     };
-    if (!all) {
-        const size_t row = (size_t)t * kCap;
-        for (int j = lane; j < cnt; j += 32) {
-            s_coef[w][j] = p.tcoef[row + j];
-            float g = p.tga[row + j];
-            s_ga[w][j] = g;
-            s_cid[w][j] = p.tcid[row + j];
-            gl = fmaxf(gl, g);
+    // Tiles come from a queue (one atomic per tile) so that expensive tiles do not
+    // pile up on a few warps; the two stages hold the two smallest tiles taken.
+    // Positions [0, H) are the heavy tiles (slow path), served first; positions H + t
+    // are tile t, skipped there when it is heavy.  Warp gw takes positions gw, gw + TW, ...
+    const int H = (int)p.ctl->heavy_cnt;
+    const int TW = gridDim.x * kAWarps;
+    int next_pos = blockIdx.x * kAWarps + w;
+    auto grab = [&](int npos) -> int {  // the warp's next npos positions (npos <= 2)
+        const int pos = next_pos;
+        next_pos += npos * TW;
+        return pos;
+    };
+    auto tile_at = [&](int pos) -> int {
+        if (pos < H) {
+            int t = 0;
+            if (lane == 0) t = p.heavy[pos];
+            return __shfl_sync(0xffffffffu, t, 0);
         }
-        __syncwarp();
-        consume(cnt);
-    } else {
-        const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
-        for (int base = 0; base < p.k; base += 32) {
-            int m = min(32, p.k - base);
-            __syncwarp();
-            if (lane < m) {
-                int c = base + lane;
-                float4 ch = cd[2 * c], cl = cd[2 * c + 1];
-                float q0 = (ch.x - o[0]) + cl.x;
-                float q1 = (ch.y - o[1]) + cl.y;
-                float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-                float g = ch.w;
-                float qq = fmaf(q2, q2, fmaf(q1, q1, q0 * q0));
-                s_coef[w][lane] = make_float4(-2.0f * g * q0, -2.0f * g * q1, -2.0f * g * q2, g * qq);
-                s_ga[w][lane] = g;
-                s_cid[w][lane] = c;
-                gl = fmaxf(gl, g);
-            }
-            __syncwarp();
-            consume(m);
+        return pos - H;  // >= ntiles: the queue is empty
+    };
+    const int pos0 = grab(1), pos1 = grab(1);
+    int tq0 = tile_at(pos0), tq1 = tile_at(pos1);
+    int hv0 = pos0 < H, hv1 = pos1 < H;
+    if (tq0 < p.ntiles) issue(tq0, 0);
+    if (tq1 < p.ntiles) issue(tq1, 1);
+    unsigned ph0 = 0, ph1 = 0;
+    unsigned long long nre = 0;
+    for (int it = 0;; ++it) {
+        const int b = it & 1;
+        const int t = b ? tq1 : tq0;
+        if (t >= p.ntiles) break;  // the other stage holds a larger index
+        const unsigned phb = b ? ph1 : ph0;
+        bool ok = mbar_wait_bounded(&bar[w][b], phb);
+        if (!__all_sync(0xffffffffu, ok)) {
+            // A bulk copy did not arrive in time: record it and stop this warp after a
+            // bounded wait for the copies still in flight (this stage and the other).
+            if (lane == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
+            mbar_wait_bounded(&bar[w][b], phb);
+            if ((b ? tq0 : tq1) < p.ntiles) mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
+            return;
         }
-    }
-    if (F64MODE) {
-        for (int off = 16; off; off >>= 1) gl = fmaxf(gl, __shfl_xor_sync(0xffffffffu, gl, off));
-        // error bound B(E) = beta0 + beta1 sqrt(E) + beta2 E (see the comment above)
-        const float R = p.R;
-        const float rp = ob.w + 2.0f * 1.7320508f * kU * R;
-        const float ex = sqrtf((float)D) * kU * (R + rp);
+        if (b) ph1 ^= 1u; else ph0 ^= 1u;
+        const AStage &S = st[w][b];
+        const int cnt = __float_as_int(S.rec[0].x);
+        const bool from_heavy = b ? hv1 : hv0;
+        if (!from_heavy && (cnt < 0 || cnt > kFastCands)) {
+            // a heavy tile met again in the ordinary range: already done; take the next
+            __syncwarp();
+            const int np = grab(1);
+            const int nt = tile_at(np);
+            if (b) { tq1 = nt; hv1 = np < H; } else { tq0 = nt; hv0 = np < H; }
+            if (nt < p.ntiles) issue(nt, b);
+            continue;
+        }
+        const float gl = S.rec[0].y;  // largest g among the tile's candidates
         const float sg = sqrtf(gl);
-        const float c2 = (2.0f * D + 10.0f) * kU;
-        const float beta2 = c2;
-        const float beta1 = c2 * 4.0f * sg * rp + 2.0f * sg * ex;
-        const float beta0 = c2 * 4.0f * gl * rp * rp + gl * ex * ex;
-        unsigned flag = 0;
+        const float4 ob = S.rec[1];
+        const float o[3] = {ob.x, ob.y, ob.z};
+        const bool all = cnt < 0;
+        const int ncand = all ? p.k : cnt;
+        const float4 *grec = p.trec + (size_t)t * kRecF4;
+        const long long i0 = (long long)t * kTile + lane * 8;
+        long long nv = p.n - i0;
+        const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+
+        float2 xp[3][4];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const float4 *src = reinterpret_cast<const float4 *>(&S.x[j][lane * 8]);
+            float4 a = src[0], c4 = src[1];
+            xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
+            xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
+            xp[j][2] = make_float2(c4.x - o[j], c4.y - o[j]);
+            xp[j][3] = make_float2(c4.z - o[j], c4.w - o[j]);
+        }
+        float E1[8], E2[8];
+        int best[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            float Estar = 2.0f * E2[q] + 2.0f * (beta0 + 2.0f * beta1 * beta1);
-            float B = 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
-            bool single = E2[q] == INFINITY && E1[q] < INFINITY;
-            bool ok = single || (E2[q] - E1[q]) > 2.0f * B;
-            if (q < nval && !ok) flag |= 1u << q;
+            E1[q] = INFINITY;
+            E2[q] = INFINITY;
+            best[q] = 0;
         }
-        if (flag) {
-            const double *g64 = p.g64_2 + (size_t)sel * p.k;
-            const int ncand = all ? p.k : cnt;
+        // Candidates: the first kFastCands come with the stage (shared-memory broadcast).
+        // The rest (or all centers when the tile overflowed) are fetched 32 at a time,
+        // one per lane, and pruned per 64-point sub-box (8 lanes) with a lower bound on
+        // the effective distance before the warp evaluates the ones some sub-box needs.
+        const int nfast = all ? 0 : min(ncand, kFastCands);
+        const bool slow = ncand > nfast;
+        auto slow_cand = [&](int jj, float4 &qg, int &c) {  // jj < ncand
+            if (!all) {
+                qg = grec[2 + 2 * jj];
+                c = __float_as_int(grec[3 + 2 * jj].x);
+            } else {
+                c = jj;
+                const float4 ch = cd[2 * c], cl = cd[2 * c + 1];
+                qg = make_float4((ch.x - o[0]) + cl.x, (ch.y - o[1]) + cl.y,
+                                 D == 3 ? (ch.z - o[2]) + cl.z : 0.0f, ch.w);
+            }
+        };
+        auto consume = [&](const float4 &qg, int c) {
+            const float2 g2 = make_float2(qg.w, qg.w), nqx = make_float2(-qg.x, -qg.x),
+                         nqy = make_float2(-qg.y, -qg.y), nqz = make_float2(-qg.z, -qg.z);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 dx = __fadd2_rn(xp[0][q], nqx);
+                const float2 dy = __fadd2_rn(xp[1][q], nqy);
+                float2 ss = __fmul2_rn(dx, dx);
+                ss = __ffma2_rn(dy, dy, ss);
+                if (D == 3) {
+                    const float2 dz = __fadd2_rn(xp[2][q], nqz);
+                    ss = __ffma2_rn(dz, dz, ss);
+                }
+                const float2 E = __fmul2_rn(g2, ss);
+                argmin_update<F64MODE>(E.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
+                argmin_update<F64MODE>(E.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
+            }
+        };
+        int jj = 0;
+        for (; jj + 1 < nfast; jj += 2) {
+            const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
+            const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
+            consume(qa, ca);
+            consume(qb, cb);
+        }
+        if (jj < nfast) {
+            const float4 qa = S.rec[2 + 2 * jj];
+            consume(qa, __float_as_int(S.rec[3 + 2 * jj].x));
+        }
+        // error-bound constants (FP64 mode); see the comment above
+        const float R = p.R;
+        const float sd = sqrtf((float)D);
+        const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
+        // coordinate term with the largest |x'| of the lane's points
+        float xn2 = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
+            xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
+        }
+        const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
+        auto point_bound = [&](int q, float sgl, float glv, float Eref) -> float {
+            (void)q;
+            const float beta1 = 2.0f * sgl * e0;
+            const float beta0 = glv * e0 * e0;
+            const float Estar = 2.0f * Eref + 2.0f * (beta0 + 2.0f * beta1 * beta1);
+            return 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
+        };
+        // 64-point sub-boxes (lanes 8s..8s+7) in tile-local coordinates, widened so that
+        // they contain the exact points
+        float sbm[3] = {0.f, 0.f, 0.f}, sbh[3] = {0.f, 0.f, 0.f};
+        if (__any_sync(0xffffffffu, slow)) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                float lo = INFINITY, hi = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (2 * q < nval) {
+                        lo = fminf(lo, xp[j][q].x);
+                        hi = fmaxf(hi, xp[j][q].x);
+                    }
+                    if (2 * q + 1 < nval) {
+                        lo = fminf(lo, xp[j][q].y);
+                        hi = fmaxf(hi, xp[j][q].y);
+                    }
+                }
+#pragma unroll
+                for (int off = 1; off < 8; off <<= 1) {
+                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+                }
+                if (lo > hi) {  // a sub-box without points: never needs a candidate
+                    lo = 0.f;
+                    hi = 0.f;
+                }
+                sbm[j] = 0.5f * lo + 0.5f * hi;
+                sbh[j] = __fadd_ru(fmaxf(__fsub_ru(hi, sbm[j]), __fsub_ru(sbm[j], lo)), 16.0f * kU * R);
+            }
+        }
+        // sub-box threshold: no candidate whose lower bound exceeds it can become a point's
+        // best (FP32 form) or best/second or pass the FP64 screen (FP64 mode)
+        auto subbox_threshold = [&]() -> float {
+            float tmax = -INFINITY;
+#pragma unroll
             for (int q = 0; q < 8; ++q) {
-                if (!((flag >> q) & 1u)) continue;
-                double x64[3] = {0.0, 0.0, 0.0};
-                for (int j = 0; j < D; ++j)
-                    x64[j] = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + i0 + q]
-                                          : (double)p.X32[(size_t)j * p.n_pad + i0 + q];
-                double bestE = INFINITY;
-                int b = 0;
-                for (int jj = 0; jj < ncand; ++jj) {
-                    int c = all ? jj : s_cid[w][jj];
-                    double s2 = 0.0;
+                if (q >= nval) continue;
+                float tq;
+                if (F64MODE)
+                    tq = E2[q] == INFINITY ? INFINITY : E2[q] + 2.0f * point_bound(q, sg, gl, E2[q]);
+                else
+                    tq = E1[q];
+                tmax = fmaxf(tmax, tq);
+            }
+#pragma unroll
+            for (int off = 1; off < 8; off <<= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
+            return tmax;
+        };
+        if (__any_sync(0xffffffffu, slow)) {
+            for (int base = nfast; base < ncand; base += 32) {
+                float4 mqg = make_float4(0.f, 0.f, 0.f, 0.f);
+                int mc = 0;
+                if (base + lane < ncand) slow_cand(base + lane, mqg, mc);
+                const float tsub = subbox_threshold();
+                // lane j's candidate: needed by some sub-box?
+                unsigned need = 0;
+#pragma unroll
+                for (int s4 = 0; s4 < 4; ++s4) {
+                    const float ts = __shfl_sync(0xffffffffu, tsub, s4 * 8);
+                    float sm[3], sh[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        sm[j] = __shfl_sync(0xffffffffu, sbm[j], s4 * 8);
+                        sh[j] = __shfl_sync(0xffffffffu, sbh[j], s4 * 8);
+                    }
+                    float l2 = 0.f;
+#pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        double df = x64[j] - p.C[c * D + j];
-                        s2 += df * df;
+                        const float qj = j == 0 ? mqg.x : (j == 1 ? mqg.y : mqg.z);
+                        const float a = fabsf(qj - sm[j]);
+                        const float h = fmaf(4.0f * kU, fabsf(qj) + R, sh[j]);
+                        const float l = fmaxf(a - h, 0.0f);
+                        l2 = fmaf(l, l, l2);
                     }
-                    double E = s2 * g64[c];
-                    if (E < bestE) {
-                        bestE = E;
-                        b = c;
-                    }
+                    if (!(mqg.w * l2 * (1.0f - 1e-5f) > ts)) need = 1;
                 }
-                best[q] = b;
+                unsigned todo = __ballot_sync(0xffffffffu, need && base + lane < ncand);
+                while (todo) {
+                    const int j = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    float4 qg;
+                    qg.x = __shfl_sync(0xffffffffu, mqg.x, j);
+                    qg.y = __shfl_sync(0xffffffffu, mqg.y, j);
+                    qg.z = __shfl_sync(0xffffffffu, mqg.z, j);
+                    qg.w = __shfl_sync(0xffffffffu, mqg.w, j);
+                    consume(qg, __shfl_sync(0xffffffffu, mc, j));
+                }
             }
         }
-        unsigned nre = __popc(flag);
+        if (F64MODE) {
+            unsigned flag = 0;
+            float thr[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float B = point_bound(q, sg, gl, E2[q]);
+                const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
+                const bool okq = single || (E2[q] - E1[q]) > 2.0f * B;
+                thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
+                if (q < nval && !okq) flag |= 1u << q;
+            }
+            // FP64 re-decision of the flagged points, only for candidates within the
+            // margin; warp-collective because the slow candidates are shuffled.
+            if (__any_sync(0xffffffffu, flag != 0u)) {
+                const double *g64 = p.g64_2 + (size_t)sel * p.k;
+                // flagged points in local arrays: this rare path stays compact (no unrolling)
+                float px[8][3], pthr[8];
+                double pE[8];
+                int pb[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 v0 = xp[0][q >> 1], v1 = xp[1][q >> 1], v2 = xp[2][q >> 1];
+                    px[q][0] = (q & 1) ? v0.y : v0.x;
+                    px[q][1] = (q & 1) ? v1.y : v1.x;
+                    px[q][2] = D == 3 ? ((q & 1) ? v2.y : v2.x) : 0.0f;
+                    pthr[q] = thr[q];
+                    pE[q] = INFINITY;
+                    pb[q] = best[q];
+                }
+                auto recheck = [&](const float4 &qg, int c) {
+#pragma unroll 1
+                    for (int q = 0; q < 8; ++q) {
+                        if (!((flag >> q) & 1u)) continue;
+                        const float d0 = px[q][0] - qg.x, d1 = px[q][1] - qg.y;
+                        const float d2 = D == 3 ? px[q][2] - qg.z : 0.0f;
+                        const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                        if (!(E32 <= pthr[q])) continue;  // cannot be the FP64 winner
+                        double s2 = 0.0;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + i0 + q]
+                                                           : (double)p.X32[(size_t)j * p.n_pad + i0 + q];
+                            const double df = xj - p.C[c * D + j];
+                            s2 += df * df;
+                        }
+                        const double E = s2 * g64[c];
+                        if (E < pE[q]) {  // ascending center order: ties keep the lowest
+                            pE[q] = E;
+                            pb[q] = c;
+                        }
+                    }
+                };
+                if (flag) {
+                    for (int jj2 = 0; jj2 < nfast; ++jj2)
+                        recheck(S.rec[2 + 2 * jj2], __float_as_int(S.rec[3 + 2 * jj2].x));
+                }
+                // slow candidates: a sub-box needs one only if its lower bound is within the
+                // screen of some flagged point of the sub-box
+                float tfl = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (!((flag >> q) & 1u)) continue;
+                    // E_fp32 >= E - B(E) grows with E: a center whose exact value exceeds
+                    // thr + 2 B(2 thr) has E_fp32 > thr whenever 2 B(2 thr) <= thr
+                    const float m2 = 2.0f * point_bound(q, sg, gl, 2.0f * thr[q]);
+                    tfl = fmaxf(tfl, m2 <= thr[q] ? thr[q] + m2 : INFINITY);
+                }
+#pragma unroll
+                for (int off = 1; off < 8; off <<= 1) tfl = fmaxf(tfl, __shfl_xor_sync(0xffffffffu, tfl, off));
+                for (int base = nfast; base < ncand; base += 32) {
+                    float4 mqg = make_float4(0.f, 0.f, 0.f, 0.f);
+                    int mc = 0;
+                    if (base + lane < ncand) slow_cand(base + lane, mqg, mc);
+                    unsigned need = 0;
+#pragma unroll
+                    for (int s4 = 0; s4 < 4; ++s4) {
+                        const float ts = __shfl_sync(0xffffffffu, tfl, s4 * 8);
+                        float sm[3], sh[3];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            sm[j] = __shfl_sync(0xffffffffu, sbm[j], s4 * 8);
+                            sh[j] = __shfl_sync(0xffffffffu, sbh[j], s4 * 8);
+                        }
+                        float l2 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < D; ++j) {
+                            const float qj = j == 0 ? mqg.x : (j == 1 ? mqg.y : mqg.z);
+                            const float a = fabsf(qj - sm[j]);
+                            const float h = fmaf(4.0f * kU, fabsf(qj) + R, sh[j]);
+                            const float l = fmaxf(a - h, 0.0f);
+                            l2 = fmaf(l, l, l2);
+                        }
+                        if (!(mqg.w * l2 * (1.0f - 1e-5f) > ts)) need = 1;
+                    }
+                    unsigned todo = __ballot_sync(0xffffffffu, need && base + lane < ncand);
+                    while (todo) {
+                        const int j = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        float4 qg;
+                        qg.x = __shfl_sync(0xffffffffu, mqg.x, j);
+                        qg.y = __shfl_sync(0xffffffffu, mqg.y, j);
+                        qg.z = __shfl_sync(0xffffffffu, mqg.z, j);
+                        qg.w = __shfl_sync(0xffffffffu, mqg.w, j);
+                        const int c = __shfl_sync(0xffffffffu, mc, j);
+                        if (flag) recheck(qg, c);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) best[q] = pb[q];
+            }
+            nre += __popc(flag);
+        }
+        __syncwarp();  // every lane is done with stage b
+        {
+            const int np = grab(1);
+            const int nt = tile_at(np);
+            if (b) { tq1 = nt; hv1 = np < H; } else { tq0 = nt; hv0 = np < H; }
+            if (nt < p.ntiles) issue(nt, b);
+        }
+        // block ids
+        if (nval == 8) {
+            int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+            dst[0] = make_int4(best[0], best[1], best[2], best[3]);
+            dst[1] = make_int4(best[4], best[5], best[6], best[7]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < nval) p.A[i0 + q] = best[q];
+        }
+        // block weights: runs inside the lane, then a segmented reduction over lanes
+        int cur = -1;
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nval) {
+                unsigned long long v = 1ull;
+                if (p.weighted)
+                    v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
+                                                          : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
+                if (best[q] != cur) {
+                    if (cur >= 0) {
+                        if (p.weighted)
+                            atomic_add_u128(&p.Sfix[2 * cur], acc);
+                        else
+                            atomicAdd(&p.Sfix[2 * cur], acc);
+                    }
+                    cur = best[q];
+                    acc = 0;
+                }
+                acc += v;
+            }
+        }
+        seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
+    }
+    if (F64MODE) {
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
-        if (lane == 0 && nre) atomicAdd(&p.ctl->rechecks, (unsigned long long)nre);
+        if (lane == 0 && nre) atomicAdd(&p.ctl->rechecks, nre);
     }
-    // block ids
-    if (nval == 8) {
-        int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
-        dst[0] = make_int4(best[0], best[1], best[2], best[3]);
-        dst[1] = make_int4(best[4], best[5], best[6], best[7]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q < nval) p.A[i0 + q] = best[q];
-    }
-    // block weights: runs inside the lane, then a segmented reduction over lanes
-    int cur = -1;
-    unsigned long long acc = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        if (q < nval) {
-            unsigned long long v = 1ull;
-            if (p.weighted)
-                v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
-                                                      : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
-            if (best[q] != cur) {
-                if (cur >= 0) {
-                    if (p.weighted)
-                        atomic_add_u128(&p.Sfix[2 * cur], acc);
-                    else
-                        atomicAdd(&p.Sfix[2 * cur], acc);
-                }
-                cur = best[q];
-                acc = 0;
-            }
-            acc += v;
-        }
-    }
-    seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
 }
 
 // ------------------------------------------------------------------------------
@@ -660,6 +933,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
         ctl->maxS_key = 0ull;
         ctl->maxg_key = 0ull;
+        ctl->heavy_cnt = 0u;  // the next filter rebuilds the heavy list
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
         if (mode == 2) return;
@@ -793,7 +1067,7 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
 }
 
 // ------------------------------------------------------------------------------
-// Center movement, part 2 (ceil(k/128) CTAs): C' = sum(w x) / sum(w) (empty block:
+// Center movement, part 2 (ceil(k/32) CTAs): C' = sum(w x) / sum(w) (empty block:
 // C' = C), delta_c = |C'_c - C_c|, and per-CTA partial sums of the block diagonals;
 // the last CTA forms beta (the mean diagonal of the non-empty blocks, summed in CTA
 // order), the convergence test and the loop decision.  mode 1: standalone.
@@ -950,10 +1224,20 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
     return cudaLaunchKernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), args1, 0, s);
 }
+static int assign_grid(const Prob &p) {
+    int need = (p.ntiles + kAWarps - 1) / kAWarps;
+    int cap = (p.nsm > 0 ? p.nsm : 152) * kAMinBlocks;
+    return need < cap ? need : cap;
+}
+static cudaError_t prepare_assign(void *fn) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
 cudaError_t launch_assign(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    return cudaLaunchKernel(assign_fn(p.d, p.assign_f64), dim3(tile_warp_grid(p)),
-                            dim3(kAssignWarps * 32), args1, 0, s);
+    void *fn = assign_fn(p.d, p.assign_f64);
+    cudaError_t e = prepare_assign(fn);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(fn, dim3(assign_grid(p)), dim3(kAWarps * 32), args1, 0, s);
 }
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s) {
     balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0);
@@ -1055,6 +1339,11 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     void *a_fb[] = {&p, &h_fin};
     const dim3 kg(kgrid(p)), kb(kKThreads), tg(tile_warp_grid(p)), tb(kAssignWarps * 32);
 
+    e = prepare_assign(assign_fn(p.d, p.assign_f64));
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+    }
     NodeAdder top{g};
     top.kernel((void *)init_a_kernel, kg, kb, a_init);
     top.kernel((void *)init_b_kernel, kg, kb, a_p);
@@ -1065,7 +1354,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
         if (body_bal) {
             NodeAdder bl{body_bal};
             bl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
-            bl.kernel(assign_fn(p.d, p.assign_f64), tg, tb, a_p);
+            bl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
             if (bl.err != cudaSuccess) mv.err = bl.err;
         }
@@ -1079,7 +1368,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     if (body_fin) {
         NodeAdder fl{body_fin};
         fl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
-        fl.kernel(assign_fn(p.d, p.assign_f64), tg, tb, a_p);
+        fl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (fl.err != cudaSuccess) top.err = fl.err;
     }

@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kNoAllocMaxK = GK_NOALLOC_MAX_K;
 constexpr int kNAThreads = 256;   // accumulation CTAs
-constexpr int kNAKThreads = 128;  // per-center CTAs (same as the allocating path)
+constexpr int kNAKThreads = kKThreads;  // per-center CTAs (same as the allocating path)
 
 struct NAScratch {
     unsigned long long xabs_key;  // ordered key of max |x| (FP64 value)
@@ -192,9 +192,9 @@ __global__ void __launch_bounds__(kNAThreads) na_accum_kernel(const T *x, const 
 __global__ void __launch_bounds__(kNAKThreads) na_finalize_kernel(NAScratch *s, int k, int d, int dtype,
                                                                  int weighted, const double *C,
                                                                  double *Cout, double *delta) {
-    __shared__ double r_sum[kNAKThreads / 32];
-    __shared__ int r_cnt[kNAKThreads / 32];
-    __shared__ double r_max[kNAKThreads / 32];
+    __shared__ double r_sum[(kNAKThreads + 31) / 32];
+    __shared__ int r_cnt[(kNAKThreads + 31) / 32];
+    __shared__ double r_max[(kNAKThreads + 31) / 32];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int Fw, Fx;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kNAKThreads) na_finalize_kernel(NAScratch *s, 
     if (tid == 0) {
         double sm = 0.0, m = 0.0;
         int nn = 0;
-        for (int w = 0; w < kNAKThreads / 32; ++w) {
+        for (int w = 0; w < (kNAKThreads + 31) / 32; ++w) {
             sm += r_sum[w];
             nn += r_cnt[w];
             m = fmax(m, r_max[w]);
