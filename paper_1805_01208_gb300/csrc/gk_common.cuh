@@ -10,14 +10,18 @@
 //   tiles  2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -};
 //   supers the same per supertile of kSuperTiles tiles.
 //   per tile record (written by the filter every pass, kRecF4 float4): header
-//          {count (int32; -1 = overflow: scan all centers), 0, 0, 0}, {tile origin xyz,
-//          tile radius}, then kCap candidates of 2 float4: {-2 g q.xyz, g |q|^2},
-//          {g, center id (int32 bits), 0, 0}; q = frame center relative to the tile
-//          origin, g = scaled 1/I^2, ascending center order.
+//          {count (int32; -1 = overflow: scan all centers), largest g of the tile's
+//          candidates, 0, 0}, {tile origin xyz, tile radius}, then up to kCap candidates
+//          of 2 float4: {q xyz, g}, {center id (int32 bits), 0, 0, 0}; q = frame center
+//          relative to the tile origin, g = scaled 1/I^2, ascending center order.
+//   heavy  ntiles entries: from the front, tiles whose candidates do not all fit the bulk
+//          copy of the assignment; from the back, tiles taken by a whole CTA.
 //   per center: C, Cm (k x d FP64, input units), delta, S64, Iin (k FP64), influence and
 //          1/I^2 double-buffered (I2, g64_2: 2 x k FP64), cdata2 (2 x 2 float4 per center:
 //          {frame center hi xyz, g32}, {frame center lo xyz, 0}), 128-bit fixed-point
 //          block weights and coordinate sums, ordered-key bounding boxes.
+//   per group of 32 consecutive centers, double-buffered like cdata2 (gdata2, 2 float4):
+//          {box mid xyz, smallest g32}, {box half extents xyz, largest g32}.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -29,11 +33,16 @@ constexpr int kTile = 256;          // points per tile (one warp of the assign k
 constexpr int kSuperTiles = 16;     // tiles per supertile (one CTA of the filter kernel)
 constexpr int kCap = 128;           // candidate centers stored per tile
 constexpr int kFastCands = 32;      // candidates brought in with the tile's bulk copy
+constexpr int kCoopCands = 64;      // tiles with more candidates are taken by a whole CTA
 constexpr int kRecF4 = 2 + 2 * kCap;  // float4 per tile record (header + candidates)
 constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // bytes of one bulk copy
 constexpr int kKThreads = 32;       // threads per CTA of the k-sized kernels
 constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
-constexpr int kCenterChunk = 1024;  // centers staged in shared memory per bulk copy
+constexpr int kGroup = 32;          // centers per group record (one CTA of the k-sized kernels)
+constexpr int kGroupCap = 1024;     // group records held in shared memory by the filter
+constexpr int kQueues = 8;          // interleaved tile queues of the assignment
+constexpr int kQueueStride = 32;    // one 128-byte line per queue counter
+static_assert(kGroup == kKThreads, "a group record is written by one CTA of the k-sized kernels");
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
 constexpr int kStripes = 64;        // striped counters for per-pass statistics
 constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers
@@ -64,8 +73,8 @@ struct Ctl {
     int iused_sel;                          // buffer the last assignment was computed with
     int gshift;                             // g32 = g * 2^-gshift
     unsigned int done_count;                // last-block-done counter (reset by the last block)
-    unsigned int tile_ctr;                  // next tile of the assignment pass (reset by the filter)
     unsigned int heavy_cnt;                 // tiles in the heavy list (reset before each filter)
+    unsigned int coop_cnt;                  // tiles in the cooperative list (same)
     int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
     double max_delta;
@@ -81,6 +90,7 @@ struct Ctl {
     unsigned long long assign_ns;           // sum of assign launch durations (globaltimer)
     unsigned long long assign_cnt;          // assign launches measured
     unsigned long long cand_stripes[kStripes];  // sum over tiles and passes of candidates x points
+    alignas(128) unsigned int tile_q[kQueues * kQueueStride];  // assignment queues (reset by the filter)
 };
 
 // Problem descriptor passed by value to every kernel.
@@ -118,6 +128,8 @@ struct Prob {
     unsigned long long *SXfix;  // 2 per (block, axis)
     unsigned long long *BBlo, *BBhi;  // per (block, axis) ordered keys (input precision)
     float4 *cdata2;             // 2 buffers x 2 float4 per block
+    float4 *gdata2;             // 2 buffers x 2 float4 per group of kGroup blocks
+    int ngroups;
     Ctl *ctl;
 };
 

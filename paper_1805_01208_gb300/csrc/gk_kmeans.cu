@@ -50,6 +50,47 @@ __device__ __forceinline__ float scaled_g32(double g, int gshift) {
     return __double2float_rn(ldexp(g, -gshift));
 }
 
+// Record of the group of kGroup consecutive centers handled by this CTA (called by all
+// of its threads; lanes without a center pass valid = false): the box of the centers'
+// FP32 frame coordinates, rounded outwards and widened by 8 u R (the lo parts and the
+// rounding of the tests that use it), and the range of their g32.  A NaN g32 widens
+// the range to [0, inf], so the group is never pruned.
+__device__ __forceinline__ void write_group(const Prob &p, float4 *gd, bool valid, const float hi[3],
+                                            float g32) {
+    float mn[3], mx[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        mn[j] = valid ? hi[j] : INFINITY;
+        mx[j] = valid ? hi[j] : -INFINITY;
+    }
+    float gmn = valid ? g32 : INFINITY, gmx = valid ? g32 : 0.0f;
+    const bool nan = __any_sync(0xffffffffu, valid && isnan(g32));
+    for (int off = 16; off; off >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mn[j] = fminf(mn[j], __shfl_xor_sync(0xffffffffu, mn[j], off));
+            mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], off));
+        }
+        gmn = fminf(gmn, __shfl_xor_sync(0xffffffffu, gmn, off));
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, off));
+    }
+    if (threadIdx.x == 0) {
+        if (nan) {
+            gmn = 0.0f;
+            gmx = INFINITY;
+        }
+        const float wide = 8.0f * 5.9604644775390625e-8f * p.R;
+        float mid[3], half[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mid[j] = 0.5f * mn[j] + 0.5f * mx[j];
+            half[j] = __fadd_ru(fmaxf(__fsub_ru(mx[j], mid[j]), __fsub_ru(mid[j], mn[j])), wide);
+        }
+        gd[2 * blockIdx.x] = make_float4(mid[0], mid[1], mid[2], gmn);
+        gd[2 * blockIdx.x + 1] = make_float4(half[0], half[1], half[2], gmx);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T block_reduce_max(T v, T *red) {  // all threads get the result
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -117,6 +158,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->maxd_key = 0ull;
         ctl->nonempty = 0;
         ctl->heavy_cnt = 0u;
+        ctl->coop_cnt = 0u;
         if (h_move) cudaGraphSetConditional(h_move, 1u);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
@@ -125,7 +167,15 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
 __global__ void __launch_bounds__(kKThreads) init_b_kernel(Prob p) {
     count_launch(p.ctl);
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < p.k) p.cdata2[2 * c].w = scaled_g32(p.g64_2[c], p.ctl->gshift);
+    const bool valid = c < p.k;
+    float4 hc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        hc = p.cdata2[2 * c];
+        hc.w = scaled_g32(p.g64_2[c], p.ctl->gshift);
+        p.cdata2[2 * c] = hc;
+    }
+    const float hi[3] = {hc.x, hc.y, hc.z};
+    write_group(p, p.gdata2, valid, hi, hc.w);
 }
 
 __global__ void final_begin_kernel(Prob p, cudaGraphConditionalHandle h_fin) {
@@ -150,10 +200,15 @@ __global__ void export_kernel(Prob p) {
 // Every point of B has effective distance <= tau to its best center, so c can only
 // win if LB_c <= tau.  Boxes are widened by 4 u R and tau by 64 u so that FP32
 // rounding of points, centers and this arithmetic never drops the FP64 winner;
-// comparisons are written so that a NaN keeps the center.  Level 1: the supertile
-// box against all centers (staged in shared memory by bulk copies).  Level 2: each
-// warp takes one tile of the supertile against the level-1 list and writes the
-// tile's coefficient table in ascending center order.
+// comparisons are written so that a NaN keeps the center.
+//
+// Persistent CTAs of kSuperTiles warps take supertiles in turn.  Level 1: the
+// supertile box against the group records (box of 32 consecutive centers and their
+// g range): a group whose lower bound exceeds the smallest group upper bound holds
+// no center that passes the test below, nor the center that attains tau; then tau
+// and the supertile's candidate list from the centers of the remaining groups.
+// Level 2: each warp takes one tile of the supertile against that list and writes the
+// tile's record in ascending center order.
 // ------------------------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void box_bounds(const float4 &ch, const float4 &cl, const float o[3],
@@ -173,202 +228,249 @@ __device__ __forceinline__ void box_bounds(const float4 &ch, const float4 &cl, c
     ub = ch.w * su;
 }
 
+// The same bounds for a group record {mid, gmin}, {half, gmax}: LB with the smallest
+// g and the box-to-box minimum distance, UB with the largest g and the maximum one.
+template <int D>
+__device__ __forceinline__ void group_bounds(const float4 &gm, const float4 &gh, const float o[3],
+                                             const float h[3], float &lb, float &ub) {
+    float sl = 0.f, su = 0.f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        float mj = j == 0 ? gm.x : (j == 1 ? gm.y : gm.z);
+        float hj = j == 0 ? gh.x : (j == 1 ? gh.y : gh.z);
+        float a = fabsf(mj - o[j]);
+        float hs = __fadd_ru(h[j], hj);
+        float l = fmaxf(a - hs, 0.0f);
+        float u = a + hs;
+        sl = fmaf(l, l, sl);
+        su = fmaf(u, u, su);
+    }
+    lb = gm.w * sl;
+    ub = gh.w * su;
+}
+
+
+static size_t filter_smem_bytes(const Prob &p) {
+    const size_t ngs = p.ngroups <= kGroupCap ? (size_t)p.ngroups : 0;
+    return (2 * ngs + 2 * (size_t)kSuperCap) * 16 + (size_t)(kSuperCap + kGroupCap) * 4;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     count_launch(p.ctl);
-    __shared__ __align__(128) float4 sc[2 * kCenterChunk];
-    __shared__ int slist[kSuperCap];
-    __shared__ float s_red[kSuperTiles];
-    __shared__ float s_gred[kSuperTiles];
+    extern __shared__ __align__(16) float4 fsm[];
+    __shared__ float s_tg[kSuperTiles], s_ga[kSuperTiles], s_tc[kSuperTiles];
     __shared__ int s_wcnt[kSuperTiles];
-    __shared__ __align__(8) unsigned long long bar;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int s = blockIdx.x;
     const int sel = p.ctl->isel;
+    const int ng = p.ngroups;
     const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float4 *gsrc = p.gdata2 + (size_t)sel * 2 * ng;
+    const bool gstaged = ng <= kGroupCap;
+    float4 *sc = fsm + (gstaged ? 2 * ng : 0);  // level-1 list: {hi, g}, {lo, -}
+    int *slist = reinterpret_cast<int *>(sc + 2 * kSuperCap);
+    int *glist = slist + kSuperCap;
+    const float4 *G = gstaged ? fsm : gsrc;
     const float infl = 4.0f * kU * p.R;
-    if (s == 0 && tid == 0) p.ctl->tile_ctr = 0u;  // tile queue of the assignment that follows
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbarrier_init();
-    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (blockIdx.x == 0 && tid < kQueues) p.ctl->tile_q[tid * kQueueStride] = 0u;  // queues of the next assignment
+    if (gstaged)
+        for (int i = tid; i < 2 * ng; i += kFilterThreads) fsm[i] = gsrc[i];
     __syncthreads();
-    float so[3], sh[3];
-    {
-        float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
-        so[0] = a.x;
-        so[1] = a.y;
-        so[2] = a.z;
-        sh[0] = __fadd_ru(b.x, infl);
-        sh[1] = __fadd_ru(b.y, infl);
-        sh[2] = __fadd_ru(b.z, infl);
-    }
-    const int nch = (p.k + kCenterChunk - 1) / kCenterChunk;
-    unsigned phase = 0;
-    auto stage = [&](int ch) -> bool {
-        int cb = ch * kCenterChunk;
-        int m = min(kCenterChunk, p.k - cb);
-        if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(&bar, (unsigned)(m * 32));
-            bulk_g2s(sc, cd + 2 * (size_t)cb, (unsigned)(m * 32), &bar);
+    // ascending compaction over the CTA: returns the position of this thread's entry
+    // and advances the running count (two barriers)
+    auto compact = [&](bool keep, int &count) -> int {
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) s_wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kSuperTiles; ++w2) {
+            const int v = s_wcnt[w2];
+            before += w2 < warp ? v : 0;
+            total += v;
         }
-        bool ok = mbar_wait_bounded(&bar, phase);
-        phase ^= 1u;
-        return !__syncthreads_or(!ok);
+        const int pos = count + before + __popc(bal & lt);
+        count += total;
+        return pos;
     };
-    bool failed = false;
-    // level 1, sweep 1: tau of the supertile (and the largest g of all centers)
-    float tau = INFINITY, gall = 0.0f;
-    for (int ch = 0; ch < nch; ++ch) {
-        if (!stage(ch)) {
-            failed = true;
-            break;
+    for (int s = blockIdx.x; s < p.nsupers; s += gridDim.x) {
+        float so[3], sh[3];
+        {
+            const float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
+            so[0] = a.x;
+            so[1] = a.y;
+            so[2] = a.z;
+            sh[0] = __fadd_ru(b.x, infl);
+            sh[1] = __fadd_ru(b.y, infl);
+            sh[2] = __fadd_ru(b.z, infl);
         }
-        int m = min(kCenterChunk, p.k - ch * kCenterChunk);
-        for (int c = tid; c < m; c += kFilterThreads) {
+        // groups: upper bound of tau, and the largest g of all centers
+        float tg = INFINITY, gall = 0.0f;
+        for (int gi = tid; gi < ng; gi += kFilterThreads) {
+            const float4 gm = G[2 * gi], gh = G[2 * gi + 1];
             float lb, ub;
-            box_bounds<D>(sc[2 * c], sc[2 * c + 1], so, sh, lb, ub);
-            tau = fminf(tau, ub);
-            gall = fmaxf(gall, sc[2 * c].w);
+            group_bounds<D>(gm, gh, so, sh, lb, ub);
+            tg = fminf(tg, ub);
+            gall = fmaxf(gall, gh.w);
+        }
+        for (int off = 16; off; off >>= 1) {
+            tg = fminf(tg, __shfl_xor_sync(0xffffffffu, tg, off));
+            gall = fmaxf(gall, __shfl_xor_sync(0xffffffffu, gall, off));
+        }
+        if (lane == 0) {
+            s_tg[warp] = tg;
+            s_ga[warp] = gall;
         }
         __syncthreads();
-    }
-    for (int off = 16; off; off >>= 1) {
-        tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, off));
-        gall = fmaxf(gall, __shfl_xor_sync(0xffffffffu, gall, off));
-    }
-    if (lane == 0) {
-        s_red[warp] = tau;
-        s_gred[warp] = gall;
-    }
-    __syncthreads();
-    tau = s_red[0];
-    gall = s_gred[0];
-    for (int w = 1; w < kSuperTiles; ++w) {
-        tau = fminf(tau, s_red[w]);
-        gall = fmaxf(gall, s_gred[w]);
-    }
-    const float tauS = __fmul_ru(tau, 1.0f + 64.0f * kU);
-    // level 1, sweep 2: ascending list of the supertile's candidates
-    int count = 0;
-    const unsigned lt = (1u << lane) - 1u;
-    for (int ch = 0; ch < nch && !failed; ++ch) {
-        if (nch > 1 && !stage(ch)) {
-            failed = true;
-            break;
+        tg = s_tg[0];
+        gall = s_ga[0];
+#pragma unroll
+        for (int w2 = 1; w2 < kSuperTiles; ++w2) {
+            tg = fminf(tg, s_tg[w2]);
+            gall = fmaxf(gall, s_ga[w2]);
         }
-        int cb = ch * kCenterChunk;
-        int m = min(kCenterChunk, p.k - cb);
-        for (int base = 0; base < m; base += kFilterThreads) {
-            int c = base + tid;
+        const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
+        int ngk = 0;  // kept groups, ascending
+        for (int base = 0; base < ng; base += kFilterThreads) {
+            const int gi = base + tid;
             bool keep = false;
-            if (c < m) {
+            if (gi < ng) {
                 float lb, ub;
-                box_bounds<D>(sc[2 * c], sc[2 * c + 1], so, sh, lb, ub);
-                keep = !(lb > tauS);
+                group_bounds<D>(G[2 * gi], G[2 * gi + 1], so, sh, lb, ub);
+                keep = !(lb > tauG);
             }
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0) s_wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int before = 0, total = 0;
-            for (int w = 0; w < kSuperTiles; ++w) {
-                int v = s_wcnt[w];
-                before += w < warp ? v : 0;
-                total += v;
-            }
-            int pos = count + before + __popc(bal & lt);
-            if (keep && pos < kSuperCap) slist[pos] = cb + c;
-            count += total;
+            const int pos = compact(keep, ngk);
+            if (keep && pos < kGroupCap) glist[pos] = gi;
             __syncthreads();
         }
-    }
-    const int t = s * kSuperTiles + warp;
-    if (failed) {
-        // A bulk copy did not complete in time: record it, let the assignment scan
-        // every center for these tiles, and wait (bounded) for the copy in flight.
-        if (tid == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
-        if (t < p.ntiles && lane == 0) {
-            p.trec[(size_t)t * kRecF4] = make_float4(__int_as_float(-1), INFINITY, 0.f, 0.f);
-            p.trec[(size_t)t * kRecF4 + 1] = p.tiles[2 * t];
-            p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
+        const bool gover = ngk > kGroupCap;  // too many groups: every center goes to level 2
+        // tau of the supertile over the centers of the kept groups (one warp per group)
+        float tc = INFINITY;
+        if (!gover) {
+            for (int i = warp; i < ngk; i += kSuperTiles) {
+                const int c = glist[i] * kGroup + lane;
+                if (c < p.k) {
+                    float lb, ub;
+                    box_bounds<D>(cd[2 * c], cd[2 * c + 1], so, sh, lb, ub);
+                    tc = fminf(tc, ub);
+                }
+            }
         }
-        mbar_wait_bounded(&bar, phase ^ 1u);
-        return;
-    }
-    const bool all = count > kSuperCap;
-    const int L = all ? p.k : count;
-    const bool in_smem = nch == 1;
-    if (t >= p.ntiles) return;
-    float o[3], h[3];
-    {
-        float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
-        o[0] = a.x;
-        o[1] = a.y;
-        o[2] = a.z;
-        h[0] = __fadd_ru(b.x, infl);
-        h[1] = __fadd_ru(b.y, infl);
-        h[2] = __fadd_ru(b.z, infl);
-    }
-    auto center = [&](int i, int &c, float4 &ch, float4 &cl) {
-        c = all ? i : slist[i];
-        if (in_smem) {
-            ch = sc[2 * c];
-            cl = sc[2 * c + 1];
-        } else {
-            ch = cd[2 * c];
-            cl = cd[2 * c + 1];
+        for (int off = 16; off; off >>= 1) tc = fminf(tc, __shfl_xor_sync(0xffffffffu, tc, off));
+        if (lane == 0) s_tc[warp] = tc;
+        __syncthreads();
+        tc = s_tc[0];
+#pragma unroll
+        for (int w2 = 1; w2 < kSuperTiles; ++w2) tc = fminf(tc, s_tc[w2]);
+        const float tauS = __fmul_ru(tc, 1.0f + 64.0f * kU);
+        // level-1 list, ascending (kept groups in order, one warp per group per round)
+        int count = gover ? kSuperCap + 1 : 0;
+        if (!gover) {
+            for (int base = 0; base < ngk; base += kSuperTiles) {
+                const int i = base + warp;
+                bool keep = false;
+                int c = 0;
+                float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+                if (i < ngk) {
+                    c = glist[i] * kGroup + lane;
+                    if (c < p.k) {
+                        ch = cd[2 * c];
+                        cl = cd[2 * c + 1];
+                        float lb, ub;
+                        box_bounds<D>(ch, cl, so, sh, lb, ub);
+                        keep = !(lb > tauS);
+                    }
+                }
+                const int pos = compact(keep, count);
+                if (keep && pos < kSuperCap) {
+                    slist[pos] = c;
+                    sc[2 * pos] = ch;
+                    sc[2 * pos + 1] = cl;
+                }
+                __syncthreads();
+            }
         }
-    };
-    float tt = INFINITY;
-    for (int i = lane; i < L; i += 32) {
-        int c;
-        float4 ch, cl;
-        center(i, c, ch, cl);
-        float lb, ub;
-        box_bounds<D>(ch, cl, o, h, lb, ub);
-        tt = fminf(tt, ub);
-    }
-    for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
-    const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
-    int cnt = 0;
-    float gkept = 0.0f;
-    float4 *rec = p.trec + (size_t)t * kRecF4;
-    for (int base = 0; base < L; base += 32) {
-        int i = base + lane;
-        bool keep = false;
-        int c = 0;
-        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
-        if (i < L) {
-            center(i, c, ch, cl);
-            float lb, ub;
-            box_bounds<D>(ch, cl, o, h, lb, ub);
-            keep = !(lb > tauT);
+        const bool all = count > kSuperCap;
+        const int L = all ? p.k : count;
+        const int t = s * kSuperTiles + warp;
+        if (t < p.ntiles) {
+            float o[3], h[3];
+            {
+                const float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
+                o[0] = a.x;
+                o[1] = a.y;
+                o[2] = a.z;
+                h[0] = __fadd_ru(b.x, infl);
+                h[1] = __fadd_ru(b.y, infl);
+                h[2] = __fadd_ru(b.z, infl);
+            }
+            auto center = [&](int i, int &c, float4 &ch, float4 &cl) {
+                if (all) {
+                    c = i;
+                    ch = cd[2 * c];
+                    cl = cd[2 * c + 1];
+                } else {
+                    c = slist[i];
+                    ch = sc[2 * i];
+                    cl = sc[2 * i + 1];
+                }
+            };
+            float tt = INFINITY;
+            for (int i = lane; i < L; i += 32) {
+                int c;
+                float4 ch, cl;
+                center(i, c, ch, cl);
+                float lb, ub;
+                box_bounds<D>(ch, cl, o, h, lb, ub);
+                tt = fminf(tt, ub);
+            }
+            for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
+            const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
+            int cnt = 0;
+            float gkept = 0.0f;
+            float4 *rec = p.trec + (size_t)t * kRecF4;
+            for (int base = 0; base < L; base += 32) {
+                const int i = base + lane;
+                bool keep = false;
+                int c = 0;
+                float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+                if (i < L) {
+                    center(i, c, ch, cl);
+                    float lb, ub;
+                    box_bounds<D>(ch, cl, o, h, lb, ub);
+                    keep = !(lb > tauT);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const int pos = cnt + __popc(bal & lt);
+                if (keep && pos < kCap) {
+                    const float q0 = (ch.x - o[0]) + cl.x;
+                    const float q1 = (ch.y - o[1]) + cl.y;
+                    const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+                    rec[2 + 2 * pos] = make_float4(q0, q1, q2, ch.w);
+                    rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                }
+                if (keep) gkept = fmaxf(gkept, ch.w);
+                cnt += __popc(bal);
+            }
+            for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
+            if (lane == 0) {
+                const bool over = cnt > kCap;
+                // header: count (-1: scan all centers) and the largest g the tile can meet
+                rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
+                rec[1] = p.tiles[2 * t];
+                if (over || cnt > kCoopCands)
+                    p.heavy[p.ntiles - 1 - (int)atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
+                else if (cnt > kFastCands)
+                    p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
+                if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
+                long long nv = p.n - (long long)t * kTile;
+                nv = nv > kTile ? kTile : nv;
+                const unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
+                atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
+            }
         }
-        unsigned bal = __ballot_sync(0xffffffffu, keep);
-        int pos = cnt + __popc(bal & lt);
-        if (keep && pos < kCap) {
-            float q0 = (ch.x - o[0]) + cl.x;
-            float q1 = (ch.y - o[1]) + cl.y;
-            float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-            rec[2 + 2 * pos] = make_float4(q0, q1, q2, ch.w);
-            rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
-        }
-        if (keep) gkept = fmaxf(gkept, ch.w);
-        cnt += __popc(bal);
-    }
-    for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
-    if (lane == 0) {
-        bool over = cnt > kCap;
-        // header: count (-1: scan all centers) and the largest g the tile can meet
-        rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
-        rec[1] = p.tiles[2 * t];
-        if (over || cnt > kFastCands) p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
-        if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
-        long long nv = p.n - (long long)t * kTile;
-        nv = nv > kTile ? kTile : nv;
-        unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
-        atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
+        __syncthreads();  // the next supertile rewrites the lists
     }
 }
 
@@ -422,16 +524,277 @@ __device__ __forceinline__ void argmin_update(float E, int c, float &E1, float &
     E1 = lt ? E : E1;
 }
 
-// Persistent warps: warp gw of TW takes tiles gw, gw + TW, ...  Each warp owns two
-// shared-memory stages; one lane issues the bulk copies (tile record with its first
-// kFastCands candidates, and the d coordinate planes of the tile) for the tile after
-// next as soon as a stage is consumed, so the loads of two tiles are always in flight.
+// Error-bound terms of the FP64-mode certification (see the comment above): the
+// bound on |E_fp32 - E_exact| for a point whose coordinate term is e0, against
+// candidates with g <= glv (sgl = sqrt(glv)), at the FP32 value Eref.
+__device__ __forceinline__ float cert_bound(float e0, float sgl, float glv, float beta2, float Eref) {
+    const float beta1 = 2.0f * sgl * e0;
+    const float beta0 = glv * e0 * e0;
+    const float Estar = 2.0f * Eref + 2.0f * (beta0 + 2.0f * beta1 * beta1);
+    return 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
+}
+
+// Block weights of one tile's assignment: runs inside the lane, then a segmented
+// reduction over lanes (unit weights: 64-bit counts; weights: 128-bit fixed point).
+__device__ __forceinline__ void tile_histogram(const Prob &p, long long i0, int nval, const int best[8]) {
+    int cur = -1;
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        if (q < nval) {
+            unsigned long long v = 1ull;
+            if (p.weighted)
+                v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
+                                                      : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
+            if (best[q] != cur) {
+                if (cur >= 0) {
+                    if (p.weighted)
+                        atomic_add_u128(&p.Sfix[2 * cur], acc);
+                    else
+                        atomicAdd(&p.Sfix[2 * cur], acc);
+                }
+                cur = best[q];
+                acc = 0;
+            }
+            acc += v;
+        }
+    }
+    seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
+}
+
+// ------------------------------------------------------------------------------
+// Cooperative tile: a tile with more candidates than one warp finishes in the time
+// the others take (more than kCoopCands, or all k centers when its list overflowed)
+// is taken by all kAWarps warps of a CTA.  Warp w evaluates the w-th contiguous
+// range of the candidates (ascending centers) for all points of the tile; the
+// per-warp (E1, E2, best) are merged in shared memory in ascending range order,
+// which keeps the lowest center index on ties.  Warp 0 then certifies (FP64 mode),
+// re-decides the flagged points over all candidates, writes the block ids and adds
+// the block weights.  Called by every thread of the CTA; scratch holds at least
+// 3 * kAWarps * kTile words.
+// ------------------------------------------------------------------------------
+template <int D, bool F64MODE>
+__device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int nwarps,
+                                       unsigned long long *nre) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float4 *grec = p.trec + (size_t)t * kRecF4;
+    const float4 hdr = grec[0], ob = grec[1];
+    const int cnt = __float_as_int(hdr.x);
+    const bool all = cnt < 0;
+    const int ncand = all ? p.k : cnt;
+    const float o[3] = {ob.x, ob.y, ob.z};
+    const float4 *cd = p.cdata2 + (size_t)p.ctl->isel * 2 * p.k;
+    const long long i0 = (long long)t * kTile + lane * 8;
+    const long long nv = p.n - i0;
+    const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+    float2 xp[3][4];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xp[j][q] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const float4 *src = reinterpret_cast<const float4 *>(p.X32 + (size_t)j * p.n_pad + i0);
+        const float4 a = src[0], c4 = src[1];
+        xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
+        xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
+        xp[j][2] = make_float2(c4.x - o[j], c4.y - o[j]);
+        xp[j][3] = make_float2(c4.z - o[j], c4.w - o[j]);
+    }
+    auto cand = [&](int jj, float4 &qg, int &c) {  // jj < ncand
+        if (!all) {
+            qg = grec[2 + 2 * jj];
+            c = __float_as_int(grec[3 + 2 * jj].x);
+        } else {
+            c = jj;
+            const float4 ch = cd[2 * c], cl = cd[2 * c + 1];
+            qg = make_float4((ch.x - o[0]) + cl.x, (ch.y - o[1]) + cl.y,
+                             D == 3 ? (ch.z - o[2]) + cl.z : 0.0f, ch.w);
+        }
+    };
+    float E1[8], E2[8];
+    int best[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        E1[q] = INFINITY;
+        E2[q] = INFINITY;
+        best[q] = 0;
+    }
+    const int rb = (int)((long long)ncand * w / nwarps), re = (int)((long long)ncand * (w + 1) / nwarps);
+    for (int base = rb; base < re; base += 32) {
+        float4 mqg = make_float4(0.f, 0.f, 0.f, 0.f);
+        int mc = 0;
+        if (base + lane < re) cand(base + lane, mqg, mc);
+        const int m = min(32, re - base);
+        for (int jj = 0; jj < m; ++jj) {
+            const float2 g2 = make_float2(__shfl_sync(0xffffffffu, mqg.w, jj), 0.f);
+            const float qx = __shfl_sync(0xffffffffu, mqg.x, jj), qy = __shfl_sync(0xffffffffu, mqg.y, jj);
+            const float qz = __shfl_sync(0xffffffffu, mqg.z, jj);
+            const int c = __shfl_sync(0xffffffffu, mc, jj);
+            const float2 gg = make_float2(g2.x, g2.x), nqx = make_float2(-qx, -qx), nqy = make_float2(-qy, -qy),
+                         nqz = make_float2(-qz, -qz);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 dx = __fadd2_rn(xp[0][q], nqx);
+                const float2 dy = __fadd2_rn(xp[1][q], nqy);
+                float2 ss = __fmul2_rn(dx, dx);
+                ss = __ffma2_rn(dy, dy, ss);
+                if (D == 3) {
+                    const float2 dz = __fadd2_rn(xp[2][q], nqz);
+                    ss = __ffma2_rn(dz, dz, ss);
+                }
+                const float2 E = __fmul2_rn(gg, ss);
+                argmin_update<true>(E.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
+                argmin_update<true>(E.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
+            }
+        }
+    }
+    // partials to shared memory: [warp][lane][q] of E1, E2, best
+    float *sE1 = scratch, *sE2 = scratch + nwarps * kTile;
+    int *sB = reinterpret_cast<int *>(scratch + 2 * nwarps * kTile);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int idx = w * kTile + q * 32 + lane;
+        sE1[idx] = E1[q];
+        sE2[idx] = E2[q];
+        sB[idx] = best[q];
+    }
+    __syncthreads();
+    if (w == 0) {
+        for (int w2 = 1; w2 < nwarps; ++w2) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int idx = w2 * kTile + q * 32 + lane;
+                const float e1 = sE1[idx], e2 = sE2[idx];
+                if (e1 < E1[q]) {  // a later range wins only when strictly smaller
+                    E2[q] = fminf(E1[q], e2);
+                    E1[q] = e1;
+                    best[q] = sB[idx];
+                } else {
+                    E2[q] = fminf(E2[q], e1);
+                }
+            }
+        }
+        if (F64MODE) {
+            const float gl = hdr.y, sg = sqrtf(gl);
+            const float R = p.R, sd = sqrtf((float)D);
+            const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
+            float xn2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
+                xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
+            }
+            const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
+            unsigned flag = 0;
+            float thr[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
+                const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
+                const bool okq = single || (E2[q] - E1[q]) > 2.0f * B;
+                thr[q] = E1[q] + 2.0f * B;
+                if (q < nval && !okq) flag |= 1u << q;
+            }
+            // FP64 re-decision, one flagged point at a time: lanes take 32 candidates at
+            // a time, screen them with the FP32 value (every possible FP64 winner has
+            // E_fp32 <= thr) and evaluate the survivors in FP64; the warp keeps the
+            // smallest value, the lowest center index on ties.
+            const double *g64 = p.g64_2 + (size_t)p.ctl->isel * p.k;
+            unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
+            while (lanes) {
+                const int L = __ffs(lanes) - 1;
+                lanes &= lanes - 1;
+                unsigned fl = __shfl_sync(0xffffffffu, flag, L);
+                while (fl) {
+                    const int q = __ffs(fl) - 1;
+                    fl &= fl - 1;
+                    float mx[3] = {0.f, 0.f, 0.f}, mt = 0.f;
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        if (qq == q) {
+#pragma unroll
+                            for (int j = 0; j < D; ++j) mx[j] = (qq & 1) ? xp[j][qq >> 1].y : xp[j][qq >> 1].x;
+                            mt = thr[qq];
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, mx[j], L);
+                    mt = __shfl_sync(0xffffffffu, mt, L);
+                    const long long ip = (long long)t * kTile + L * 8 + q;
+                    double X[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+                    for (int j = 0; j < D; ++j)
+                        X[j] = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip] : (double)p.X32[(size_t)j * p.n_pad + ip];
+                    double bE = INFINITY;
+                    int bc = 0x7fffffff;
+                    for (int base = 0; base < ncand; base += 32) {
+                        float4 qg;
+                        int c = 0x7fffffff;
+                        double E = INFINITY;
+                        if (base + lane < ncand) {
+                            cand(base + lane, qg, c);
+                            const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
+                            const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
+                            const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                            if (E32 <= mt) {
+                                double s2 = 0.0;
+#pragma unroll
+                                for (int j = 0; j < D; ++j) {
+                                    const double df = X[j] - p.C[c * D + j];
+                                    s2 += df * df;
+                                }
+                                E = s2 * g64[c];
+                            }
+                        }
+                        if (E < bE || (E == bE && c < bc)) {
+                            bE = E;
+                            bc = c;
+                        }
+                    }
+                    for (int off = 16; off; off >>= 1) {
+                        const double oE = __shfl_xor_sync(0xffffffffu, bE, off);
+                        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                        if (oE < bE || (oE == bE && oc < bc)) {
+                            bE = oE;
+                            bc = oc;
+                        }
+                    }
+                    if (lane == L && bc != 0x7fffffff) {
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq)
+                            if (qq == q) best[qq] = bc;
+                    }
+                }
+            }
+            *nre += __popc(flag);
+        }
+        if (nval == 8) {
+            int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+            dst[0] = make_int4(best[0], best[1], best[2], best[3]);
+            dst[1] = make_int4(best[4], best[5], best[6], best[7]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < nval) p.A[i0 + q] = best[q];
+        }
+        tile_histogram(p, i0, nval, best);
+    }
+}
+
+// Persistent warps take tiles from shared queues.  Each warp owns two shared-memory
+// stages; one lane issues the bulk copies (tile record with its first kFastCands
+// candidates, and the d coordinate planes of the tile) for the tile after next as
+// soon as a stage is consumed, so the loads of two tiles are always in flight.
 constexpr int kAWarps = 4;
 constexpr int kAMinBlocks = 5;
 struct AStage {
     float4 rec[2 + 2 * kFastCands];
     float x[3][kTile];
 };
+static_assert(sizeof(AStage) * 2 * kAWarps >= 3 * kAWarps * kTile * 4, "scratch of the cooperative tiles");
 
 template <int D, bool F64MODE>
 __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob p) {
@@ -449,6 +812,16 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
     const int sel = p.ctl->isel;
     const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
     const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4);
+    unsigned long long nre = 0;
+    {
+        // cooperative tiles first (the stages serve as scratch; no copy is in flight yet)
+        const int HC = (int)p.ctl->coop_cnt;
+        float *scratch = reinterpret_cast<float *>(&st[0][0]);
+        for (int ci = blockIdx.x; ci < HC; ci += gridDim.x) {
+            coop_tile<D, F64MODE>(p, p.heavy[p.ntiles - 1 - ci], scratch, kAWarps, &nre);
+            __syncthreads();
+        }
+    }
     auto issue = [&](int t, int b) {
         if (lane == 0) {
             fence_proxy_async();
@@ -459,37 +832,52 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
                          &bar[w][b]);
         }
     };
-    // Tiles come from a queue (one atomic per tile) so that expensive tiles do not
-    // pile up on a few warps; the two stages hold the two smallest tiles taken.
-    // Positions [0, H) are the heavy tiles (slow path), served first; positions H + t
-    // are tile t, skipped there when it is heavy.  Warp gw takes positions gw, gw + TW, ...
+    // Tiles come from kQueues interleaved queues: queue q serves positions q, q + kQueues,
+    // ... (one atomic per tile, requested two tiles ahead so that its latency and the
+    // read of the heavy list are hidden).  Positions [0, H) are the heavy tiles, served
+    // first; position H + t is tile t, skipped there when it is heavy.  A warp's
+    // positions increase, so once a stage holds no tile the other one holds none either.
+    // The queue state lives in lane 0 and is broadcast when a stage is consumed.
     const int H = (int)p.ctl->heavy_cnt;
-    const int TW = gridDim.x * kAWarps;
-    int next_pos = blockIdx.x * kAWarps + w;
-    auto grab = [&](int npos) -> int {  // the warp's next npos positions (npos <= 2)
-        const int pos = next_pos;
-        next_pos += npos * TW;
-        return pos;
+    const int qi = (blockIdx.x * kAWarps + w) & (kQueues - 1);
+    unsigned *qctr = &p.ctl->tile_q[qi * kQueueStride];
+    // a queued tile: index in bits 0..29 (ntiles when the queue is empty), bit 30 set
+    // when it came from the heavy range
+    constexpr int kHv = 1 << 30;
+    auto resolve = [&](unsigned m) -> int {  // lane 0
+        const long long pos = (long long)qi + (long long)kQueues * m;
+        if (pos < H) return p.heavy[pos] | kHv;
+        return pos - H < (long long)p.ntiles ? (int)(pos - H) : p.ntiles;
     };
-    auto tile_at = [&](int pos) -> int {
-        if (pos < H) {
-            int t = 0;
-            if (lane == 0) t = p.heavy[pos];
-            return __shfl_sync(0xffffffffu, t, 0);
+    int tq0 = p.ntiles, tq1 = p.ntiles, t_next = p.ntiles;
+    unsigned m_req = 0;
+    if (lane == 0) {
+        const unsigned m0 = atomicAdd(qctr, 1u), m1 = atomicAdd(qctr, 1u), m2 = atomicAdd(qctr, 1u);
+        m_req = atomicAdd(qctr, 1u);
+        tq0 = resolve(m0);
+        tq1 = resolve(m1);
+        t_next = resolve(m2);
+        if ((tq0 & (kHv - 1)) < p.ntiles) issue(tq0 & (kHv - 1), 0);
+        if ((tq1 & (kHv - 1)) < p.ntiles) issue(tq1 & (kHv - 1), 1);
+    }
+    // stage b is free again: load the next tile into it (lane 0)
+    auto refill = [&](int b) {
+        if (lane == 0) {
+            if (b)
+                tq1 = t_next;
+            else
+                tq0 = t_next;
+            if ((t_next & (kHv - 1)) < p.ntiles) issue(t_next & (kHv - 1), b);
+            t_next = resolve(m_req);
+            m_req = atomicAdd(qctr, 1u);
         }
-        return pos - H;  // >= ntiles: the queue is empty
     };
-    const int pos0 = grab(1), pos1 = grab(1);
-    int tq0 = tile_at(pos0), tq1 = tile_at(pos1);
-    int hv0 = pos0 < H, hv1 = pos1 < H;
-    if (tq0 < p.ntiles) issue(tq0, 0);
-    if (tq1 < p.ntiles) issue(tq1, 1);
     unsigned ph0 = 0, ph1 = 0;
-    unsigned long long nre = 0;
     for (int it = 0;; ++it) {
         const int b = it & 1;
-        const int t = b ? tq1 : tq0;
-        if (t >= p.ntiles) break;  // the other stage holds a larger index
+        const int tqb = __shfl_sync(0xffffffffu, b ? tq1 : tq0, 0);
+        const int t = tqb & (kHv - 1);
+        if (t >= p.ntiles) break;  // the other stage holds no tile either
         const unsigned phb = b ? ph1 : ph0;
         bool ok = mbar_wait_bounded(&bar[w][b], phb);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -497,20 +885,18 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
             // bounded wait for the copies still in flight (this stage and the other).
             if (lane == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
             mbar_wait_bounded(&bar[w][b], phb);
-            if ((b ? tq0 : tq1) < p.ntiles) mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
+            if ((__shfl_sync(0xffffffffu, b ? tq0 : tq1, 0) & (kHv - 1)) < p.ntiles)
+                mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
             return;
         }
         if (b) ph1 ^= 1u; else ph0 ^= 1u;
         const AStage &S = st[w][b];
         const int cnt = __float_as_int(S.rec[0].x);
-        const bool from_heavy = b ? hv1 : hv0;
+        const bool from_heavy = (tqb & kHv) != 0;
         if (!from_heavy && (cnt < 0 || cnt > kFastCands)) {
             // a heavy tile met again in the ordinary range: already done; take the next
             __syncwarp();
-            const int np = grab(1);
-            const int nt = tile_at(np);
-            if (b) { tq1 = nt; hv1 = np < H; } else { tq0 = nt; hv0 = np < H; }
-            if (nt < p.ntiles) issue(nt, b);
+            refill(b);
             continue;
         }
         const float gl = S.rec[0].y;  // largest g among the tile's candidates
@@ -604,10 +990,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
         const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
         auto point_bound = [&](int q, float sgl, float glv, float Eref) -> float {
             (void)q;
-            const float beta1 = 2.0f * sgl * e0;
-            const float beta0 = glv * e0 * e0;
-            const float Estar = 2.0f * Eref + 2.0f * (beta0 + 2.0f * beta1 * beta1);
-            return 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
+            return cert_bound(e0, sgl, glv, beta2, Eref);
         };
         // 64-point sub-boxes (lanes 8s..8s+7) in tile-local coordinates, widened so that
         // they contain the exact points
@@ -812,12 +1195,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
             nre += __popc(flag);
         }
         __syncwarp();  // every lane is done with stage b
-        {
-            const int np = grab(1);
-            const int nt = tile_at(np);
-            if (b) { tq1 = nt; hv1 = np < H; } else { tq0 = nt; hv0 = np < H; }
-            if (nt < p.ntiles) issue(nt, b);
-        }
+        refill(b);
         // block ids
         if (nval == 8) {
             int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
@@ -828,30 +1206,7 @@ __global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob 
             for (int q = 0; q < 8; ++q)
                 if (q < nval) p.A[i0 + q] = best[q];
         }
-        // block weights: runs inside the lane, then a segmented reduction over lanes
-        int cur = -1;
-        unsigned long long acc = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q < nval) {
-                unsigned long long v = 1ull;
-                if (p.weighted)
-                    v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
-                                                          : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
-                if (best[q] != cur) {
-                    if (cur >= 0) {
-                        if (p.weighted)
-                            atomic_add_u128(&p.Sfix[2 * cur], acc);
-                        else
-                            atomicAdd(&p.Sfix[2 * cur], acc);
-                    }
-                    cur = best[q];
-                    acc = 0;
-                }
-                acc += v;
-            }
-        }
-        seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
+        tile_histogram(p, i0, nval, best);
     }
     if (F64MODE) {
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
@@ -897,6 +1252,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
     const double target = ctl->target;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     double S = 0.0, gnew = 0.0;
+    float4 hc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < p.k) {
         unsigned long long lo = p.Sfix[2 * c], hi = p.Sfix[2 * c + 1];
         S = p.weighted ? i128_to_f64(lo, hi, p.Fw) : (double)lo;
@@ -917,10 +1273,14 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
             gnew = 1.0 / (In * In);
             p.I2[(size_t)nsel * p.k + c] = In;
             p.g64_2[(size_t)nsel * p.k + c] = gnew;
-            float4 hc = p.cdata2[(size_t)sel * 2 * p.k + 2 * c];
+            hc = p.cdata2[(size_t)sel * 2 * p.k + 2 * c];
             hc.w = scaled_g32(gnew, gshift);
             p.cdata2[(size_t)nsel * 2 * p.k + 2 * c] = hc;
         }
+    }
+    if (mode != 2) {
+        const float hi[3] = {hc.x, hc.y, hc.z};
+        write_group(p, p.gdata2 + (size_t)nsel * 2 * p.ngroups, c < p.k, hi, hc.w);
     }
     double mS = block_reduce_max(S, red);
     double mg = block_reduce_max(gnew, red);
@@ -933,7 +1293,8 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
         ctl->maxS_key = 0ull;
         ctl->maxg_key = 0ull;
-        ctl->heavy_cnt = 0u;  // the next filter rebuilds the heavy list
+        ctl->heavy_cnt = 0u;  // the next filter rebuilds the heavy and cooperative lists
+        ctl->coop_cnt = 0u;
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
         if (mode == 2) return;
@@ -1166,33 +1527,37 @@ __global__ void __launch_bounds__(kKThreads) finalize_b_kernel(Prob p) {
     const Ctl *ctl = p.ctl;
     if (!ctl->cont_move) return;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.k) return;
+    const bool valid = c < p.k;
     const int sel = ctl->isel;
     const double beta = ctl->beta;
-    for (int j = 0; j < p.d; ++j) p.C[c * p.d + j] = p.Cm[c * p.d + j];
-    double *Ip = p.I2 + (size_t)sel * p.k;
-    double I = Ip[c];
-    if (p.erosion) {
-        double dl = p.delta[c];
-        double alpha;
-        if (beta > 0.0) {
-            double tt = fmin(-dl / beta, 0.0);
-            alpha = 2.0 / (1.0 + exp(tt)) - 1.0;
-        } else {
-            alpha = dl > 0.0 ? 1.0 : 0.0;
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3], g32 = 0.0f;
+    if (valid) {
+        for (int j = 0; j < p.d; ++j) p.C[c * p.d + j] = p.Cm[c * p.d + j];
+        double *Ip = p.I2 + (size_t)sel * p.k;
+        double I = Ip[c];
+        if (p.erosion) {
+            double dl = p.delta[c];
+            double alpha;
+            if (beta > 0.0) {
+                double tt = fmin(-dl / beta, 0.0);
+                alpha = 2.0 / (1.0 + exp(tt)) - 1.0;
+            } else {
+                alpha = dl > 0.0 ? 1.0 : 0.0;
+            }
+            I = exp((1.0 - alpha) * log(I));
+            Ip[c] = I;
         }
-        I = exp((1.0 - alpha) * log(I));
-        Ip[c] = I;
+        double g = 1.0 / (I * I);
+        p.g64_2[(size_t)sel * p.k + c] = g;
+        g32 = scaled_g32(g, ctl->gshift);
+        frame_center(p, c, hi, lo);
+        for (int b = 0; b < 2; ++b) {
+            float4 *cd = p.cdata2 + (size_t)b * 2 * p.k;
+            cd[2 * c] = make_float4(hi[0], hi[1], hi[2], b == sel ? g32 : 0.0f);
+            cd[2 * c + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+        }
     }
-    double g = 1.0 / (I * I);
-    p.g64_2[(size_t)sel * p.k + c] = g;
-    float hi[3], lo[3];
-    frame_center(p, c, hi, lo);
-    for (int b = 0; b < 2; ++b) {
-        float4 *cd = p.cdata2 + (size_t)b * 2 * p.k;
-        cd[2 * c] = make_float4(hi[0], hi[1], hi[2], b == sel ? scaled_g32(g, ctl->gshift) : 0.0f);
-        cd[2 * c + 1] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-    }
+    write_group(p, p.gdata2 + (size_t)sel * 2 * p.ngroups, valid, hi, g32);
 }
 
 // ------------------------------------------------------------------------------
@@ -1220,9 +1585,40 @@ cudaError_t launch_init(const Prob &p, cudaStream_t s) {
 }
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s) { return launch_init(p, s); }
 
+// Persistent filter: as many CTAs as fit on the device at once (at most one per
+// supertile), with the dynamic shared memory the problem needs.
+static cudaError_t filter_config(const Prob &p, dim3 &grid, size_t &smem) {
+    void *fn = filter_fn(p.d);
+    smem = filter_smem_bytes(p);
+    static void *last_fn = nullptr;
+    static size_t last_smem = 0;
+    static int last_dev = -1, last_blocks = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (fn != last_fn || smem != last_smem || dev != last_dev) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFilterThreads, smem);
+        if (e != cudaSuccess) return e;
+        last_fn = fn;
+        last_smem = smem;
+        last_dev = dev;
+        last_blocks = nb > 0 ? nb : 1;
+    }
+    long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * last_blocks;
+    grid = dim3((unsigned)(p.nsupers < cap ? p.nsupers : cap));
+    return cudaSuccess;
+}
+
 cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    return cudaLaunchKernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), args1, 0, s);
+    dim3 grid;
+    size_t smem;
+    cudaError_t e = filter_config(p, grid, smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
 }
 static int assign_grid(const Prob &p) {
     int need = (p.ntiles + kAWarps - 1) / kAWarps;
@@ -1289,14 +1685,14 @@ struct NodeAdder {
     cudaGraph_t g;
     cudaGraphNode_t last = nullptr;
     cudaError_t err = cudaSuccess;
-    void kernel(void *fn, dim3 grid, dim3 block, void **args) {
+    void kernel(void *fn, dim3 grid, dim3 block, void **args, size_t smem = 0) {
         if (err != cudaSuccess) return;
         cudaGraphNodeParams np{};
         np.type = cudaGraphNodeTypeKernel;
         np.kernel.func = fn;
         np.kernel.gridDim = grid;
         np.kernel.blockDim = block;
-        np.kernel.sharedMemBytes = 0;
+        np.kernel.sharedMemBytes = (unsigned)smem;
         np.kernel.kernelParams = args;
         cudaGraphNode_t node;
         err = cudaGraphAddNode(&node, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
@@ -1340,6 +1736,9 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     const dim3 kg(kgrid(p)), kb(kKThreads), tg(tile_warp_grid(p)), tb(kAssignWarps * 32);
 
     e = prepare_assign(assign_fn(p.d, p.assign_f64));
+    dim3 fgrid;
+    size_t fsmem = 0;
+    if (e == cudaSuccess) e = filter_config(p, fgrid, fsmem);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return e;
@@ -1353,7 +1752,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
         cudaGraph_t body_bal = mv.loop(h_bal);
         if (body_bal) {
             NodeAdder bl{body_bal};
-            bl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
+            bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
             bl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
             if (bl.err != cudaSuccess) mv.err = bl.err;
@@ -1367,7 +1766,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     cudaGraph_t body_fin = top.loop(h_fin);
     if (body_fin) {
         NodeAdder fl{body_fin};
-        fl.kernel(filter_fn(p.d), dim3(p.nsupers), dim3(kFilterThreads), a_p);
+        fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         fl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (fl.err != cudaSuccess) top.err = fl.err;
