@@ -104,6 +104,8 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
     p.heavy = (int *)take((size_t)p.ntiles * 4);
+    p.bigs = (int *)take((size_t)p.nsupers * 12);
+    p.blists = (int *)take((size_t)p.nsupers * kWarpList * 4);
     p.C = (double *)take((size_t)k * d * 8);
     p.Cm = (double *)take((size_t)k * d * 8);
     p.delta = (double *)take((size_t)k * 8);

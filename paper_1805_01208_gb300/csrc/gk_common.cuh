@@ -41,6 +41,9 @@ constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
 constexpr int kGroup = 32;          // centers per group record (one CTA of the k-sized kernels)
 constexpr int kGroupCap = 1024;     // group records held in shared memory by the filter
 constexpr int kQueues = 8;          // interleaved tile queues of the assignment
+constexpr int kWarpList = 512;      // level-1 candidate list kept per supertile by the filter
+constexpr int kWarpGroups = 64;     // kept center groups per supertile
+constexpr int kLaneMax = 64;        // longer lists: level 2 with a warp per tile
 constexpr int kQueueStride = 32;    // one 128-byte line per queue counter
 static_assert(kGroup == kKThreads, "a group record is written by one CTA of the k-sized kernels");
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
@@ -75,6 +78,7 @@ struct Ctl {
     unsigned int done_count;                // last-block-done counter (reset by the last block)
     unsigned int heavy_cnt;                 // tiles in the heavy list (reset before each filter)
     unsigned int coop_cnt;                  // tiles in the cooperative list (same)
+    unsigned int big_cnt;                   // supertiles with long candidate lists (same)
     int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
     double max_delta;
@@ -121,6 +125,8 @@ struct Prob {
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;
     int *heavy;
+    int *bigs;                  // per long-list supertile: index, list length, largest g (bits)
+    int *blists;                // their candidate lists, kWarpList entries each
     int nsm;                    // streaming multiprocessors of the device
     // per-center state
     double *C, *Cm, *delta, *S64, *Iin, *I2, *g64_2, *part;

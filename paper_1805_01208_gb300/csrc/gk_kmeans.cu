@@ -23,7 +23,8 @@
 namespace gk {
 
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of FP32
-constexpr int kFilterThreads = kSuperTiles * 32;
+constexpr int kFilterWarps = 8;                   // supertiles per CTA of the filter
+constexpr int kFilterThreads = kFilterWarps * 32;
 constexpr int kAssignWarps = 8;
 
 __device__ __forceinline__ int exponent_above(double v) {  // smallest e with |v| < 2^e
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->nonempty = 0;
         ctl->heavy_cnt = 0u;
         ctl->coop_cnt = 0u;
+        ctl->big_cnt = 0u;
         if (h_move) cudaGraphSetConditional(h_move, 1u);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
@@ -202,12 +204,11 @@ __global__ void export_kernel(Prob p) {
 // rounding of points, centers and this arithmetic never drops the FP64 winner;
 // comparisons are written so that a NaN keeps the center.
 //
-// Persistent CTAs of kSuperTiles warps take supertiles in turn.  Level 1: the
-// supertile box against the group records (box of 32 consecutive centers and their
-// g range): a group whose lower bound exceeds the smallest group upper bound holds
-// no center that passes the test below, nor the center that attains tau; then tau
-// and the supertile's candidate list from the centers of the remaining groups.
-// Level 2: each warp takes one tile of the supertile against that list and writes the
+// Level 1: the supertile box against the group records (box of 32 consecutive
+// centers and their g range): a group whose lower bound exceeds the smallest group
+// upper bound holds no center that passes the test below, nor the center that attains
+// tau; then tau and the supertile's candidate list from the centers of the remaining
+// groups.  Level 2: each tile of the supertile against that list, written to the
 // tile's record in ascending center order.
 // ------------------------------------------------------------------------------
 template <int D>
@@ -250,227 +251,287 @@ __device__ __forceinline__ void group_bounds(const float4 &gm, const float4 &gh,
 }
 
 
-static size_t filter_smem_bytes(const Prob &p) {
-    const size_t ngs = p.ngroups <= kGroupCap ? (size_t)p.ngroups : 0;
-    return (2 * ngs + 2 * (size_t)kSuperCap) * 16 + (size_t)(kSuperCap + kGroupCap) * 4;
-}
+// Level 1 of the filter for supertile s, by one warp: writes the ascending list of
+// the supertile's candidates to glist_out (kWarpList entries, global) and its first
+// kLaneMax entries to list (shared), and returns its length (> kWarpList: the list
+// did not fit, every center is a candidate); gall gets the largest g of all centers.
+// Loads of a sweep are issued together and the lower bounds of the first sweep are
+// kept in registers, so that the second sweep does not wait on memory again.
+constexpr int kGroupRegs = 8;   // group chunks whose bounds stay in registers
+constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in registers
 
 template <int D>
-__global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
-    count_launch(p.ctl);
-    extern __shared__ __align__(16) float4 fsm[];
-    __shared__ float s_tg[kSuperTiles], s_ga[kSuperTiles], s_tc[kSuperTiles];
-    __shared__ int s_wcnt[kSuperTiles];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sel = p.ctl->isel;
-    const int ng = p.ngroups;
-    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
-    const float4 *gsrc = p.gdata2 + (size_t)sel * 2 * ng;
-    const bool gstaged = ng <= kGroupCap;
-    float4 *sc = fsm + (gstaged ? 2 * ng : 0);  // level-1 list: {hi, g}, {lo, -}
-    int *slist = reinterpret_cast<int *>(sc + 2 * kSuperCap);
-    int *glist = slist + kSuperCap;
-    const float4 *G = gstaged ? fsm : gsrc;
-    const float infl = 4.0f * kU * p.R;
+__device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4 *cd, const float4 *gd,
+                                              int *list, int *glist, int *glist_out, float &gall) {
+    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    if (blockIdx.x == 0 && tid < kQueues) p.ctl->tile_q[tid * kQueueStride] = 0u;  // queues of the next assignment
-    if (gstaged)
-        for (int i = tid; i < 2 * ng; i += kFilterThreads) fsm[i] = gsrc[i];
-    __syncthreads();
-    // ascending compaction over the CTA: returns the position of this thread's entry
-    // and advances the running count (two barriers)
-    auto compact = [&](bool keep, int &count) -> int {
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) s_wcnt[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, total = 0;
+    const int ng = p.ngroups;
+    const float infl = 4.0f * kU * p.R;
+    float so[3], sh[3];
+    {
+        const float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
+        so[0] = a.x;
+        so[1] = a.y;
+        so[2] = a.z;
+        sh[0] = __fadd_ru(b.x, infl);
+        sh[1] = __fadd_ru(b.y, infl);
+        sh[2] = __fadd_ru(b.z, infl);
+    }
+    // groups: an upper bound of tau, and the largest g of all centers
+    float tg = INFINITY, ga = 0.0f;
+    float glb[kGroupRegs];
 #pragma unroll
-        for (int w2 = 0; w2 < kSuperTiles; ++w2) {
-            const int v = s_wcnt[w2];
-            before += w2 < warp ? v : 0;
-            total += v;
-        }
-        const int pos = count + before + __popc(bal & lt);
-        count += total;
-        return pos;
-    };
-    for (int s = blockIdx.x; s < p.nsupers; s += gridDim.x) {
-        float so[3], sh[3];
-        {
-            const float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
-            so[0] = a.x;
-            so[1] = a.y;
-            so[2] = a.z;
-            sh[0] = __fadd_ru(b.x, infl);
-            sh[1] = __fadd_ru(b.y, infl);
-            sh[2] = __fadd_ru(b.z, infl);
-        }
-        // groups: upper bound of tau, and the largest g of all centers
-        float tg = INFINITY, gall = 0.0f;
-        for (int gi = tid; gi < ng; gi += kFilterThreads) {
-            const float4 gm = G[2 * gi], gh = G[2 * gi + 1];
+    for (int r = 0; r < kGroupRegs; ++r) glb[r] = INFINITY;
+#pragma unroll 4
+    for (int r = 0; r * 32 < ng; ++r) {
+        const int gi = r * 32 + lane;
+        if (gi < ng) {
+            const float4 gm = __ldg(&gd[2 * gi]), gh = __ldg(&gd[2 * gi + 1]);
             float lb, ub;
             group_bounds<D>(gm, gh, so, sh, lb, ub);
             tg = fminf(tg, ub);
-            gall = fmaxf(gall, gh.w);
+            ga = fmaxf(ga, gh.w);
+#pragma unroll
+            for (int q = 0; q < kGroupRegs; ++q)
+                if (q == r) glb[q] = lb;
         }
-        for (int off = 16; off; off >>= 1) {
-            tg = fminf(tg, __shfl_xor_sync(0xffffffffu, tg, off));
-            gall = fmaxf(gall, __shfl_xor_sync(0xffffffffu, gall, off));
+    }
+    for (int off = 16; off; off >>= 1) {
+        tg = fminf(tg, __shfl_xor_sync(0xffffffffu, tg, off));
+        ga = fmaxf(ga, __shfl_xor_sync(0xffffffffu, ga, off));
+    }
+    gall = ga;
+    const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
+    int ngk = 0;  // kept groups, ascending
+    for (int r = 0; r * 32 < ng; ++r) {
+        const int gi = r * 32 + lane;
+        bool keep = false;
+        if (gi < ng) {
+            float lb = INFINITY;
+            if (r < kGroupRegs) {
+#pragma unroll
+                for (int q = 0; q < kGroupRegs; ++q)
+                    if (q == r) lb = glb[q];
+            } else {
+                float ub;
+                group_bounds<D>(__ldg(&gd[2 * gi]), __ldg(&gd[2 * gi + 1]), so, sh, lb, ub);
+            }
+            keep = !(lb > tauG);
         }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = ngk + __popc(bal & lt);
+        if (keep && pos < kWarpGroups) glist[pos] = gi;
+        ngk += __popc(bal);
+    }
+    __syncwarp();
+    const bool gover = ngk > kWarpGroups;  // too many groups: sweep every center
+    // tau of the supertile over the centers of the kept groups (lane = center of the group)
+    float tc = INFINITY;
+    float clb[kCenterRegs];
+#pragma unroll
+    for (int r = 0; r < kCenterRegs; ++r) clb[r] = INFINITY;
+    const int nsweep = gover ? (p.k + 31) / 32 : ngk;
+#pragma unroll 4
+    for (int i = 0; i < nsweep; ++i) {
+        const int c = (gover ? i : glist[i]) * kGroup + lane;
+        if (c < p.k) {
+            float lb, ub;
+            box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+            tc = fminf(tc, ub);
+#pragma unroll
+            for (int q = 0; q < kCenterRegs; ++q)
+                if (q == i) clb[q] = lb;
+        }
+    }
+    for (int off = 16; off; off >>= 1) tc = fminf(tc, __shfl_xor_sync(0xffffffffu, tc, off));
+    const float tauS = __fmul_ru(tc, 1.0f + 64.0f * kU);
+    int L = 0;
+    for (int i = 0; i < nsweep; ++i) {
+        const int c = (gover ? i : glist[i]) * kGroup + lane;
+        bool keep = false;
+        if (c < p.k) {
+            float lb = INFINITY;
+            if (i < kCenterRegs) {
+#pragma unroll
+                for (int q = 0; q < kCenterRegs; ++q)
+                    if (q == i) lb = clb[q];
+            } else {
+                float ub;
+                box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+            }
+            keep = !(lb > tauS);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = L + __popc(bal & lt);
+        if (keep && pos < kWarpList) glist_out[pos] = c;
+        if (keep && pos < kLaneMax) list[pos] = c;
+        L += __popc(bal);
+    }
+    __syncwarp();
+    return L;
+}
+
+// Header of tile t's record and its entry in the heavy / cooperative lists (one
+// thread per tile).
+__device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float gkept, float gall,
+                                            const float4 &tb0) {
+    const bool over = cnt > kCap;
+    float4 *rec = p.trec + (size_t)t * kRecF4;
+    // count (-1: scan all centers) and the largest g the tile can meet
+    rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
+    rec[1] = tb0;
+    if (over || cnt > kCoopCands)
+        p.heavy[p.ntiles - 1 - (int)atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
+    else if (cnt > kFastCands)
+        p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
+    if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
+    long long nv = p.n - (long long)t * kTile;
+    nv = nv > kTile ? kTile : nv;
+    const unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
+    atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
+}
+
+// One warp per supertile, with no block-wide synchronisation: level 1; then, for a
+// list of at most kLaneMax centers, level 2 with one lane per tile (lanes 0-15), each
+// walking the list.  A longer list is handed to filter_big_kernel.
+template <int D>
+__global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
+    count_launch(p.ctl);
+    __shared__ int s_list[kFilterWarps][kLaneMax];     // short level-1 lists
+    __shared__ int s_grp[kFilterWarps][kWarpGroups];   // kept groups (scratch of level 1)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x < kQueues) p.ctl->tile_q[threadIdx.x * kQueueStride] = 0u;
+    const int s = blockIdx.x * kFilterWarps + warp;
+    if (s >= p.nsupers) return;
+    const int sel = p.ctl->isel;
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
+    const float infl = 4.0f * kU * p.R;
+    // this lane's tile box, loaded while level 1 runs
+    const int t = s * kSuperTiles + lane;
+    const bool has_tile = lane < kSuperTiles && t < p.ntiles;
+    float4 tb0 = make_float4(0.f, 0.f, 0.f, 0.f), tb1 = tb0;
+    if (has_tile) {
+        tb0 = p.tiles[2 * t];
+        tb1 = p.tiles[2 * t + 1];
+    }
+    float gall;
+    int *gl_out = p.blists + (size_t)s * kWarpList;
+    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_grp[warp], gl_out, gall);
+    if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
-            s_tg[warp] = tg;
-            s_ga[warp] = gall;
+            const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
+            p.bigs[3 * slot] = s;
+            p.bigs[3 * slot + 1] = L;
+            p.bigs[3 * slot + 2] = __float_as_int(gall);
         }
-        __syncthreads();
-        tg = s_tg[0];
-        gall = s_ga[0];
-#pragma unroll
-        for (int w2 = 1; w2 < kSuperTiles; ++w2) {
-            tg = fminf(tg, s_tg[w2]);
-            gall = fmaxf(gall, s_ga[w2]);
+        return;
+    }
+    // level 2, short list: lane = tile
+    if (!has_tile) return;
+    const int *list = s_list[warp];
+    const float o[3] = {tb0.x, tb0.y, tb0.z};
+    const float h[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
+    float tt = INFINITY;
+#pragma unroll 4
+    for (int i = 0; i < L; ++i) {
+        const int c = list[i];
+        float lb, ub;
+        box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), o, h, lb, ub);
+        tt = fminf(tt, ub);
+    }
+    const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
+    int cnt = 0;
+    float gkept = 0.0f;
+    float4 *rec = p.trec + (size_t)t * kRecF4;
+    for (int i = 0; i < L; ++i) {
+        const int c = list[i];
+        const float4 ch = __ldg(&cd[2 * c]), cl = __ldg(&cd[2 * c + 1]);
+        float lb, ub;
+        box_bounds<D>(ch, cl, o, h, lb, ub);
+        if (!(lb > tauT)) {  // L <= kLaneMax <= kCap: always stored
+            const float q0 = (ch.x - o[0]) + cl.x;
+            const float q1 = (ch.y - o[1]) + cl.y;
+            const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+            rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
+            rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+            gkept = fmaxf(gkept, ch.w);
+            ++cnt;
         }
-        const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
-        int ngk = 0;  // kept groups, ascending
-        for (int base = 0; base < ng; base += kFilterThreads) {
-            const int gi = base + tid;
+    }
+    finish_tile(p, t, cnt, gkept, gall, tb0);
+}
+static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
+static_assert(kSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
+
+// Level 2 of the supertiles with long lists: one warp per tile, lanes over chunks
+// of 32 candidates (tau pass, then the ascending keep pass with ballots).
+template <int D>
+__global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
+    count_launch(p.ctl);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int total = (int)p.ctl->big_cnt * kSuperTiles;
+    const int sel = p.ctl->isel;
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float infl = 4.0f * kU * p.R;
+    const int TW = gridDim.x * kFilterWarps;
+    for (int item = blockIdx.x * kFilterWarps + (threadIdx.x >> 5); item < total; item += TW) {
+        const int slot = item / kSuperTiles;
+        const int s = p.bigs[3 * slot], Lr = p.bigs[3 * slot + 1];
+        const float gall = __int_as_float(p.bigs[3 * slot + 2]);
+        const int t = s * kSuperTiles + item % kSuperTiles;
+        if (t >= p.ntiles) continue;
+        const bool all = Lr > kWarpList;
+        const int L = all ? p.k : Lr;
+        const int *list = p.blists + (size_t)s * kWarpList;
+        const float4 tb0 = p.tiles[2 * t], tb1 = p.tiles[2 * t + 1];
+        const float o[3] = {tb0.x, tb0.y, tb0.z};
+        const float h[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
+        auto center = [&](int i, int &c, float4 &ch, float4 &cl) {
+            c = all ? i : list[i];
+            ch = __ldg(&cd[2 * c]);
+            cl = __ldg(&cd[2 * c + 1]);
+        };
+        float tt = INFINITY;
+        for (int i = lane; i < L; i += 32) {
+            int c;
+            float4 ch, cl;
+            center(i, c, ch, cl);
+            float lb, ub;
+            box_bounds<D>(ch, cl, o, h, lb, ub);
+            tt = fminf(tt, ub);
+        }
+        for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
+        const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
+        int cnt = 0;
+        float gkept = 0.0f;
+        float4 *rec = p.trec + (size_t)t * kRecF4;
+        for (int base = 0; base < L; base += 32) {
+            const int i = base + lane;
             bool keep = false;
-            if (gi < ng) {
-                float lb, ub;
-                group_bounds<D>(G[2 * gi], G[2 * gi + 1], so, sh, lb, ub);
-                keep = !(lb > tauG);
-            }
-            const int pos = compact(keep, ngk);
-            if (keep && pos < kGroupCap) glist[pos] = gi;
-            __syncthreads();
-        }
-        const bool gover = ngk > kGroupCap;  // too many groups: every center goes to level 2
-        // tau of the supertile over the centers of the kept groups (one warp per group)
-        float tc = INFINITY;
-        if (!gover) {
-            for (int i = warp; i < ngk; i += kSuperTiles) {
-                const int c = glist[i] * kGroup + lane;
-                if (c < p.k) {
-                    float lb, ub;
-                    box_bounds<D>(cd[2 * c], cd[2 * c + 1], so, sh, lb, ub);
-                    tc = fminf(tc, ub);
-                }
-            }
-        }
-        for (int off = 16; off; off >>= 1) tc = fminf(tc, __shfl_xor_sync(0xffffffffu, tc, off));
-        if (lane == 0) s_tc[warp] = tc;
-        __syncthreads();
-        tc = s_tc[0];
-#pragma unroll
-        for (int w2 = 1; w2 < kSuperTiles; ++w2) tc = fminf(tc, s_tc[w2]);
-        const float tauS = __fmul_ru(tc, 1.0f + 64.0f * kU);
-        // level-1 list, ascending (kept groups in order, one warp per group per round)
-        int count = gover ? kSuperCap + 1 : 0;
-        if (!gover) {
-            for (int base = 0; base < ngk; base += kSuperTiles) {
-                const int i = base + warp;
-                bool keep = false;
-                int c = 0;
-                float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
-                if (i < ngk) {
-                    c = glist[i] * kGroup + lane;
-                    if (c < p.k) {
-                        ch = cd[2 * c];
-                        cl = cd[2 * c + 1];
-                        float lb, ub;
-                        box_bounds<D>(ch, cl, so, sh, lb, ub);
-                        keep = !(lb > tauS);
-                    }
-                }
-                const int pos = compact(keep, count);
-                if (keep && pos < kSuperCap) {
-                    slist[pos] = c;
-                    sc[2 * pos] = ch;
-                    sc[2 * pos + 1] = cl;
-                }
-                __syncthreads();
-            }
-        }
-        const bool all = count > kSuperCap;
-        const int L = all ? p.k : count;
-        const int t = s * kSuperTiles + warp;
-        if (t < p.ntiles) {
-            float o[3], h[3];
-            {
-                const float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
-                o[0] = a.x;
-                o[1] = a.y;
-                o[2] = a.z;
-                h[0] = __fadd_ru(b.x, infl);
-                h[1] = __fadd_ru(b.y, infl);
-                h[2] = __fadd_ru(b.z, infl);
-            }
-            auto center = [&](int i, int &c, float4 &ch, float4 &cl) {
-                if (all) {
-                    c = i;
-                    ch = cd[2 * c];
-                    cl = cd[2 * c + 1];
-                } else {
-                    c = slist[i];
-                    ch = sc[2 * i];
-                    cl = sc[2 * i + 1];
-                }
-            };
-            float tt = INFINITY;
-            for (int i = lane; i < L; i += 32) {
-                int c;
-                float4 ch, cl;
+            int c = 0;
+            float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+            if (i < L) {
                 center(i, c, ch, cl);
                 float lb, ub;
                 box_bounds<D>(ch, cl, o, h, lb, ub);
-                tt = fminf(tt, ub);
+                keep = !(lb > tauT);
             }
-            for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
-            const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
-            int cnt = 0;
-            float gkept = 0.0f;
-            float4 *rec = p.trec + (size_t)t * kRecF4;
-            for (int base = 0; base < L; base += 32) {
-                const int i = base + lane;
-                bool keep = false;
-                int c = 0;
-                float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
-                if (i < L) {
-                    center(i, c, ch, cl);
-                    float lb, ub;
-                    box_bounds<D>(ch, cl, o, h, lb, ub);
-                    keep = !(lb > tauT);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                const int pos = cnt + __popc(bal & lt);
-                if (keep && pos < kCap) {
-                    const float q0 = (ch.x - o[0]) + cl.x;
-                    const float q1 = (ch.y - o[1]) + cl.y;
-                    const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-                    rec[2 + 2 * pos] = make_float4(q0, q1, q2, ch.w);
-                    rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
-                }
-                if (keep) gkept = fmaxf(gkept, ch.w);
-                cnt += __popc(bal);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int pos = cnt + __popc(bal & lt);
+            if (keep && pos < kCap) {
+                const float q0 = (ch.x - o[0]) + cl.x;
+                const float q1 = (ch.y - o[1]) + cl.y;
+                const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+                rec[2 + 2 * pos] = make_float4(q0, q1, q2, ch.w);
+                rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
             }
-            for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
-            if (lane == 0) {
-                const bool over = cnt > kCap;
-                // header: count (-1: scan all centers) and the largest g the tile can meet
-                rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
-                rec[1] = p.tiles[2 * t];
-                if (over || cnt > kCoopCands)
-                    p.heavy[p.ntiles - 1 - (int)atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
-                else if (cnt > kFastCands)
-                    p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
-                if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
-                long long nv = p.n - (long long)t * kTile;
-                nv = nv > kTile ? kTile : nv;
-                const unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
-                atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
-            }
+            if (keep) gkept = fmaxf(gkept, ch.w);
+            cnt += __popc(bal);
         }
-        __syncthreads();  // the next supertile rewrites the lists
+        for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
+        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0);
     }
 }
 
@@ -789,7 +850,8 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
 // candidates, and the d coordinate planes of the tile) for the tile after next as
 // soon as a stage is consumed, so the loads of two tiles are always in flight.
 constexpr int kAWarps = 4;
-constexpr int kAMinBlocks = 5;
+constexpr int kAMinBlocks = 5;     // CTAs per SM of the FP32 form
+constexpr int kAMinBlocks64 = 4;   // FP64 mode: more registers for the certification
 struct AStage {
     float4 rec[2 + 2 * kFastCands];
     float x[3][kTile];
@@ -797,7 +859,7 @@ struct AStage {
 static_assert(sizeof(AStage) * 2 * kAWarps >= 3 * kAWarps * kTile * 4, "scratch of the cooperative tiles");
 
 template <int D, bool F64MODE>
-__global__ void __launch_bounds__(kAWarps * 32, kAMinBlocks) assign_kernel(Prob p) {
+__global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinBlocks) assign_kernel(Prob p) {
     count_launch(p.ctl);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_assign0 = globaltimer_ns();
     __shared__ __align__(128) AStage st[kAWarps][2];
@@ -1295,6 +1357,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         ctl->maxg_key = 0ull;
         ctl->heavy_cnt = 0u;  // the next filter rebuilds the heavy and cooperative lists
         ctl->coop_cnt = 0u;
+        ctl->big_cnt = 0u;
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
         if (mode == 2) return;
@@ -1568,6 +1631,14 @@ static int kgrid(const Prob &p) { return (p.k + kKThreads - 1) / kKThreads; }
 static void *filter_fn(int d) {
     return d == 2 ? (void *)filter_kernel<2> : (void *)filter_kernel<3>;
 }
+static void *filter_big_fn(int d) {
+    return d == 2 ? (void *)filter_big_kernel<2> : (void *)filter_big_kernel<3>;
+}
+static dim3 filter_big_grid(const Prob &p) {
+    const long long need = ((long long)p.nsupers * kSuperTiles + kFilterWarps - 1) / kFilterWarps;
+    const long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * 8;
+    return dim3((unsigned)(need < cap ? need : cap));
+}
 static void *assign_fn(int d, int f64) {
     if (d == 2) return f64 ? (void *)assign_kernel<2, true> : (void *)assign_kernel<2, false>;
     return f64 ? (void *)assign_kernel<3, true> : (void *)assign_kernel<3, false>;
@@ -1585,30 +1656,10 @@ cudaError_t launch_init(const Prob &p, cudaStream_t s) {
 }
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s) { return launch_init(p, s); }
 
-// Persistent filter: as many CTAs as fit on the device at once (at most one per
-// supertile), with the dynamic shared memory the problem needs.
+// Filter launch: one warp per supertile.
 static cudaError_t filter_config(const Prob &p, dim3 &grid, size_t &smem) {
-    void *fn = filter_fn(p.d);
-    smem = filter_smem_bytes(p);
-    static void *last_fn = nullptr;
-    static size_t last_smem = 0;
-    static int last_dev = -1, last_blocks = 0;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (fn != last_fn || smem != last_smem || dev != last_dev) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kFilterThreads, smem);
-        if (e != cudaSuccess) return e;
-        last_fn = fn;
-        last_smem = smem;
-        last_dev = dev;
-        last_blocks = nb > 0 ? nb : 1;
-    }
-    long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * last_blocks;
-    grid = dim3((unsigned)(p.nsupers < cap ? p.nsupers : cap));
+    smem = 0;
+    grid = dim3((unsigned)((p.nsupers + kFilterWarps - 1) / kFilterWarps));
     return cudaSuccess;
 }
 
@@ -1618,11 +1669,13 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     size_t smem;
     cudaError_t e = filter_config(p, grid, smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
+    e = cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
 }
 static int assign_grid(const Prob &p) {
     int need = (p.ntiles + kAWarps - 1) / kAWarps;
-    int cap = (p.nsm > 0 ? p.nsm : 152) * kAMinBlocks;
+    int cap = (p.nsm > 0 ? p.nsm : 152) * (p.assign_f64 ? kAMinBlocks64 : kAMinBlocks);
     return need < cap ? need : cap;
 }
 static cudaError_t prepare_assign(void *fn) {
@@ -1753,6 +1806,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
         if (body_bal) {
             NodeAdder bl{body_bal};
             bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
+            bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
             if (bl.err != cudaSuccess) mv.err = bl.err;
@@ -1767,6 +1821,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     if (body_fin) {
         NodeAdder fl{body_fin};
         fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
+        fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (fl.err != cudaSuccess) top.err = fl.err;
@@ -1774,7 +1829,7 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     e = top.err;
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec_out, g, 0);
     cudaGraphDestroy(g);
-    if (nodes_per_pass) *nodes_per_pass = 3;
+    if (nodes_per_pass) *nodes_per_pass = 4;
     return e;
 }
 
