@@ -262,7 +262,8 @@ constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in regis
 
 template <int D>
 __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4 *cd, const float4 *gd,
-                                              int *list, int *glist, int *glist_out, float &gall) {
+                                              int *list, float4 *lcd, int *glist, int *glist_out,
+                                              float &gall) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ng = p.ngroups;
@@ -296,11 +297,40 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
                 if (q == r) glb[q] = lb;
         }
     }
+    // the nearest group (smallest lower bound): its centers' exact upper bounds give a
+    // much tighter bound of tau than the group boxes do
+    float nlb = INFINITY;
+    int ngi = 0x7fffffff;
+#pragma unroll
+    for (int r = 0; r < kGroupRegs; ++r) {
+        const int gi = r * 32 + lane;
+        if (gi < ng && glb[r] < nlb) {
+            nlb = glb[r];
+            ngi = gi;
+        }
+    }
     for (int off = 16; off; off >>= 1) {
         tg = fminf(tg, __shfl_xor_sync(0xffffffffu, tg, off));
         ga = fmaxf(ga, __shfl_xor_sync(0xffffffffu, ga, off));
+        const float olb = __shfl_xor_sync(0xffffffffu, nlb, off);
+        const int ogi = __shfl_xor_sync(0xffffffffu, ngi, off);
+        if (olb < nlb || (olb == nlb && ogi < ngi)) {
+            nlb = olb;
+            ngi = ogi;
+        }
     }
     gall = ga;
+    if (ngi != 0x7fffffff) {
+        const int c = ngi * kGroup + lane;
+        float t1 = INFINITY;
+        if (c < p.k) {
+            float lb, ub;
+            box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+            t1 = ub;
+        }
+        for (int off = 16; off; off >>= 1) t1 = fminf(t1, __shfl_xor_sync(0xffffffffu, t1, off));
+        tg = fminf(tg, t1);
+    }
     const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
     int ngk = 0;  // kept groups, ascending
     for (int r = 0; r * 32 < ng; ++r) {
@@ -364,7 +394,11 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = L + __popc(bal & lt);
         if (keep && pos < kWarpList) glist_out[pos] = c;
-        if (keep && pos < kLaneMax) list[pos] = c;
+        if (keep && pos < kLaneMax) {
+            list[pos] = c;
+            lcd[2 * pos] = __ldg(&cd[2 * c]);
+            lcd[2 * pos + 1] = __ldg(&cd[2 * c + 1]);
+        }
         L += __popc(bal);
     }
     __syncwarp();
@@ -398,6 +432,7 @@ template <int D>
 __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     count_launch(p.ctl);
     __shared__ int s_list[kFilterWarps][kLaneMax];     // short level-1 lists
+    __shared__ float4 s_lcd[kFilterWarps][2 * kLaneMax];  // their center data
     __shared__ int s_grp[kFilterWarps][kWarpGroups];   // kept groups (scratch of level 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x < kQueues) p.ctl->tile_q[threadIdx.x * kQueueStride] = 0u;
@@ -417,7 +452,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     }
     float gall;
     int *gl_out = p.blists + (size_t)s * kWarpList;
-    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_grp[warp], gl_out, gall);
+    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp], gl_out, gall);
     if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
             const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
@@ -430,14 +465,14 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     // level 2, short list: lane = tile
     if (!has_tile) return;
     const int *list = s_list[warp];
+    const float4 *lcd = s_lcd[warp];
     const float o[3] = {tb0.x, tb0.y, tb0.z};
     const float h[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
     float tt = INFINITY;
 #pragma unroll 4
     for (int i = 0; i < L; ++i) {
-        const int c = list[i];
         float lb, ub;
-        box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), o, h, lb, ub);
+        box_bounds<D>(lcd[2 * i], lcd[2 * i + 1], o, h, lb, ub);
         tt = fminf(tt, ub);
     }
     const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
@@ -446,7 +481,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     float4 *rec = p.trec + (size_t)t * kRecF4;
     for (int i = 0; i < L; ++i) {
         const int c = list[i];
-        const float4 ch = __ldg(&cd[2 * c]), cl = __ldg(&cd[2 * c + 1]);
+        const float4 ch = lcd[2 * i], cl = lcd[2 * i + 1];
         float lb, ub;
         box_bounds<D>(ch, cl, o, h, lb, ub);
         if (!(lb > tauT)) {  // L <= kLaneMax <= kCap: always stored
