@@ -213,9 +213,10 @@ __global__ void keys_kernel(Prob p, unsigned long long *keys_out, unsigned *perm
 // ------------------------------------------------------------------------------
 // LSD radix sort of (uint64 key, uint32 value), 8-bit digits, stable.
 // The array is cut into G contiguous segments of whole tiles (2048 items); each
-// CTA owns one segment.  Per pass: upsweep (segment digit counts), one-CTA scan of
-// the digit-major count table, downsweep (tiles of a segment in order; stable
-// ranks inside a tile from per-warp match_any counting).
+// CTA owns one segment.  Per pass: upsweep (segment digit counts), a scan of each
+// digit's row of the count table (one CTA per digit), downsweep (digit starts from
+// the digit totals and the row prefixes; tiles of a segment in order; stable ranks
+// inside a tile from per-warp match_any counting).
 // ------------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
@@ -237,42 +238,69 @@ __global__ void radix_upsweep(const unsigned long long *keys, long long n, int s
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * G + blockIdx.x] = cnt[i];
 }
 
-// Exclusive scan of m counts with one CTA of 1024 threads.
-__global__ void radix_scan(unsigned *hist, int m, Ctl *ctl) {
+// Row scan of the digit-major count table: CTA d turns hist[d][0..G) into exclusive
+// prefixes over the segments and writes the digit's total to totals[d].
+__global__ void __launch_bounds__(256) radix_scan(unsigned *hist, int G, unsigned *totals, Ctl *ctl) {
     count_launch(ctl);
-    __shared__ unsigned part[1024];
-    int t = threadIdx.x;
-    int per = (m + 1023) / 1024;
-    int b = t * per, e = min(m, b + per);
+    __shared__ unsigned wsum[8];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned *row = hist + (long long)blockIdx.x * G;
+    const int per = (G + 255) / 256;
+    const int b = t * per, e = min(G, b + per);
     unsigned s = 0;
-    for (int i = b; i < e; ++i) s += hist[i];
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        unsigned v = t >= off ? part[t - off] : 0u;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    for (int i = b; i < e; ++i) s += row[i];
+    // exclusive scan of the 256 thread sums
+    unsigned x = s;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
     }
-    unsigned run = part[t] - s;  // exclusive prefix of this thread's chunk
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        before += w < warp ? wsum[w] : 0u;
+        total += wsum[w];
+    }
+    unsigned run = before + x - s;
     for (int i = b; i < e; ++i) {
-        unsigned c = hist[i];
-        hist[i] = run;
+        const unsigned c = row[i];
+        row[i] = run;
         run += c;
     }
+    if (t == 0) totals[blockIdx.x] = total;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
                 unsigned long long *keys_out, unsigned *vals_out, long long n, int shift,
-                int tiles_per_seg, int G, const unsigned *offs, Ctl *ctl) {
+                int tiles_per_seg, int G, const unsigned *offs, const unsigned *totals, Ctl *ctl) {
     count_launch(ctl);
     __shared__ unsigned run_off[256];
     __shared__ unsigned whist[kSortWarps][256];
     __shared__ unsigned wofs[kSortWarps][256];
     __shared__ unsigned tcnt[256];
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < 256; i += kSortThreads) run_off[i] = offs[(long long)i * G + blockIdx.x];
+    static_assert(kSortThreads == 256, "one thread per digit below");
+    {
+        // start of each digit: exclusive scan of the digit totals, plus this segment's
+        // prefix within the digit
+        const unsigned tot = totals[tid];
+        unsigned x = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) tcnt[warp] = x;
+        __syncthreads();
+        unsigned before = 0;
+        for (int w = 0; w < warp; ++w) before += tcnt[w];
+        run_off[tid] = before + x - tot + offs[(long long)tid * G + blockIdx.x];
+        __syncthreads();
+    }
     for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&whist[0][0])[i] = 0;
     __syncthreads();
     unsigned lt_mask = (1u << lane) - 1u;
@@ -499,7 +527,7 @@ size_t radix_hist_entries(long long n) {
     if (tps < 1) tps = 1;
     long long G = (ntiles + tps - 1) / tps;
     if (G < 1) G = 1;
-    return (size_t)(256 * G);
+    return (size_t)(256 * G + 256);  // count table, then the digit totals
 }
 
 // Sorts keys[0]/perm[0] (n items) in place through the alternate buffers; returns
@@ -515,9 +543,11 @@ cudaError_t launch_radix_sort(const Prob &p, int key_bits, unsigned *hist, int *
     int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
         radix_upsweep<<<G, 256, 0, s>>>(p.keys[cur], n, shift, tps, G, hist, p.ctl);
-        radix_scan<<<1, 1024, 0, s>>>(hist, 256 * G, p.ctl);
+        unsigned *totals = hist + (size_t)256 * G;
+        radix_scan<<<256, 256, 0, s>>>(hist, G, totals, p.ctl);
         radix_downsweep<<<G, kSortThreads, 0, s>>>(p.keys[cur], p.perm[cur], p.keys[cur ^ 1],
-                                                    p.perm[cur ^ 1], n, shift, tps, G, hist, p.ctl);
+                                                    p.perm[cur ^ 1], n, shift, tps, G, hist, totals,
+                                                    p.ctl);
         cur ^= 1;
     }
     *sel = cur;

@@ -390,3 +390,48 @@ def test_full_size_gmm3d_1e7_k1024(gk):
     Cr, dr, br = oracle.move_centers(x, None, A, C)
     assert _rel_center_err(_np(Cn), Cr, x) < 1e-10
     assert math.isclose(beta, br, rel_tol=1e-12)
+
+
+# ----------------------------------------------------------------------------------------
+# Full size of the FP32-form workloads (2-D, n = 1e8 with k = 4096, and n = 1e9 with
+# k = 16384), checked on sampled outputs: Hilbert keys bit-exact on a sample (the sample
+# carries the points that attain the bounding box, so the oracle quantises with the
+# same box), the balance bound exactly on the host, the FP32-form disagreement with the
+# FP64 argmin under the returned state, and the centers of the returned assignment.
+# ----------------------------------------------------------------------------------------
+FP32_FORM_MAX_DISAGREEMENT = 1e-4
+
+
+def _full_size_fp32_form(gk, name, nsample):
+    import torch
+    x, w, spec = synth.workload(name, threads=THREADS)
+    n, k, eps = len(x), spec["k"], spec["eps"]
+    xt = _dev(x)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([rng.choice(n, nsample, replace=False), x.argmin(0), x.argmax(0)]))
+    keys = gk.hilbert_keys(xt)
+    assert np.array_equal(_np(keys[_dev(idx)]).view(np.uint64), oracle.hilbert_keys(x[idx]))
+    del keys
+    block, C, I, res = gk.partition(xt, k, eps, options=gk.default_options(assign_dtype="f32"))
+    torch.cuda.synchronize()
+    A, C, I = _np(block), _np(C), _np(I)
+    assert res["status"] == 0 and res["balanced"] == 1
+    S = np.bincount(A, minlength=k)
+    assert S.sum() == n and S.max() <= (1 + eps) * math.ceil(n / k)
+    sub = idx[:nsample]
+    A_ref, _, _ = oracle.assign(x[sub].astype(np.float64), C, I, threads=THREADS)
+    assert (A[sub] != A_ref).mean() <= FP32_FORM_MAX_DISAGREEMENT
+    Cn, delta, beta = gk.move_centers(xt, _dev(A), _dev(C))
+    Cr, dr, br = oracle.move_centers(x, None, A, C)
+    assert _rel_center_err(_np(Cn), Cr, x[idx].astype(np.float64)) < 1e-10
+    assert math.isclose(beta, br, rel_tol=1e-12)
+
+
+@pytest.mark.slow
+def test_full_size_radial2d_1e8_k4096_fp32_form(gk):
+    _full_size_fp32_form(gk, "radial2d_1e8_k4096_f32", 100_000)
+
+
+@pytest.mark.slow
+def test_full_size_spots2d_1e9_k16384_fp32_form(gk):
+    _full_size_fp32_form(gk, "spots2d_1e9_k16384_f32", 50_000)
