@@ -270,13 +270,19 @@ def main():
     _, _, _, tres = step(timed)
     ev_avg = tres["time_assign_ms"] / max(1, tres["assign_launches"])
     es = 8 if spec["dtype"] == "f64" else 4
-    bytes_per_pt = 4 * d + 4 + (es if spec["weighted"] else 0)
-    bytes_per_launch = n * bytes_per_pt
+    sw = es if spec["weighted"] else 0
+    # algorithmic bytes of one balance pass: every point's coordinates (and weight) read
+    # once; writing the block ids is not counted (only the last pass of a loop needs it)
+    bytes_per_launch = n * (d * es + sw)
+    # what this assignment kernel itself streams: FP32 frame coordinates, block ids
+    kernel_bytes = n * (d * 4 + 4 + sw)
     peak, peak_kind = _peaks()
     achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": None, "kernel": "assign_kernel",
-            "bytes_per_launch": bytes_per_launch, "launch_ms_events": ev_avg,
+            "bytes_per_launch": bytes_per_launch, "kernel_stream_bytes_per_launch": kernel_bytes,
+            "kernel_stream_frac": kernel_bytes / (ev_avg * 1e-3) / 1e9 / peak,
+            "launch_ms_events": ev_avg,
             "launch_ms_live_graph": live_ms / max(1, live_n), "peak_source": peak_kind,
             "other_kernels_ms_per_pass": {
                 "filter": tres["time_filter_ms"] / max(1, tres["filter_launches"]),
