@@ -196,6 +196,38 @@ gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, i
                        int32_t *block_out, double *centers_out, double *influence_out,
                        gk_result *result, void *stream);
 
+/* One problem of a batch (gk_partition_batched). */
+typedef struct gk_instance {
+    const void *coords;     /* n x d row-major, dtype; device memory                 */
+    const void *weights;    /* n values of dtype, or NULL (unit weights); device     */
+    int64_t n;
+    int32_t d;              /* 2 or 3                                                */
+    int32_t dtype;          /* GK_F32 or GK_F64                                      */
+    int32_t k;              /* 1 <= k <= n                                           */
+    int32_t reserved;       /* must be 0                                             */
+    double eps;             /* >= 0                                                  */
+    int32_t *block_out;     /* n int32 in input order; device memory                 */
+    double *centers_out;    /* k x d FP64, nullable; host or device                  */
+    double *influence_out;  /* k FP64, nullable; host or device                      */
+} gk_instance;
+
+/*
+ * gk_partition for count independent problems of any mix of n, d, dtype and k
+ * (Algorithm 2 for each; the paper partitions one point set at a time, so there
+ * is no counterpart of the batch itself).  The bootstraps run in turn, then the
+ * k-means loops of all problems run as one CUDA graph launch with one chain per
+ * problem, so that small problems proceed beside large ones.  Every instance's
+ * coords, weights and block_out must be device memory of the current device.
+ *   opt: NULL = defaults, shared by all instances.
+ *   results: count entries (nullable); results[i].status is instance i's status;
+ *            the times are those of the whole batch.
+ * Returns GK_OK when every instance succeeded; otherwise GK_ERR_INVALID_ARG
+ * (before any launch), GK_ERR_CUDA / GK_ERR_OOM, else GK_ERR_TIMEOUT if an
+ * instance timed out, else GK_ERR_NOT_BALANCED if an instance ended unbalanced.
+ */
+gk_status gk_partition_batched(const gk_instance *inst, int32_t count, const gk_options *opt,
+                               gk_result *results, void *stream);
+
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);
 

@@ -83,6 +83,23 @@ class Result(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved0"}
 
 
+class Instance(ctypes.Structure):
+    """gk_instance: one problem of gk_partition_batched (device pointers)."""
+    _fields_ = [
+        ("coords", ctypes.c_void_p),
+        ("weights", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("eps", ctypes.c_double),
+        ("block_out", ctypes.c_void_p),
+        ("centers_out", ctypes.c_void_p),
+        ("influence_out", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 
 
@@ -109,6 +126,8 @@ def lib():
             getattr(L, name).restype = i32
         L.gk_move_centers_noalloc.argtypes = [P, i32, P, i64, i32, i32, P, P, P, P, P, P]
         L.gk_move_centers_noalloc.restype = i32
+        L.gk_partition_batched.argtypes = [P, i32, P, P, P]
+        L.gk_partition_batched.restype = i32
         L.gk_release.argtypes = []
         _lib = L
     return _lib
@@ -298,6 +317,33 @@ def partition(coords, k: int, eps: float, weights=None, options: Options | None 
                             ctypes.byref(res), _stream(coords, stream))
     _check(st, "gk_partition", allow=(GK_ERR_NOT_BALANCED,))
     return block, centers, infl, res.as_dict()
+
+
+def partition_batched(problems, options: Options | None = None, stream=None):
+    """gk_partition_batched over a list of (coords, k, eps, weights-or-None) with CUDA
+    tensors.  Returns (list of (block, centers, influence, result dict), status)."""
+    import torch
+    m = len(problems)
+    inst = (Instance * m)()
+    outs = []
+    for i, (coords, k, eps, weights) in enumerate(problems):
+        n, d = _shape(coords)
+        _same_dtype(coords, weights)
+        if not (_is_torch(coords) and coords.is_cuda):
+            raise ValueError("batched problems take CUDA tensors")
+        block = torch.empty(n, dtype=torch.int32, device=coords.device)
+        centers = torch.empty((k, d), dtype=torch.float64, device=coords.device)
+        infl = torch.empty(k, dtype=torch.float64, device=coords.device)
+        inst[i] = Instance(_ptr(coords), _ptr(weights), n, d, _dtype_code(coords), k, 0, eps,
+                           _ptr(block), _ptr(centers), _ptr(infl))
+        outs.append((block, centers, infl))
+    res = (Result * m)()
+    opt = options if options is not None else default_options()
+    st = lib().gk_partition_batched(ctypes.cast(inst, ctypes.c_void_p), m, ctypes.byref(opt),
+                                    ctypes.cast(res, ctypes.c_void_p),
+                                    _stream(problems[0][0], stream))
+    _check(st, "gk_partition_batched", allow=(GK_ERR_NOT_BALANCED,))
+    return [(b, c, i_, res[j].as_dict()) for j, (b, c, i_) in enumerate(outs)], st
 
 
 def release():

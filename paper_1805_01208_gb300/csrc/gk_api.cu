@@ -4,6 +4,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/gk.h"
@@ -29,6 +31,11 @@ struct Workspace {
     bool has_graph = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t kev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // batches: pinned control blocks and the cached graph of the last batch
+    Ctl *batch_ctl = nullptr;
+    int batch_cap = 0;
+    cudaGraphExec_t batch_exec = nullptr;
+    std::vector<Prob> batch_key;
 };
 Workspace g_ws;
 
@@ -36,12 +43,16 @@ void drop_graph() {
     if (g_ws.exec) cudaGraphExecDestroy(g_ws.exec);
     g_ws.exec = nullptr;
     g_ws.has_graph = false;
+    if (g_ws.batch_exec) cudaGraphExecDestroy(g_ws.batch_exec);
+    g_ws.batch_exec = nullptr;
+    g_ws.batch_key.clear();
 }
 
 void release_all() {
     drop_graph();
     if (g_ws.dev) cudaFree(g_ws.dev);
     if (g_ws.host_ctl) cudaFreeHost(g_ws.host_ctl);
+    if (g_ws.batch_ctl) cudaFreeHost(g_ws.batch_ctl);
     for (auto &e : g_ws.ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : g_ws.kev)
@@ -201,8 +212,7 @@ struct Call {
     Prob p;
     Bufs b;
     bool coords_host, weights_host;
-    gk_status init(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
-                   int32_t k, bool sort, bool block_host, bool perm_out) {
+    gk_status setup(const void *weights, int64_t n, int32_t d, int32_t k, int32_t dtype) {
         memset(&p, 0, sizeof(p));
         p.n = n;
         p.n_pad = (n + kTile - 1) / kTile * kTile;
@@ -216,6 +226,32 @@ struct Call {
         int dev = 0;
         GK_CUDA(cudaGetDevice(&dev));
         GK_CUDA(cudaDeviceGetAttribute(&p.nsm, cudaDevAttrMultiProcessorCount, dev));
+        return GK_OK;
+    }
+    // Control block (from the pinned host slot hc) and accumulators of the problem.
+    gk_status upload_state(Ctl *hc) {
+        Ctl c0;
+        memset(&c0, 0, sizeof(c0));
+        for (int j = 0; j < 3; ++j) {
+            c0.bb_lo[j] = ~0ull;
+            c0.bb_hi[j] = 0ull;
+        }
+        c0.w_lo = ~0ull;
+        c0.w_hi = 0ull;
+        *hc = c0;
+        GK_CUDA(cudaMemcpyAsync(p.ctl, hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaMemsetAsync(p.Sfix, 0, (size_t)p.k * 16, s));
+        GK_CUDA(cudaMemsetAsync(p.SXfix, 0, (size_t)p.k * p.d * 16, s));
+        GK_CUDA(cudaMemsetAsync(p.BBlo, 0xff, (size_t)p.k * p.d * 8, s));
+        GK_CUDA(cudaMemsetAsync(p.BBhi, 0, (size_t)p.k * p.d * 8, s));
+        return GK_OK;
+    }
+    gk_status init(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
+                   int32_t k, bool sort, bool block_host, bool perm_out) {
+        gk_status st0 = setup(weights, n, d, k, dtype);
+        if (st0 != GK_OK) return st0;
+        int dev = 0;
+        GK_CUDA(cudaGetDevice(&dev));
         PtrKind kc = ptr_kind(coords, dev);
         PtrKind kw = weights ? ptr_kind(weights, dev) : kHost;
         if (kc == kForeign || kw == kForeign) return GK_ERR_INVALID_ARG;
@@ -237,22 +273,7 @@ struct Call {
         if (weights_host)
             GK_CUDA(cudaMemcpyAsync(b.weights_stage, weights, (size_t)n * es,
                                     cudaMemcpyHostToDevice, s));
-        // control block and accumulators
-        Ctl c0;
-        memset(&c0, 0, sizeof(c0));
-        for (int j = 0; j < 3; ++j) {
-            c0.bb_lo[j] = ~0ull;
-            c0.bb_hi[j] = 0ull;
-        }
-        c0.w_lo = ~0ull;
-        c0.w_hi = 0ull;
-        *g_ws.host_ctl = c0;
-        GK_CUDA(cudaMemcpyAsync(p.ctl, g_ws.host_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
-        GK_CUDA(cudaMemsetAsync(p.Sfix, 0, (size_t)k * 16, s));
-        GK_CUDA(cudaMemsetAsync(p.SXfix, 0, (size_t)k * d * 16, s));
-        GK_CUDA(cudaMemsetAsync(p.BBlo, 0xff, (size_t)k * d * 8, s));
-        GK_CUDA(cudaMemsetAsync(p.BBhi, 0, (size_t)k * d * 8, s));
-        return GK_OK;
+        return upload_state(g_ws.host_ctl);
     }
     gk_status read_ctl() {
         GK_CUDA(cudaMemcpyAsync(g_ws.host_ctl, p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
@@ -264,7 +285,9 @@ struct Call {
         GK_CUDA(launch_bbox(p, s));
         gk_status st = read_ctl();
         if (st != GK_OK) return st;
-        Ctl &c = *g_ws.host_ctl;
+        return frame(*g_ws.host_ctl, delta_threshold);
+    }
+    gk_status frame(const Ctl &c, double delta_threshold) {
         if (c.nonfinite || c.nonpositive_w) return GK_ERR_INVALID_ARG;
         double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, ext = 0.0, xmax = 0.0;
         for (int j = 0; j < p.d; ++j) {
@@ -363,8 +386,7 @@ gk_status run_loop(Call &cl, const gk_options &o) {
         if (!(g_ws.has_graph && memcmp(&key, &g_ws.graph_key, sizeof(Prob)) == 0)) {
             drop_graph();
             cudaGraphExec_t ex = nullptr;
-            int npp = 0;
-            if (build_loop_graph(key, &ex, &npp) != cudaSuccess) {
+            if (build_loop_graph(&key, 1, &ex) != cudaSuccess) {
                 cudaGetLastError();
                 return GK_ERR_CUDA;
             }
@@ -500,6 +522,135 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     return res;
 }
 
+// gk_partition_batched: every instance in its own slice of the workspace; bounding
+// boxes of all instances and one readback; the bootstraps in turn; the loops of all
+// instances as one graph (independent chains); scatter and export per instance.
+gk_status partition_batched(const gk_instance *inst, int32_t count, const gk_options *opt,
+                            gk_result *results, void *stream) {
+    if (!inst || count < 1) return GK_ERR_INVALID_ARG;
+    gk_options o;
+    options_or_default(opt, &o);
+    gk_status st = check_options(o);
+    if (st != GK_OK) return st;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i) {
+        const gk_instance &q = inst[i];
+        if ((st = check_common(q.coords, q.dtype, q.n, q.d)) != GK_OK) return st;
+        if (q.k < 1 || q.k > q.n || !(q.eps >= 0.0) || !q.block_out || q.reserved != 0)
+            return GK_ERR_INVALID_ARG;
+        const size_t es = q.dtype == GK_F64 ? 8 : 4;
+        if (ptr_kind(q.coords, dev) != kDevice || ((uintptr_t)q.coords % es)) return GK_ERR_INVALID_ARG;
+        if (q.weights && (ptr_kind(q.weights, dev) != kDevice || ((uintptr_t)q.weights % es)))
+            return GK_ERR_INVALID_ARG;
+        if (ptr_kind(q.block_out, dev) != kDevice || ((uintptr_t)q.block_out % 4)) return GK_ERR_INVALID_ARG;
+        if ((q.centers_out && ptr_kind(q.centers_out, dev) == kForeign) ||
+            (q.influence_out && ptr_kind(q.influence_out, dev) == kForeign))
+            return GK_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<Call> cl(count);
+    std::vector<size_t> off(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        cl[i].s = s;
+        if ((st = cl[i].setup(inst[i].weights, inst[i].n, inst[i].d, inst[i].k, inst[i].dtype)) != GK_OK)
+            return st;
+        off[i + 1] = off[i] + align_up(layout(cl[i].p, cl[i].b, nullptr, true, false, false, false, false));
+    }
+    if ((st = ensure_workspace(off[count])) != GK_OK) return st;
+    if (g_ws.batch_cap < count) {
+        if (g_ws.batch_ctl) cudaFreeHost(g_ws.batch_ctl);
+        g_ws.batch_ctl = nullptr;
+        g_ws.batch_cap = 0;
+        if (cudaMallocHost((void **)&g_ws.batch_ctl, sizeof(Ctl) * (size_t)count) != cudaSuccess) {
+            cudaGetLastError();
+            return GK_ERR_OOM;
+        }
+        g_ws.batch_cap = count;
+    }
+    Ctl *hc = g_ws.batch_ctl;
+    GK_CUDA(cudaEventRecord(g_ws.ev[0], s));
+    for (int i = 0; i < count; ++i) {
+        Prob &p = cl[i].p;
+        layout(p, cl[i].b, g_ws.dev + off[i], true, false, false, false, false);
+        p.coords = inst[i].coords;
+        p.weights = inst[i].weights;
+        p.eps = inst[i].eps;
+        p.assign_f64 = o.assign_dtype == GK_F64;
+        p.max_iter = o.max_iter;
+        p.max_balance_iter = o.max_balance_iter;
+        p.final_balance_iter = o.final_balance_iter;
+        p.erosion = o.erosion;
+        if ((st = cl[i].upload_state(&hc[i])) != GK_OK) return st;
+        GK_CUDA(launch_bbox(p, s));
+    }
+    for (int i = 0; i < count; ++i)
+        GK_CUDA(cudaMemcpyAsync(&hc[i], cl[i].p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    std::vector<const unsigned *> perm(count);
+    for (int i = 0; i < count; ++i) {
+        Prob &p = cl[i].p;
+        if ((st = cl[i].frame(hc[i], o.delta_threshold)) != GK_OK) return st;
+        GK_CUDA(cudaMemcpyAsync(&p.ctl->thr, &cl[i].thr, sizeof(double), cudaMemcpyHostToDevice, s));
+        Prob kp = cl[i].key_prob();
+        GK_CUDA(launch_keys(kp, p.keys[0], p.perm[0], s));
+        int sel = 0;
+        GK_CUDA(launch_radix_sort(p, p.d == 2 ? 64 : 63, cl[i].b.hist, &sel, s));
+        perm[i] = p.perm[sel];
+        GK_CUDA(launch_gather(p, perm[i], s));
+        GK_CUDA(launch_centers(p, s));
+    }
+    GK_CUDA(cudaEventRecord(g_ws.ev[1], s));
+    std::vector<Prob> key(count);
+    for (int i = 0; i < count; ++i) {
+        key[i] = cl[i].p;
+        key[i].coords = nullptr;
+        key[i].weights = nullptr;
+    }
+    bool same = g_ws.batch_exec && g_ws.batch_key.size() == key.size() &&
+                memcmp(g_ws.batch_key.data(), key.data(), sizeof(Prob) * key.size()) == 0;
+    if (!same) {
+        if (g_ws.batch_exec) cudaGraphExecDestroy(g_ws.batch_exec);
+        g_ws.batch_exec = nullptr;
+        g_ws.batch_key.clear();
+        cudaGraphExec_t ex = nullptr;
+        if (build_loop_graph(key.data(), count, &ex) != cudaSuccess) {
+            cudaGetLastError();
+            return GK_ERR_CUDA;
+        }
+        g_ws.batch_exec = ex;
+        g_ws.batch_key = key;
+    }
+    GK_CUDA(cudaGraphLaunch(g_ws.batch_exec, s));
+    GK_CUDA(cudaEventRecord(g_ws.ev[2], s));
+    for (int i = 0; i < count; ++i) {
+        Prob &p = cl[i].p;
+        GK_CUDA(launch_scatter(p, perm[i], inst[i].block_out, s));
+        if ((st = copy_out(inst[i].centers_out, p.C, (size_t)p.k * p.d * 8, s)) != GK_OK) return st;
+        GK_CUDA(launch_export(p, s));
+        if ((st = copy_out(inst[i].influence_out, p.Iin, (size_t)p.k * 8, s)) != GK_OK) return st;
+        GK_CUDA(cudaMemcpyAsync(&hc[i], p.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    }
+    GK_CUDA(cudaEventRecord(g_ws.ev[3], s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    const double t_boot = elapsed(g_ws.ev[0], g_ws.ev[1]), t_loop = elapsed(g_ws.ev[1], g_ws.ev[2]),
+                 t_tot = elapsed(g_ws.ev[0], g_ws.ev[3]);
+    bool any_timeout = false, any_unbalanced = false;
+    for (int i = 0; i < count; ++i) {
+        const Ctl &c = hc[i];
+        gk_status r = GK_OK;
+        if (c.status != kOk) {
+            r = GK_ERR_TIMEOUT;
+            any_timeout = true;
+        } else if (!c.balanced) {
+            r = GK_ERR_NOT_BALANCED;
+            any_unbalanced = true;
+        }
+        if (results) fill_result(&results[i], c, r, t_boot, t_loop, t_tot, inst[i].n, cl[i]);
+    }
+    return any_timeout ? GK_ERR_TIMEOUT : (any_unbalanced ? GK_ERR_NOT_BALANCED : GK_OK);
+}
+
 }  // namespace
 }  // namespace gk
 
@@ -532,6 +683,11 @@ const char *gk_status_string(int32_t status) {
 }
 
 int32_t gk_abi_version(void) { return GK_ABI_VERSION; }
+
+gk_status gk_partition_batched(const gk_instance *inst, int32_t count, const gk_options *opt,
+                               gk_result *results, void *stream) {
+    return partition_batched(inst, count, opt, results, stream);
+}
 
 gk_status gk_hilbert_keys(const void *coords, int32_t dtype, int64_t n, int32_t d,
                           uint64_t *keys_out, void *stream) {

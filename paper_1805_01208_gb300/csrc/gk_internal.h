@@ -29,6 +29,7 @@ cudaError_t launch_block_weights(const Prob &p, cudaStream_t s);
 cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s);
 cudaError_t launch_final_begin(const Prob &p, cudaStream_t s);
 cudaError_t launch_export(const Prob &p, cudaStream_t s);
-cudaError_t build_loop_graph(const Prob &p, cudaGraphExec_t *exec_out, int *nodes_per_pass);
+// The whole loop of each of count problems as one graph (independent chains).
+cudaError_t build_loop_graph(const Prob *probs, int count, cudaGraphExec_t *exec_out);
 
 }  // namespace gk

@@ -1764,9 +1764,11 @@ cudaError_t launch_export(const Prob &p, cudaStream_t s) {
 
 // ------------------------------------------------------------------------------
 // The whole loop as one CUDA graph:
-//   init_a -> init_b -> while(h_move){ while(h_bal){ filter -> assign -> balance(0) }
-//   -> centroid -> finalize_a -> finalize_b } -> final_begin -> while(h_fin){ filter ->
-//   assign -> balance(1) }
+//   init_a -> init_b -> while(h_move){ while(h_bal){ filter -> filter_big -> assign ->
+//   balance(0) } -> centroid -> finalize_a -> finalize_b } -> final_begin ->
+//   while(h_fin){ filter -> filter_big -> assign -> balance(1) }
+// A batch of problems is one graph with one such chain per problem, no edges between
+// chains, so that the chains of small problems run beside those of large ones.
 // ------------------------------------------------------------------------------
 namespace {
 struct NodeAdder {
@@ -1801,19 +1803,15 @@ struct NodeAdder {
 };
 }  // namespace
 
-cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nodes_per_pass) {
+// Adds one problem's loop as an independent chain of graph g (its own conditional
+// handles).  The kernel parameters are copied when the nodes are created.
+cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
     Prob p = pc;
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaGraphCreate(&g, 0);
-    if (e != cudaSuccess) return e;
     cudaGraphConditionalHandle h_move, h_bal, h_fin;
-    e = cudaGraphConditionalHandleCreate(&h_move, g, 1, cudaGraphCondAssignDefault);
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_move, g, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_bal, g, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_fin, g, 0, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return e;
-    }
+    if (e != cudaSuccess) return e;
     int mode0 = 0, mode1 = 1;
     void *a_init[] = {&p, &h_move, &h_bal};
     void *a_p[] = {&p};
@@ -1822,15 +1820,11 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
     void *a_fin[] = {&p, &mode0, &h_move, &h_bal};
     void *a_fb[] = {&p, &h_fin};
     const dim3 kg(kgrid(p)), kb(kKThreads), tg(tile_warp_grid(p)), tb(kAssignWarps * 32);
-
     e = prepare_assign(assign_fn(p.d, p.assign_f64));
     dim3 fgrid;
     size_t fsmem = 0;
     if (e == cudaSuccess) e = filter_config(p, fgrid, fsmem);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return e;
-    }
+    if (e != cudaSuccess) return e;
     NodeAdder top{g};
     top.kernel((void *)init_a_kernel, kg, kb, a_init);
     top.kernel((void *)init_b_kernel, kg, kb, a_p);
@@ -1861,10 +1855,16 @@ cudaError_t build_loop_graph(const Prob &pc, cudaGraphExec_t *exec_out, int *nod
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (fl.err != cudaSuccess) top.err = fl.err;
     }
-    e = top.err;
+    return top.err;
+}
+
+cudaError_t build_loop_graph(const Prob *probs, int count, cudaGraphExec_t *exec_out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < count && e == cudaSuccess; ++i) e = add_loop_chain(g, probs[i]);
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec_out, g, 0);
     cudaGraphDestroy(g);
-    if (nodes_per_pass) *nodes_per_pass = 4;
     return e;
 }
 

@@ -26,7 +26,7 @@ def test_header_declares_the_entry_points():
     names = _declared()
     for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
-                 "gk_status_string", "gk_abi_version"):
+                 "gk_status_string", "gk_abi_version", "gk_partition_batched"):
         assert want in names
 
 
@@ -50,6 +50,17 @@ def test_struct_layouts_match_header():
     # gk_options: 4 int32, double, 3 int32, 5 int32 reserved (8-byte aligned double)
     assert ctypes.sizeof(gk.Options) == 4 * 4 + 8 + 3 * 4 + 5 * 4
     assert ctypes.sizeof(gk.Result) == 6 * 4 + 4 * 8 + 2 * 8 + 3 * 8 + 4 * 8 + 4 * 8 + 8 + 8
+    # gk_instance: 2 pointers, int64, 4 int32, double, 3 pointers
+    assert ctypes.sizeof(gk.Instance) == 2 * 8 + 8 + 4 * 4 + 8 + 3 * 8
+
+
+def test_batched_rejects_empty_batch_before_any_launch(libgk):
+    import paper_1805_01208_gb300 as gk
+    L = gk.lib()
+    assert L.gk_partition_batched(None, 0, None, None, None) == gk.GK_ERR_INVALID_ARG
+    inst = (gk.Instance * 1)()
+    assert L.gk_partition_batched(ctypes.cast(inst, ctypes.c_void_p), 0, None, None, None) == \
+        gk.GK_ERR_INVALID_ARG
 
 
 def test_library_is_built_for_sm103a(libgk):
