@@ -191,10 +191,15 @@ def _config(spec, args):
 # --------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------
+BATCHED_WORKLOAD = "batched64_f32"
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == BATCHED_WORKLOAD:
+        return run_batched(args)
     import torch
 
     rank = int(os.environ.get("RANK", "0"))
@@ -332,6 +337,106 @@ def main():
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
                 "fp32_form": fp32, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batched(args):
+    """64 instances of mixed n, d, k with weights, FP32 form, one gk_partition_batched
+    call per step (one graph launch for all k-means loops)."""
+    import torch
+    import paper_1805_01208_gb300 as gk
+    from paper_1805_01208_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gk.build()
+    specs = synth.batched_instances(64, seed=4 + 1000 * rank)
+    host = [synth.instance_data(sp) for sp in specs]
+    xs = [torch.from_numpy(x).to(dev) for x, _ in host]
+    ws = [torch.from_numpy(w).to(dev) if w is not None else None for _, w in host]
+    probs = [(xs[i], sp["k"], sp["eps"], ws[i]) for i, sp in enumerate(specs)]
+    opts = gk.default_options(assign_dtype="f32")
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gk.partition_batched(probs, options=opts)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    times, pp = [], 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs, st = gk.partition_batched(probs, options=opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        pp += sum(sp["n"] * r["balance_passes"] for sp, (_, _, _, r) in zip(specs, outs))
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        q = torch.tensor([pp], device=dev, dtype=torch.float64)
+        dist.all_reduce(q)
+        pp = float(q.item())
+    res = [r for _, _, _, r in outs]
+    # end to end: inputs from pinned host memory, block ids back, inside the timed region
+    hx = [torch.from_numpy(x).pin_memory() for x, _ in host]
+    hw = [torch.from_numpy(w).pin_memory() if w is not None else None for _, w in host]
+    hb = [torch.empty(sp["n"], dtype=torch.int32).pin_memory() for sp in specs]
+    e2e_ms, e2e_pp = 0.0, 0.0
+    for _ in range(max(1, min(3, args.steps))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(len(specs)):
+            xs[i].copy_(hx[i], non_blocking=True)
+            if ws[i] is not None:
+                ws[i].copy_(hw[i], non_blocking=True)
+        outs, st = gk.partition_batched(probs, options=opts)
+        for i, (b, _, _, _) in enumerate(outs):
+            hb[i].copy_(b, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_pp += sum(sp["n"] * r["balance_passes"] for sp, (_, _, _, r) in zip(specs, outs))
+    h2d = sum(x.nbytes + (0 if w is None else w.nbytes) for x, w in host)
+    if rank == 0:
+        ntot = sum(sp["n"] for sp in specs)
+        line = {"metric": METRIC, "value": pp / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": BATCHED_WORKLOAD, "instances": len(specs), "points": ntot,
+                           "n_range": [min(sp["n"] for sp in specs), max(sp["n"] for sp in specs)],
+                           "k_range": [min(sp["k"] for sp in specs), max(sp["k"] for sp in specs)],
+                           "weights": "uniform[1,10]", "assign": "f32",
+                           "l2": "a 512 MB write between timed steps", "parallelism": "single"},
+                "partition_time_s": total_ms / args.steps / 1e3,
+                "balance_passes_total": int(sum(r["balance_passes"] for r in res)),
+                "balance_passes_max": int(max(r["balance_passes"] for r in res)),
+                "balanced": int(sum(r["balanced"] for r in res)),
+                "bootstrap_ms": res[0]["time_bootstrap_ms"], "kmeans_loop_ms": res[0]["time_kmeans_ms"],
+                "gpu_launches": int(sum(r["kernel_launches"] for r in res)) * args.steps,
+                "clocks": clk, "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": e2e_pp / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 4 * ntot, "ms_per_step": e2e_ms / max(1, min(3, args.steps))}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -1190,104 +1190,82 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
                 thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
                 if (q < nval && !okq) flag |= 1u << q;
             }
-            // FP64 re-decision of the flagged points, only for candidates within the
-            // margin; warp-collective because the slow candidates are shuffled.
-            if (__any_sync(0xffffffffu, flag != 0u)) {
-                const double *g64 = p.g64_2 + (size_t)sel * p.k;
-                // flagged points in local arrays: this rare path stays compact (no unrolling)
-                float px[8][3], pthr[8];
-                double pE[8];
-                int pb[8];
+            // FP64 re-decision, one flagged point at a time: lanes take 32 candidates at
+            // a time, screen them with the FP32 value (every possible FP64 winner has
+            // E_fp32 <= thr) and evaluate the survivors in FP64 from the raw coordinates;
+            // the warp keeps the smallest value, the lowest center index on ties.
+            const double *g64 = p.g64_2 + (size_t)sel * p.k;
+            unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
+            while (lanes) {
+                const int Lf = __ffs(lanes) - 1;
+                lanes &= lanes - 1;
+                unsigned fl = __shfl_sync(0xffffffffu, flag, Lf);
+                while (fl) {
+                    const int q = __ffs(fl) - 1;
+                    fl &= fl - 1;
+                    float mx[3] = {0.f, 0.f, 0.f}, mt = 0.f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float2 v0 = xp[0][q >> 1], v1 = xp[1][q >> 1], v2 = xp[2][q >> 1];
-                    px[q][0] = (q & 1) ? v0.y : v0.x;
-                    px[q][1] = (q & 1) ? v1.y : v1.x;
-                    px[q][2] = D == 3 ? ((q & 1) ? v2.y : v2.x) : 0.0f;
-                    pthr[q] = thr[q];
-                    pE[q] = INFINITY;
-                    pb[q] = best[q];
-                }
-                auto recheck = [&](const float4 &qg, int c) {
-#pragma unroll 1
-                    for (int q = 0; q < 8; ++q) {
-                        if (!((flag >> q) & 1u)) continue;
-                        const float d0 = px[q][0] - qg.x, d1 = px[q][1] - qg.y;
-                        const float d2 = D == 3 ? px[q][2] - qg.z : 0.0f;
-                        const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-                        if (!(E32 <= pthr[q])) continue;  // cannot be the FP64 winner
-                        double s2 = 0.0;
+                    for (int qq = 0; qq < 8; ++qq) {
+                        if (qq == q) {
 #pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + i0 + q]
-                                                           : (double)p.X32[(size_t)j * p.n_pad + i0 + q];
-                            const double df = xj - p.C[c * D + j];
-                            s2 += df * df;
-                        }
-                        const double E = s2 * g64[c];
-                        if (E < pE[q]) {  // ascending center order: ties keep the lowest
-                            pE[q] = E;
-                            pb[q] = c;
+                            for (int j = 0; j < D; ++j) mx[j] = (qq & 1) ? xp[j][qq >> 1].y : xp[j][qq >> 1].x;
+                            mt = thr[qq];
                         }
                     }
-                };
-                if (flag) {
-                    for (int jj2 = 0; jj2 < nfast; ++jj2)
-                        recheck(S.rec[2 + 2 * jj2], __float_as_int(S.rec[3 + 2 * jj2].x));
-                }
-                // slow candidates: a sub-box needs one only if its lower bound is within the
-                // screen of some flagged point of the sub-box
-                float tfl = -INFINITY;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (!((flag >> q) & 1u)) continue;
-                    // E_fp32 >= E - B(E) grows with E: a center whose exact value exceeds
-                    // thr + 2 B(2 thr) has E_fp32 > thr whenever 2 B(2 thr) <= thr
-                    const float m2 = 2.0f * point_bound(q, sg, gl, 2.0f * thr[q]);
-                    tfl = fmaxf(tfl, m2 <= thr[q] ? thr[q] + m2 : INFINITY);
-                }
+                    for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, mx[j], Lf);
+                    mt = __shfl_sync(0xffffffffu, mt, Lf);
+                    const long long ip = (long long)t * kTile + Lf * 8 + q;
+                    double X[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-                for (int off = 1; off < 8; off <<= 1) tfl = fmaxf(tfl, __shfl_xor_sync(0xffffffffu, tfl, off));
-                for (int base = nfast; base < ncand; base += 32) {
-                    float4 mqg = make_float4(0.f, 0.f, 0.f, 0.f);
-                    int mc = 0;
-                    if (base + lane < ncand) slow_cand(base + lane, mqg, mc);
-                    unsigned need = 0;
+                    for (int j = 0; j < D; ++j)
+                        X[j] = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip] : (double)p.X32[(size_t)j * p.n_pad + ip];
+                    double bE = INFINITY;
+                    int bc = 0x7fffffff;
+                    for (int base = 0; base < ncand; base += 32) {
+                        const int i = base + lane;
+                        int c = 0x7fffffff;
+                        double E = INFINITY;
+                        if (i < ncand) {
+                            float4 qg;
+                            if (i < nfast) {
+                                qg = S.rec[2 + 2 * i];
+                                c = __float_as_int(S.rec[3 + 2 * i].x);
+                            } else {
+                                slow_cand(i, qg, c);
+                            }
+                            const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
+                            const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
+                            const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                            if (E32 <= mt) {
+                                double s2 = 0.0;
 #pragma unroll
-                    for (int s4 = 0; s4 < 4; ++s4) {
-                        const float ts = __shfl_sync(0xffffffffu, tfl, s4 * 8);
-                        float sm[3], sh[3];
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            sm[j] = __shfl_sync(0xffffffffu, sbm[j], s4 * 8);
-                            sh[j] = __shfl_sync(0xffffffffu, sbh[j], s4 * 8);
+                                for (int j = 0; j < D; ++j) {
+                                    const double df = X[j] - p.C[c * D + j];
+                                    s2 += df * df;
+                                }
+                                E = s2 * g64[c];
+                            }
                         }
-                        float l2 = 0.f;
-#pragma unroll
-                        for (int j = 0; j < D; ++j) {
-                            const float qj = j == 0 ? mqg.x : (j == 1 ? mqg.y : mqg.z);
-                            const float a = fabsf(qj - sm[j]);
-                            const float h = fmaf(4.0f * kU, fabsf(qj) + R, sh[j]);
-                            const float l = fmaxf(a - h, 0.0f);
-                            l2 = fmaf(l, l, l2);
+                        if (E < bE || (E == bE && c < bc)) {
+                            bE = E;
+                            bc = c;
                         }
-                        if (!(mqg.w * l2 * (1.0f - 1e-5f) > ts)) need = 1;
                     }
-                    unsigned todo = __ballot_sync(0xffffffffu, need && base + lane < ncand);
-                    while (todo) {
-                        const int j = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        float4 qg;
-                        qg.x = __shfl_sync(0xffffffffu, mqg.x, j);
-                        qg.y = __shfl_sync(0xffffffffu, mqg.y, j);
-                        qg.z = __shfl_sync(0xffffffffu, mqg.z, j);
-                        qg.w = __shfl_sync(0xffffffffu, mqg.w, j);
-                        const int c = __shfl_sync(0xffffffffu, mc, j);
-                        if (flag) recheck(qg, c);
+                    for (int off = 16; off; off >>= 1) {
+                        const double oE = __shfl_xor_sync(0xffffffffu, bE, off);
+                        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                        if (oE < bE || (oE == bE && oc < bc)) {
+                            bE = oE;
+                            bc = oc;
+                        }
+                    }
+                    if (lane == Lf && bc != 0x7fffffff) {
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq)
+                            if (qq == q) best[qq] = bc;
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < 8; ++q) best[q] = pb[q];
             }
             nre += __popc(flag);
         }
