@@ -124,6 +124,23 @@ class Clocks:
 # --------------------------------------------------------------------------------------
 # CPU baseline: the oracle's balance pass (assign + block weights + influence update)
 # --------------------------------------------------------------------------------------
+def replica_points(spec, rank: int):
+    """Points of rank's independent replica of a workload (rank 0: the workload itself)."""
+    from paper_1805_01208_gb300 import synth
+    return synth.make_points(spec["shape"], spec["n"], spec["d"], spec["seed"] + 1000 * rank,
+                             spec["dtype"])
+
+
+def reduce_over_ranks(total_ms: float, work: float, dist, device):
+    """Whole-job figures of N replicas: the slowest rank's time, the sum of their work."""
+    import torch
+    t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], device=device, dtype=torch.float64)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 def cpu_baseline(x, w, spec, seconds: float):
     import oracle
     cores = len(os.sched_getaffinity(0))
@@ -220,8 +237,7 @@ def main():
     if args.assign:
         spec["assign"] = args.assign
     if world > 1 and rank > 0:  # replicas: an independent instance per rank
-        x = synth.make_points(spec["shape"], spec["n"], spec["d"], spec["seed"] + 1000 * rank,
-                              spec["dtype"])
+        x = replica_points(spec, rank)
     n, d, k, eps = len(x), spec["d"], spec["k"], spec["eps"]
     xt = torch.from_numpy(x).to(dev)
     wt = None if w is None else torch.from_numpy(w).to(dev)
@@ -255,12 +271,7 @@ def main():
     total_ms = float(sum(times))
     points_passes = float(sum(n * r["balance_passes"] for r in results))
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pp = torch.tensor([points_passes], device=dev, dtype=torch.float64)
-        dist.all_reduce(pp)
-        points_passes = float(pp.item())
+        total_ms, points_passes = reduce_over_ranks(total_ms, points_passes, dist, dev)
     value = points_passes / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
     launches = int(sum(r["kernel_launches"] for r in results))
@@ -389,12 +400,7 @@ def run_batched(args):
     clk = clocks.stop()
     total_ms = float(sum(times))
     if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        q = torch.tensor([pp], device=dev, dtype=torch.float64)
-        dist.all_reduce(q)
-        pp = float(q.item())
+        total_ms, pp = reduce_over_ranks(total_ms, pp, dist, dev)
     res = [r for _, _, _, r in outs]
     # end to end: inputs from pinned host memory, block ids back, inside the timed region
     hx = [torch.from_numpy(x).pin_memory() for x, _ in host]
