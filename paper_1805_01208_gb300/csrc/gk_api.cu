@@ -114,7 +114,7 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.tiles = (float4 *)take((size_t)p.ntiles * 32);
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
-    p.heavy = (int *)take((size_t)p.ntiles * 4);
+    p.coop = (int *)take((size_t)p.ntiles * 4);
     p.bigs = (int *)take((size_t)p.nsupers * 12);
     p.blists = (int *)take((size_t)p.nsupers * kWarpList * 4);
     p.C = (double *)take((size_t)k * d * 8);
@@ -178,6 +178,25 @@ gk_status ensure_workspace(size_t bytes) {
         }                                 \
     } while (0)
 
+long long gcd_ll(long long a, long long b) {
+    while (b) {
+        long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Multiplier of the assignment's tile order (see assign_kernel): coprime to ntiles,
+// near 0.618 ntiles, so that consecutive positions land far apart on the curve.
+int tile_order_multiplier(int ntiles) {
+    if (ntiles <= 2) return 1;
+    long long m = (long long)(0.6180339887498949 * ntiles);
+    if (m < 1) m = 1;
+    while (gcd_ll(m, ntiles) != 1) ++m;
+    return (int)(m % ntiles == 0 ? 1 : m);
+}
+
 int exponent_above(double v) {  // smallest e with |v| < 2^e (v finite)
     if (v == 0.0) return 0;
     int e;
@@ -222,6 +241,7 @@ struct Call {
         p.weighted = weights != nullptr;
         p.ntiles = (int)(p.n_pad / kTile);
         p.nsupers = (p.ntiles + kSuperTiles - 1) / kSuperTiles;
+        p.qmul = tile_order_multiplier(p.ntiles);
         p.bits = d == 2 ? 32 : 21;
         int dev = 0;
         GK_CUDA(cudaGetDevice(&dev));

@@ -14,8 +14,8 @@
 //          candidates, 0, 0}, {tile origin xyz, tile radius}, then up to kCap candidates
 //          of 2 float4: {q xyz, g}, {center id (int32 bits), 0, 0, 0}; q = frame center
 //          relative to the tile origin, g = scaled 1/I^2, ascending center order.
-//   heavy  ntiles entries: from the front, tiles whose candidates do not all fit the bulk
-//          copy of the assignment; from the back, tiles taken by a whole CTA.
+//   coop   the tiles with more than kFastCands candidates (or an overflowed list), taken
+//          by a whole CTA of the assignment.
 //   per center: C, Cm (k x d FP64, input units), delta, S64, Iin (k FP64), influence and
 //          1/I^2 double-buffered (I2, g64_2: 2 x k FP64), cdata2 (2 x 2 float4 per center:
 //          {frame center hi xyz, g32}, {frame center lo xyz, 0}), 128-bit fixed-point
@@ -33,7 +33,7 @@ constexpr int kTile = 256;          // points per tile (one warp of the assign k
 constexpr int kSuperTiles = 16;     // tiles per supertile (one CTA of the filter kernel)
 constexpr int kCap = 128;           // candidate centers stored per tile
 constexpr int kFastCands = 32;      // candidates brought in with the tile's bulk copy
-constexpr int kCoopCands = 64;      // tiles with more candidates are taken by a whole CTA
+constexpr int kCoopCands = kFastCands;  // tiles with more candidates are taken by a whole CTA
 constexpr int kRecF4 = 2 + 2 * kCap;  // float4 per tile record (header + candidates)
 constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // bytes of one bulk copy
 constexpr int kKThreads = 32;       // threads per CTA of the k-sized kernels
@@ -76,8 +76,7 @@ struct Ctl {
     int iused_sel;                          // buffer the last assignment was computed with
     int gshift;                             // g32 = g * 2^-gshift
     unsigned int done_count;                // last-block-done counter (reset by the last block)
-    unsigned int heavy_cnt;                 // tiles in the heavy list (reset before each filter)
-    unsigned int coop_cnt;                  // tiles in the cooperative list (same)
+    unsigned int coop_cnt;                  // tiles in the cooperative list (reset before each filter)
     unsigned int big_cnt;                   // supertiles with long candidate lists (same)
     int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
@@ -103,6 +102,7 @@ struct Prob {
     long long n_pad;
     int d, k, dtype, weighted, assign_f64;
     int ntiles, nsupers;
+    int qmul;                   // tile order of the assignment: t = pos * qmul mod ntiles
     int bits, grid_m;           // Hilbert bits per axis and the scaling exponent b - E
     int Fw, Fx;                 // fixed-point exponents of weights and coordinate sums
     double origin[3];           // frame: (x - origin) * scale
@@ -124,7 +124,7 @@ struct Prob {
     float4 *tiles, *supers;
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;
-    int *heavy;
+    int *coop;                  // tiles of the cooperative path (ntiles entries)
     int *bigs;                  // per long-list supertile: index, list length, largest g (bits)
     int *blists;                // their candidate lists, kWarpList entries each
     int nsm;                    // streaming multiprocessors of the device

@@ -158,7 +158,6 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->maxS_key = 0ull;
         ctl->maxd_key = 0ull;
         ctl->nonempty = 0;
-        ctl->heavy_cnt = 0u;
         ctl->coop_cnt = 0u;
         ctl->big_cnt = 0u;
         if (h_move) cudaGraphSetConditional(h_move, 1u);
@@ -405,19 +404,17 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
     return L;
 }
 
-// Header of tile t's record and its entry in the heavy / cooperative lists (one
-// thread per tile).
+// Header of tile t's record (count, -1: scan all centers; the largest g the tile can
+// meet) and, for a tile with more than kCoopCands candidates, its entry in the
+// cooperative list (one thread per tile).
 __device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float gkept, float gall,
                                             const float4 &tb0) {
     const bool over = cnt > kCap;
     float4 *rec = p.trec + (size_t)t * kRecF4;
-    // count (-1: scan all centers) and the largest g the tile can meet
     rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
     rec[1] = tb0;
-    if (over || cnt > kCoopCands)
-        p.heavy[p.ntiles - 1 - (int)atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
-    else if (cnt > kFastCands)
-        p.heavy[atomicAdd(&p.ctl->heavy_cnt, 1u)] = t;
+    const bool coop = over || cnt > kCoopCands;
+    if (coop) p.coop[atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
     if (over) atomicAdd(&p.ctl->overflow_tiles, 1ull);
     long long nv = p.n - (long long)t * kTile;
     nv = nv > kTile ? kTile : nv;
@@ -463,38 +460,39 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         return;
     }
     // level 2, short list: lane = tile
-    if (!has_tile) return;
     const int *list = s_list[warp];
     const float4 *lcd = s_lcd[warp];
-    const float o[3] = {tb0.x, tb0.y, tb0.z};
-    const float h[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
-    float tt = INFINITY;
+    if (has_tile) {
+        const float o[3] = {tb0.x, tb0.y, tb0.z};
+        const float h[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
+        float tt = INFINITY;
 #pragma unroll 4
-    for (int i = 0; i < L; ++i) {
-        float lb, ub;
-        box_bounds<D>(lcd[2 * i], lcd[2 * i + 1], o, h, lb, ub);
-        tt = fminf(tt, ub);
-    }
-    const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
-    int cnt = 0;
-    float gkept = 0.0f;
-    float4 *rec = p.trec + (size_t)t * kRecF4;
-    for (int i = 0; i < L; ++i) {
-        const int c = list[i];
-        const float4 ch = lcd[2 * i], cl = lcd[2 * i + 1];
-        float lb, ub;
-        box_bounds<D>(ch, cl, o, h, lb, ub);
-        if (!(lb > tauT)) {  // L <= kLaneMax <= kCap: always stored
-            const float q0 = (ch.x - o[0]) + cl.x;
-            const float q1 = (ch.y - o[1]) + cl.y;
-            const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-            rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
-            rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
-            gkept = fmaxf(gkept, ch.w);
-            ++cnt;
+        for (int i = 0; i < L; ++i) {
+            float lb, ub;
+            box_bounds<D>(lcd[2 * i], lcd[2 * i + 1], o, h, lb, ub);
+            tt = fminf(tt, ub);
         }
+        const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
+        int cnt = 0;
+        float gkept = 0.0f;
+        float4 *rec = p.trec + (size_t)t * kRecF4;
+        for (int i = 0; i < L; ++i) {
+            const int c = list[i];
+            const float4 ch = lcd[2 * i], cl = lcd[2 * i + 1];
+            float lb, ub;
+            box_bounds<D>(ch, cl, o, h, lb, ub);
+            if (!(lb > tauT)) {  // L <= kLaneMax <= kCap: always stored
+                const float q0 = (ch.x - o[0]) + cl.x;
+                const float q1 = (ch.y - o[1]) + cl.y;
+                const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
+                rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
+                rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                gkept = fmaxf(gkept, ch.w);
+                ++cnt;
+            }
+        }
+        finish_tile(p, t, cnt, gkept, gall, tb0);
     }
-    finish_tile(p, t, cnt, gkept, gall, tb0);
 }
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
 static_assert(kSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
@@ -907,7 +905,6 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     }
     __syncwarp();
     const int sel = p.ctl->isel;
-    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
     const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4);
     unsigned long long nre = 0;
     {
@@ -915,7 +912,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         const int HC = (int)p.ctl->coop_cnt;
         float *scratch = reinterpret_cast<float *>(&st[0][0]);
         for (int ci = blockIdx.x; ci < HC; ci += gridDim.x) {
-            coop_tile<D, F64MODE>(p, p.heavy[p.ntiles - 1 - ci], scratch, kAWarps, &nre);
+            coop_tile<D, F64MODE>(p, p.coop[ci], scratch, kAWarps, &nre);
             __syncthreads();
         }
     }
@@ -930,42 +927,59 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         }
     };
     // Tiles come from kQueues interleaved queues: queue q serves positions q, q + kQueues,
-    // ... (one atomic per tile, requested two tiles ahead so that its latency and the
-    // read of the heavy list are hidden).  Positions [0, H) are the heavy tiles, served
-    // first; position H + t is tile t, skipped there when it is heavy.  A warp's
-    // positions increase, so once a stage holds no tile the other one holds none either.
-    // The queue state lives in lane 0 and is broadcast when a stage is consumed.
-    const int H = (int)p.ctl->heavy_cnt;
+    // ... (one atomic per tile, requested two tiles ahead so that its latency is
+    // hidden).  A tile with more than kFastCands candidates was taken by a cooperative
+    // CTA above: lane 0 reads the count of the tile's record when it resolves the
+    // position and marks the tile (kPass), so that no copy is issued for it and the
+    // warp passes over it without waiting.  A warp's positions increase, so once a
+    // stage holds no tile the other one holds none either.  The queue state lives in
+    // lane 0 and is broadcast when a stage is consumed.
+    constexpr int kPass = 1 << 30;
     const int qi = (blockIdx.x * kAWarps + w) & (kQueues - 1);
     unsigned *qctr = &p.ctl->tile_q[qi * kQueueStride];
-    // a queued tile: index in bits 0..29 (ntiles when the queue is empty), bit 30 set
-    // when it came from the heavy range
-    constexpr int kHv = 1 << 30;
-    auto resolve = [&](unsigned m) -> int {  // lane 0
+    // position -> tile (ntiles when the queue is empty) and its record count, whose load
+    // is only used one refill later
+    // Positions map to tiles through the permutation t = pos * qmul mod ntiles (qmul
+    // coprime to ntiles, near 0.618 ntiles): the warps working at the same time then
+    // hold tiles from all over the curve, whose blocks differ, instead of neighbouring
+    // tiles that all add to the weights of the same few blocks.
+    auto resolve = [&](unsigned m, int &tile, int &cnt) {  // lane 0
         const long long pos = (long long)qi + (long long)kQueues * m;
-        if (pos < H) return p.heavy[pos] | kHv;
-        return pos - H < (long long)p.ntiles ? (int)(pos - H) : p.ntiles;
+        if (pos >= p.ntiles) {
+            tile = p.ntiles;
+            cnt = 0;
+            return;
+        }
+        tile = (int)((unsigned long long)pos * (unsigned long long)p.qmul % (unsigned long long)p.ntiles);
+        cnt = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4].x));
     };
-    int tq0 = p.ntiles, tq1 = p.ntiles, t_next = p.ntiles;
+    auto mark = [&](int tile, int cnt) -> int {  // kPass for a cooperative tile
+        return (tile < p.ntiles && (cnt < 0 || cnt > kFastCands)) ? (tile | kPass) : tile;
+    };
+    int tq0 = p.ntiles, tq1 = p.ntiles, t_next = p.ntiles, c_next = 0;
     unsigned m_req = 0;
     if (lane == 0) {
         const unsigned m0 = atomicAdd(qctr, 1u), m1 = atomicAdd(qctr, 1u), m2 = atomicAdd(qctr, 1u);
         m_req = atomicAdd(qctr, 1u);
-        tq0 = resolve(m0);
-        tq1 = resolve(m1);
-        t_next = resolve(m2);
-        if ((tq0 & (kHv - 1)) < p.ntiles) issue(tq0 & (kHv - 1), 0);
-        if ((tq1 & (kHv - 1)) < p.ntiles) issue(tq1 & (kHv - 1), 1);
+        int c0, c1;
+        resolve(m0, tq0, c0);
+        resolve(m1, tq1, c1);
+        resolve(m2, t_next, c_next);
+        tq0 = mark(tq0, c0);
+        tq1 = mark(tq1, c1);
+        if (tq0 < p.ntiles) issue(tq0, 0);
+        if (tq1 < p.ntiles) issue(tq1, 1);
     }
     // stage b is free again: load the next tile into it (lane 0)
     auto refill = [&](int b) {
         if (lane == 0) {
+            const int tn = mark(t_next, c_next);
             if (b)
-                tq1 = t_next;
+                tq1 = tn;
             else
-                tq0 = t_next;
-            if ((t_next & (kHv - 1)) < p.ntiles) issue(t_next & (kHv - 1), b);
-            t_next = resolve(m_req);
+                tq0 = tn;
+            if (tn < p.ntiles) issue(tn, b);
+            resolve(m_req, t_next, c_next);
             m_req = atomicAdd(qctr, 1u);
         }
     };
@@ -973,8 +987,12 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     for (int it = 0;; ++it) {
         const int b = it & 1;
         const int tqb = __shfl_sync(0xffffffffu, b ? tq1 : tq0, 0);
-        const int t = tqb & (kHv - 1);
-        if (t >= p.ntiles) break;  // the other stage holds no tile either
+        if ((tqb & (kPass - 1)) >= p.ntiles) break;  // the other stage holds no tile either
+        if (tqb & kPass) {  // a cooperative tile: nothing was copied into this stage
+            refill(b);
+            continue;
+        }
+        const int t = tqb;
         const unsigned phb = b ? ph1 : ph0;
         bool ok = mbar_wait_bounded(&bar[w][b], phb);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -982,27 +1000,17 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             // bounded wait for the copies still in flight (this stage and the other).
             if (lane == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
             mbar_wait_bounded(&bar[w][b], phb);
-            if ((__shfl_sync(0xffffffffu, b ? tq0 : tq1, 0) & (kHv - 1)) < p.ntiles)
+            if (__shfl_sync(0xffffffffu, b ? tq0 : tq1, 0) < p.ntiles)
                 mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
             return;
         }
         if (b) ph1 ^= 1u; else ph0 ^= 1u;
         const AStage &S = st[w][b];
-        const int cnt = __float_as_int(S.rec[0].x);
-        const bool from_heavy = (tqb & kHv) != 0;
-        if (!from_heavy && (cnt < 0 || cnt > kFastCands)) {
-            // a heavy tile met again in the ordinary range: already done; take the next
-            __syncwarp();
-            refill(b);
-            continue;
-        }
+        const int ncand = __float_as_int(S.rec[0].x);  // 0 < ncand <= kFastCands
         const float gl = S.rec[0].y;  // largest g among the tile's candidates
         const float sg = sqrtf(gl);
         const float4 ob = S.rec[1];
         const float o[3] = {ob.x, ob.y, ob.z};
-        const bool all = cnt < 0;
-        const int ncand = all ? p.k : cnt;
-        const float4 *grec = p.trec + (size_t)t * kRecF4;
         const long long i0 = (long long)t * kTile + lane * 8;
         long long nv = p.n - i0;
         const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
@@ -1025,23 +1033,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             E2[q] = INFINITY;
             best[q] = 0;
         }
-        // Candidates: the first kFastCands come with the stage (shared-memory broadcast).
-        // The rest (or all centers when the tile overflowed) are fetched 32 at a time,
-        // one per lane, and pruned per 64-point sub-box (8 lanes) with a lower bound on
-        // the effective distance before the warp evaluates the ones some sub-box needs.
-        const int nfast = all ? 0 : min(ncand, kFastCands);
-        const bool slow = ncand > nfast;
-        auto slow_cand = [&](int jj, float4 &qg, int &c) {  // jj < ncand
-            if (!all) {
-                qg = grec[2 + 2 * jj];
-                c = __float_as_int(grec[3 + 2 * jj].x);
-            } else {
-                c = jj;
-                const float4 ch = cd[2 * c], cl = cd[2 * c + 1];
-                qg = make_float4((ch.x - o[0]) + cl.x, (ch.y - o[1]) + cl.y,
-                                 D == 3 ? (ch.z - o[2]) + cl.z : 0.0f, ch.w);
-            }
-        };
+        // candidates from the stage (shared-memory broadcast), two at a time
         auto consume = [&](const float4 &qg, int c) {
             const float2 g2 = make_float2(qg.w, qg.w), nqx = make_float2(-qg.x, -qg.x),
                          nqy = make_float2(-qg.y, -qg.y), nqz = make_float2(-qg.z, -qg.z);
@@ -1061,139 +1053,45 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             }
         };
         int jj = 0;
-        for (; jj + 1 < nfast; jj += 2) {
+        for (; jj + 1 < ncand; jj += 2) {
             const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
             const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
             consume(qa, ca);
             consume(qb, cb);
         }
-        if (jj < nfast) {
+        if (jj < ncand) {
             const float4 qa = S.rec[2 + 2 * jj];
             consume(qa, __float_as_int(S.rec[3 + 2 * jj].x));
         }
-        // error-bound constants (FP64 mode); see the comment above
-        const float R = p.R;
-        const float sd = sqrtf((float)D);
-        const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
-        // coordinate term with the largest |x'| of the lane's points
-        float xn2 = 0.0f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
-            xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
-        }
-        const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
-        auto point_bound = [&](int q, float sgl, float glv, float Eref) -> float {
-            (void)q;
-            return cert_bound(e0, sgl, glv, beta2, Eref);
-        };
-        // 64-point sub-boxes (lanes 8s..8s+7) in tile-local coordinates, widened so that
-        // they contain the exact points
-        float sbm[3] = {0.f, 0.f, 0.f}, sbh[3] = {0.f, 0.f, 0.f};
-        if (__any_sync(0xffffffffu, slow)) {
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                float lo = INFINITY, hi = -INFINITY;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (2 * q < nval) {
-                        lo = fminf(lo, xp[j][q].x);
-                        hi = fmaxf(hi, xp[j][q].x);
-                    }
-                    if (2 * q + 1 < nval) {
-                        lo = fminf(lo, xp[j][q].y);
-                        hi = fmaxf(hi, xp[j][q].y);
-                    }
-                }
-#pragma unroll
-                for (int off = 1; off < 8; off <<= 1) {
-                    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
-                    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
-                }
-                if (lo > hi) {  // a sub-box without points: never needs a candidate
-                    lo = 0.f;
-                    hi = 0.f;
-                }
-                sbm[j] = 0.5f * lo + 0.5f * hi;
-                sbh[j] = __fadd_ru(fmaxf(__fsub_ru(hi, sbm[j]), __fsub_ru(sbm[j], lo)), 16.0f * kU * R);
-            }
-        }
-        // sub-box threshold: no candidate whose lower bound exceeds it can become a point's
-        // best (FP32 form) or best/second or pass the FP64 screen (FP64 mode)
-        auto subbox_threshold = [&]() -> float {
-            float tmax = -INFINITY;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q >= nval) continue;
-                float tq;
-                if (F64MODE)
-                    tq = E2[q] == INFINITY ? INFINITY : E2[q] + 2.0f * point_bound(q, sg, gl, E2[q]);
-                else
-                    tq = E1[q];
-                tmax = fmaxf(tmax, tq);
-            }
-#pragma unroll
-            for (int off = 1; off < 8; off <<= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, off));
-            return tmax;
-        };
-        if (__any_sync(0xffffffffu, slow)) {
-            for (int base = nfast; base < ncand; base += 32) {
-                float4 mqg = make_float4(0.f, 0.f, 0.f, 0.f);
-                int mc = 0;
-                if (base + lane < ncand) slow_cand(base + lane, mqg, mc);
-                const float tsub = subbox_threshold();
-                // lane j's candidate: needed by some sub-box?
-                unsigned need = 0;
-#pragma unroll
-                for (int s4 = 0; s4 < 4; ++s4) {
-                    const float ts = __shfl_sync(0xffffffffu, tsub, s4 * 8);
-                    float sm[3], sh[3];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        sm[j] = __shfl_sync(0xffffffffu, sbm[j], s4 * 8);
-                        sh[j] = __shfl_sync(0xffffffffu, sbh[j], s4 * 8);
-                    }
-                    float l2 = 0.f;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        const float qj = j == 0 ? mqg.x : (j == 1 ? mqg.y : mqg.z);
-                        const float a = fabsf(qj - sm[j]);
-                        const float h = fmaf(4.0f * kU, fabsf(qj) + R, sh[j]);
-                        const float l = fmaxf(a - h, 0.0f);
-                        l2 = fmaf(l, l, l2);
-                    }
-                    if (!(mqg.w * l2 * (1.0f - 1e-5f) > ts)) need = 1;
-                }
-                unsigned todo = __ballot_sync(0xffffffffu, need && base + lane < ncand);
-                while (todo) {
-                    const int j = __ffs(todo) - 1;
-                    todo &= todo - 1;
-                    float4 qg;
-                    qg.x = __shfl_sync(0xffffffffu, mqg.x, j);
-                    qg.y = __shfl_sync(0xffffffffu, mqg.y, j);
-                    qg.z = __shfl_sync(0xffffffffu, mqg.z, j);
-                    qg.w = __shfl_sync(0xffffffffu, mqg.w, j);
-                    consume(qg, __shfl_sync(0xffffffffu, mc, j));
-                }
-            }
-        }
         if (F64MODE) {
+            // error-bound constants; see the comment above
+            const float R = p.R;
+            const float sd = sqrtf((float)D);
+            const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
+            // coordinate term with the largest |x'| of the lane's points
+            float xn2 = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
+                xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
+            }
+            const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
             unsigned flag = 0;
             float thr[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float B = point_bound(q, sg, gl, E2[q]);
+                const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
                 const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
                 const bool okq = single || (E2[q] - E1[q]) > 2.0f * B;
                 thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
                 if (q < nval && !okq) flag |= 1u << q;
             }
-            // FP64 re-decision, one flagged point at a time: lanes take 32 candidates at
-            // a time, screen them with the FP32 value (every possible FP64 winner has
-            // E_fp32 <= thr) and evaluate the survivors in FP64 from the raw coordinates;
-            // the warp keeps the smallest value, the lowest center index on ties.
+            // FP64 re-decision, one flagged point at a time: lane j takes candidate j,
+            // screens it with the FP32 value (every possible FP64 winner has E_fp32 <=
+            // thr) and evaluates a survivor in FP64 from the raw coordinates; the warp
+            // keeps the smallest value, the lowest center index on ties.
             const double *g64 = p.g64_2 + (size_t)sel * p.k;
             unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
             while (lanes) {
@@ -1216,39 +1114,24 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
                     for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, mx[j], Lf);
                     mt = __shfl_sync(0xffffffffu, mt, Lf);
                     const long long ip = (long long)t * kTile + Lf * 8 + q;
-                    double X[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-                    for (int j = 0; j < D; ++j)
-                        X[j] = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip] : (double)p.X32[(size_t)j * p.n_pad + ip];
                     double bE = INFINITY;
                     int bc = 0x7fffffff;
-                    for (int base = 0; base < ncand; base += 32) {
-                        const int i = base + lane;
-                        int c = 0x7fffffff;
-                        double E = INFINITY;
-                        if (i < ncand) {
-                            float4 qg;
-                            if (i < nfast) {
-                                qg = S.rec[2 + 2 * i];
-                                c = __float_as_int(S.rec[3 + 2 * i].x);
-                            } else {
-                                slow_cand(i, qg, c);
-                            }
-                            const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
-                            const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
-                            const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-                            if (E32 <= mt) {
-                                double s2 = 0.0;
+                    if (lane < ncand) {
+                        const float4 qg = S.rec[2 + 2 * lane];
+                        const int c = __float_as_int(S.rec[3 + 2 * lane].x);
+                        const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
+                        const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
+                        const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                        if (E32 <= mt) {
+                            double s2 = 0.0;
 #pragma unroll
-                                for (int j = 0; j < D; ++j) {
-                                    const double df = X[j] - p.C[c * D + j];
-                                    s2 += df * df;
-                                }
-                                E = s2 * g64[c];
+                            for (int j = 0; j < D; ++j) {
+                                const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip]
+                                                               : (double)p.X32[(size_t)j * p.n_pad + ip];
+                                const double df = xj - p.C[c * D + j];
+                                s2 += df * df;
                             }
-                        }
-                        if (E < bE || (E == bE && c < bc)) {
-                            bE = E;
+                            bE = s2 * g64[c];
                             bc = c;
                         }
                     }
@@ -1368,8 +1251,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
         ctl->maxS_key = 0ull;
         ctl->maxg_key = 0ull;
-        ctl->heavy_cnt = 0u;  // the next filter rebuilds the heavy and cooperative lists
-        ctl->coop_cnt = 0u;
+        ctl->coop_cnt = 0u;  // the next filter rebuilds the cooperative list
         ctl->big_cnt = 0u;
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
