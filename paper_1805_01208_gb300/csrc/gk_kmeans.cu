@@ -1301,8 +1301,10 @@ template <typename T, int D>
 __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     count_launch(p.ctl);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int t = blockIdx.x * kAssignWarps + w;
-    if (t >= p.ntiles) return;
+    const int pos = blockIdx.x * kAssignWarps + w;
+    if (pos >= p.ntiles) return;
+    // the tile order of the assignment: neighbouring warps take tiles of different blocks
+    const int t = (int)((unsigned long long)pos * (unsigned long long)p.qmul % (unsigned long long)p.ntiles);
     const long long i0 = (long long)t * kTile + lane * 8;
     long long nv = p.n - i0;
     const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
