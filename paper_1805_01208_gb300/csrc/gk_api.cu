@@ -132,6 +132,8 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.cdata2 = (float4 *)take((size_t)2 * k * 32);
     p.ngroups = (int)((k + kGroup - 1) / kGroup);
     p.gdata2 = (float4 *)take((size_t)2 * p.ngroups * 32);
+    p.nsgroups = p.ngroups > 2 * kSuperGroup ? (p.ngroups + kSuperGroup - 1) / kSuperGroup : 0;
+    p.sgdata = (float4 *)take((size_t)(p.nsgroups > 0 ? p.nsgroups : 1) * 32);
     b.block_stage = stage_block ? (int *)take((size_t)n * 4) : nullptr;
     b.perm_stage = perm_out ? (long long *)take((size_t)n * 8) : nullptr;
     return off;

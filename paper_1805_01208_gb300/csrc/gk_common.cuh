@@ -21,7 +21,8 @@
 //          {frame center hi xyz, g32}, {frame center lo xyz, 0}), 128-bit fixed-point
 //          block weights and coordinate sums, ordered-key bounding boxes.
 //   per group of 32 consecutive centers, double-buffered like cdata2 (gdata2, 2 float4):
-//          {box mid xyz, smallest g32}, {box half extents xyz, largest g32}.
+//          {box mid xyz, smallest g32}, {box half extents xyz, largest g32}; the same per
+//          supergroup of 32 groups (sgdata, rebuilt from the current buffer's groups).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,7 +40,8 @@ constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // bytes of one b
 constexpr int kKThreads = 32;       // threads per CTA of the k-sized kernels
 constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
 constexpr int kGroup = 32;          // centers per group record (one CTA of the k-sized kernels)
-constexpr int kGroupCap = 1024;     // group records held in shared memory by the filter
+constexpr int kSuperGroup = 32;     // groups per supergroup record (used when ngroups > 64)
+constexpr int kWarpSG = 8;          // kept supergroups per supertile (more: sweep every group)
 constexpr int kQueues = 8;          // interleaved tile queues of the assignment
 constexpr int kWarpList = 512;      // level-1 candidate list kept per supertile by the filter
 constexpr int kWarpGroups = 64;     // kept center groups per supertile
@@ -136,6 +138,8 @@ struct Prob {
     float4 *cdata2;             // 2 buffers x 2 float4 per block
     float4 *gdata2;             // 2 buffers x 2 float4 per group of kGroup blocks
     int ngroups;
+    float4 *sgdata;             // 2 float4 per supergroup of kSuperGroup groups (current buffer)
+    int nsgroups;               // 0: no supergroup level
     Ctl *ctl;
 };
 

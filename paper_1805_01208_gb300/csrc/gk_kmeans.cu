@@ -92,6 +92,47 @@ __device__ __forceinline__ void write_group(const Prob &p, float4 *gd, bool vali
     }
 }
 
+// Supergroup record sg (one CTA of 32 threads, lane = group): union of the boxes of its
+// groups' records in the current buffer (rounded outwards) and the range of their g.
+__global__ void __launch_bounds__(kSuperGroup) supergroup_kernel(Prob p) {
+    count_launch(p.ctl);
+    const int lane = threadIdx.x;
+    const int g = blockIdx.x * kSuperGroup + lane;
+    const float4 *gd = p.gdata2 + (size_t)p.ctl->isel * 2 * p.ngroups;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float gmn = INFINITY, gmx = 0.0f;
+    if (g < p.ngroups) {
+        const float4 m = gd[2 * g], h = gd[2 * g + 1];
+        const float mm[3] = {m.x, m.y, m.z}, hh[3] = {h.x, h.y, h.z};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = __fsub_rd(mm[j], hh[j]);
+            hi[j] = __fadd_ru(mm[j], hh[j]);
+        }
+        gmn = m.w;
+        gmx = h.w;
+    }
+    for (int off = 16; off; off >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], off));
+            hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], off));
+        }
+        gmn = fminf(gmn, __shfl_xor_sync(0xffffffffu, gmn, off));
+        gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, off));
+    }
+    if (lane == 0) {
+        float mid[3], half[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            mid[j] = 0.5f * lo[j] + 0.5f * hi[j];
+            half[j] = fmaxf(__fsub_ru(hi[j], mid[j]), __fsub_ru(mid[j], lo[j]));
+        }
+        p.sgdata[2 * blockIdx.x] = make_float4(mid[0], mid[1], mid[2], gmn);
+        p.sgdata[2 * blockIdx.x + 1] = make_float4(half[0], half[1], half[2], gmx);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T block_reduce_max(T v, T *red) {  // all threads get the result
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -254,15 +295,19 @@ __device__ __forceinline__ void group_bounds(const float4 &gm, const float4 &gh,
 // the supertile's candidates to glist_out (kWarpList entries, global) and its first
 // kLaneMax entries to list (shared), and returns its length (> kWarpList: the list
 // did not fit, every center is a candidate); gall gets the largest g of all centers.
-// Loads of a sweep are issued together and the lower bounds of the first sweep are
-// kept in registers, so that the second sweep does not wait on memory again.
+//
+// tau is first bounded by the exact upper bounds of the centers of the nearest group
+// (the group with the smallest lower bound, found inside the nearest supergroup when
+// there are supergroups): every supergroup and group whose lower bound exceeds that
+// bound is dropped (it holds no center that passes the test below, nor the center
+// that attains tau).  Then tau and the list from the remaining groups' centers.
 constexpr int kGroupRegs = 8;   // group chunks whose bounds stay in registers
 constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in registers
 
 template <int D>
 __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4 *cd, const float4 *gd,
-                                              int *list, float4 *lcd, int *glist, int *glist_out,
-                                              float &gall) {
+                                              int *list, float4 *lcd, int *glist, int *sglist,
+                                              int *glist_out, float &gall) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ng = p.ngroups;
@@ -277,50 +322,74 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         sh[1] = __fadd_ru(b.y, infl);
         sh[2] = __fadd_ru(b.z, infl);
     }
-    // groups: an upper bound of tau, and the largest g of all centers
-    float tg = INFINITY, ga = 0.0f;
+    // warp-wide argmin of (value, index), the smallest index on ties
+    auto argmin = [&](float &v, int &i) {
+        for (int off = 16; off; off >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, v, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, i, off);
+            if (ov < v || (ov == v && oi < i)) {
+                v = ov;
+                i = oi;
+            }
+        }
+    };
+    float ga = 0.0f;
+    const int nsg = p.nsgroups;
+    float sglb = INFINITY;  // lane's supergroup lower bound (supergroup index = lane)
+    int g0 = 0, g1 = ng;    // groups searched for the nearest one
+    if (nsg > 0) {
+        float nl = INFINITY;
+        int ni = 0x7fffffff;
+        for (int si = lane; si < nsg; si += 32) {
+            const float4 m = __ldg(&p.sgdata[2 * si]), h = __ldg(&p.sgdata[2 * si + 1]);
+            float lb, ub;
+            group_bounds<D>(m, h, so, sh, lb, ub);
+            ga = fmaxf(ga, h.w);
+            if (si == lane) sglb = lb;
+            if (lb < nl) {
+                nl = lb;
+                ni = si;
+            }
+        }
+        argmin(nl, ni);
+        if (ni != 0x7fffffff) {
+            g0 = ni * kSuperGroup;
+            g1 = min(ng, g0 + kSuperGroup);
+        }
+    }
+    // the nearest group: sweep of all groups (or of the nearest supergroup's groups),
+    // with the bounds of the first chunks kept in registers for the keep pass
     float glb[kGroupRegs];
 #pragma unroll
     for (int r = 0; r < kGroupRegs; ++r) glb[r] = INFINITY;
+    float tg = INFINITY, nl = INFINITY;
+    int ni = 0x7fffffff;
 #pragma unroll 4
-    for (int r = 0; r * 32 < ng; ++r) {
-        const int gi = r * 32 + lane;
-        if (gi < ng) {
+    for (int r = 0; g0 + r * 32 < g1; ++r) {
+        const int gi = g0 + r * 32 + lane;
+        if (gi < g1) {
             const float4 gm = __ldg(&gd[2 * gi]), gh = __ldg(&gd[2 * gi + 1]);
             float lb, ub;
             group_bounds<D>(gm, gh, so, sh, lb, ub);
             tg = fminf(tg, ub);
-            ga = fmaxf(ga, gh.w);
+            if (nsg == 0) ga = fmaxf(ga, gh.w);
+            if (lb < nl) {
+                nl = lb;
+                ni = gi;
+            }
 #pragma unroll
             for (int q = 0; q < kGroupRegs; ++q)
                 if (q == r) glb[q] = lb;
         }
     }
-    // the nearest group (smallest lower bound): its centers' exact upper bounds give a
-    // much tighter bound of tau than the group boxes do
-    float nlb = INFINITY;
-    int ngi = 0x7fffffff;
-#pragma unroll
-    for (int r = 0; r < kGroupRegs; ++r) {
-        const int gi = r * 32 + lane;
-        if (gi < ng && glb[r] < nlb) {
-            nlb = glb[r];
-            ngi = gi;
-        }
-    }
     for (int off = 16; off; off >>= 1) {
         tg = fminf(tg, __shfl_xor_sync(0xffffffffu, tg, off));
         ga = fmaxf(ga, __shfl_xor_sync(0xffffffffu, ga, off));
-        const float olb = __shfl_xor_sync(0xffffffffu, nlb, off);
-        const int ogi = __shfl_xor_sync(0xffffffffu, ngi, off);
-        if (olb < nlb || (olb == nlb && ogi < ngi)) {
-            nlb = olb;
-            ngi = ogi;
-        }
     }
+    argmin(nl, ni);
     gall = ga;
-    if (ngi != 0x7fffffff) {
-        const int c = ngi * kGroup + lane;
+    if (ni != 0x7fffffff) {
+        const int c = ni * kGroup + lane;
         float t1 = INFINITY;
         if (c < p.k) {
             float lb, ub;
@@ -331,13 +400,40 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         tg = fminf(tg, t1);
     }
     const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
+    // chunks of 32 groups to test: all groups, or those of the kept supergroups
+    int nchunk = (ng + 31) / 32;
+    bool by_sg = false;
+    if (nsg > 0) {
+        int nks = 0;
+        for (int r = 0; r * 32 < nsg; ++r) {
+            const int si = r * 32 + lane;
+            bool keep = false;
+            if (si < nsg) {
+                float lb = sglb;
+                if (r > 0) {
+                    float ub;
+                    group_bounds<D>(__ldg(&p.sgdata[2 * si]), __ldg(&p.sgdata[2 * si + 1]), so, sh, lb, ub);
+                }
+                keep = !(lb > tauG);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int pos = nks + __popc(bal & lt);
+            if (keep && pos < kWarpSG) sglist[pos] = si;
+            nks += __popc(bal);
+        }
+        __syncwarp();
+        if (nks <= kWarpSG) {
+            by_sg = true;
+            nchunk = nks;
+        }
+    }
     int ngk = 0;  // kept groups, ascending
-    for (int r = 0; r * 32 < ng; ++r) {
-        const int gi = r * 32 + lane;
+    for (int r = 0; r < nchunk; ++r) {
+        const int gi = (by_sg ? sglist[r] * kSuperGroup : r * 32) + lane;
         bool keep = false;
         if (gi < ng) {
             float lb = INFINITY;
-            if (r < kGroupRegs) {
+            if (!by_sg && nsg == 0 && r < kGroupRegs) {
 #pragma unroll
                 for (int q = 0; q < kGroupRegs; ++q)
                     if (q == r) lb = glb[q];
@@ -431,6 +527,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     __shared__ int s_list[kFilterWarps][kLaneMax];     // short level-1 lists
     __shared__ float4 s_lcd[kFilterWarps][2 * kLaneMax];  // their center data
     __shared__ int s_grp[kFilterWarps][kWarpGroups];   // kept groups (scratch of level 1)
+    __shared__ int s_sg[kFilterWarps][kWarpSG];        // kept supergroups (scratch of level 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x < kQueues) p.ctl->tile_q[threadIdx.x * kQueueStride] = 0u;
     const int s = blockIdx.x * kFilterWarps + warp;
@@ -449,7 +546,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     }
     float gall;
     int *gl_out = p.blists + (size_t)s * kWarpList;
-    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp], gl_out, gall);
+    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp], s_sg[warp],
+                                    gl_out, gall);
     if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
             const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
@@ -1546,9 +1644,15 @@ static void *centroid_fn(int d, int dtype) {
 }
 static int tile_warp_grid(const Prob &p) { return (p.ntiles + kAssignWarps - 1) / kAssignWarps; }
 
+// Supergroup records of the current buffer, after every change of the group records.
+static void launch_supergroups(const Prob &p, cudaStream_t s) {
+    if (p.nsgroups > 0) supergroup_kernel<<<p.nsgroups, kSuperGroup, 0, s>>>(p);
+}
+
 cudaError_t launch_init(const Prob &p, cudaStream_t s) {
     init_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, 0, 0);
     init_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+    launch_supergroups(p, s);
     return cudaGetLastError();
 }
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s) { return launch_init(p, s); }
@@ -1587,6 +1691,7 @@ cudaError_t launch_assign(const Prob &p, cudaStream_t s) {
 }
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s) {
     balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0);
+    if (mode != 2) launch_supergroups(p, s);
     return cudaGetLastError();
 }
 cudaError_t launch_pass(const Prob &p, int mode, cudaStream_t s) {
@@ -1610,7 +1715,10 @@ cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s) {
                                      dim3(kAssignWarps * 32), args1, 0, s);
     if (e != cudaSuccess) return e;
     finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
-    if (mode == 0) finalize_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+    if (mode == 0) {
+        finalize_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+        launch_supergroups(p, s);
+    }
     return cudaGetLastError();
 }
 
@@ -1690,6 +1798,8 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
     NodeAdder top{g};
     top.kernel((void *)init_a_kernel, kg, kb, a_init);
     top.kernel((void *)init_b_kernel, kg, kb, a_p);
+    const dim3 sgg(p.nsgroups > 0 ? p.nsgroups : 1), sgb(kSuperGroup);
+    if (p.nsgroups > 0) top.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
     cudaGraph_t body_move = top.loop(h_move);
     if (body_move) {
         NodeAdder mv{body_move};
@@ -1700,11 +1810,13 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
             bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
+            if (p.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
             if (bl.err != cudaSuccess) mv.err = bl.err;
         }
         mv.kernel(centroid_fn(p.d, p.dtype), tg, tb, a_p);
         mv.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
         mv.kernel((void *)finalize_b_kernel, kg, kb, a_p);
+        if (p.nsgroups > 0) mv.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
         if (mv.err != cudaSuccess) top.err = mv.err;
     }
     top.kernel((void *)final_begin_kernel, dim3(1), dim3(32), a_fb);
@@ -1715,6 +1827,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
         fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
+        if (p.nsgroups > 0) fl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
         if (fl.err != cudaSuccess) top.err = fl.err;
     }
     return top.err;

@@ -149,6 +149,21 @@ def test_assign_unsorted_points_and_many_centers(gk):
     _assert_same_assignment(_np(block), x, C, I)
 
 
+@pytest.mark.parametrize("coherent", [True, False])
+def test_assign_with_supergroups(gk, coherent):
+    """k = 6000 centers (188 groups of 32, 6 supergroups): the filter prunes supergroups
+    before groups.  Curve-ordered centers give compact supergroups; random centers give
+    supergroups spanning the domain (the filter then sweeps every group)."""
+    x = _sorted(synth.make_points("gmm", 60_000, 2, 19, "f64"))
+    k = 6000
+    rng = np.random.default_rng(2)
+    C = oracle.sfc_centers(x, k) if coherent else rng.random((k, 2))
+    I = rng.uniform(0.9, 1.1, k)
+    for dt in ("f64", "f32"):
+        block, _ = gk.assign(_dev(x), _dev(C), _dev(I), assign_dtype=dt)
+        _assert_same_assignment(_np(block), x, C, I, max_frac=0.0 if dt == "f64" else 1e-3)
+
+
 def test_assign_weighted_block_weights(gk):
     x = _sorted(_points("gmm", 30_000, 2, 19, "f64"))
     w = synth.uniform_weights(len(x), 19)
