@@ -1176,14 +1176,25 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
                 xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
             }
             const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
+            // B grows with E: one bound at the lane's largest finite runner-up certifies
+            // most points; a point it does not certify gets its own bound
+            float e2max = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (E2[q] < INFINITY) e2max = fmaxf(e2max, E2[q]);
+            const float Bl = cert_bound(e0, sg, gl, beta2, e2max);
             unsigned flag = 0;
             float thr[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
                 const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
-                const bool okq = single || (E2[q] - E1[q]) > 2.0f * B;
-                thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
+                bool okq = single || (E2[q] - E1[q]) > 2.0f * Bl;
+                thr[q] = INFINITY;
+                if (!okq) {
+                    const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
+                    okq = (E2[q] - E1[q]) > 2.0f * B;
+                    thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
+                }
                 if (q < nval && !okq) flag |= 1u << q;
             }
             // FP64 re-decision, one flagged point at a time: lane j takes candidate j,
