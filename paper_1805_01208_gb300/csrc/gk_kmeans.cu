@@ -1308,7 +1308,6 @@ __global__ void block_weights_kernel(Prob p) {
 __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
                                                             cudaGraphConditionalHandle h) {
     count_launch(p.ctl);
-    __shared__ double red[32];
     Ctl *ctl = p.ctl;
     if (blockIdx.x == 0 && threadIdx.x == 0) {  // the assignment kernel ran just before
         ctl->assign_ns += globaltimer_ns() - ctl->t_assign0;
@@ -1349,8 +1348,12 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         const float hi[3] = {hc.x, hc.y, hc.z};
         write_group(p, p.gdata2 + (size_t)nsel * 2 * p.ngroups, c < p.k, hi, hc.w);
     }
-    double mS = block_reduce_max(S, red);
-    double mg = block_reduce_max(gnew, red);
+    // the CTA is one warp (kKThreads == 32): warp reductions of the two maxima
+    double mS = S, mg = gnew;
+    for (int off = 16; off; off >>= 1) {
+        mS = fmax(mS, __shfl_xor_sync(0xffffffffu, mS, off));
+        mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, off));
+    }
     if (threadIdx.x == 0) {
         atomicMax(&ctl->maxS_key, okey_f64(mS));
         if (mode != 2) atomicMax(&ctl->maxg_key, okey_f64(mg));
