@@ -108,6 +108,12 @@ def lib():
         L.or_balanced_kmeans.restype = i32
         L.or_partition.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P]
         L.or_partition.restype = i32
+        L.or_sample_first.argtypes = [i64, i32, i64]
+        L.or_sample_first.restype = i64
+        L.or_sample_rounds.argtypes = [i64, i64, i32]
+        L.or_sample_rounds.restype = i32
+        L.or_partition_sampled.argtypes = [P, i32, P, i64, i32, i32, dbl, P, i64, P, P, P, P, P]
+        L.or_partition_sampled.restype = i32
         _lib = L
     return _lib
 
@@ -256,4 +262,35 @@ def partition(x, w, k: int, eps: float, options: Options | None = None):
     opt = options if options is not None else default_options()
     lib().or_partition(_ptr(x), is_f32, _ptr(w), n, d, k, eps, ctypes.byref(opt), _ptr(A),
                        _ptr(C), _ptr(I), ctypes.byref(res))
+    return {"A": A, "C": C, "I": I, "result": res.as_dict()}
+
+
+def sample_first(n: int, k: int, sample0: int = 0) -> int:
+    """Size of the first sample of the random initialization (Section 4.5)."""
+    return int(lib().or_sample_first(n, k, sample0))
+
+
+def sample_rounds(n: int, m0: int, max_iter: int = 50) -> int:
+    """Number of sample rounds of the random initialization (Section 4.5)."""
+    return int(lib().or_sample_rounds(n, m0, max_iter))
+
+
+def partition_sampled(x, w, k: int, eps: float, order, sample0: int = 0,
+                      options: Options | None = None):
+    """Whole partitioner with the random initialization of Section 4.5; order is a
+    permutation of the input indices (the random order of the points), sample0 the
+    first sample size (0: 100 k).  Returns a dict with A (input order), C, I
+    (I_used), result."""
+    is_f32 = 1 if x.dtype == np.float32 else 0
+    x = np.ascontiguousarray(x) if is_f32 else _f64(x)
+    n, d = x.shape
+    w = None if w is None else _f64(w)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    A = np.empty(n, dtype=np.int32)
+    C = np.empty((k, d))
+    I = np.empty(k)
+    res = Result()
+    opt = options if options is not None else default_options()
+    lib().or_partition_sampled(_ptr(x), is_f32, _ptr(w), n, d, k, eps, _ptr(order), sample0,
+                               ctypes.byref(opt), _ptr(A), _ptr(C), _ptr(I), ctypes.byref(res))
     return {"A": A, "C": C, "I": I, "result": res.as_dict()}

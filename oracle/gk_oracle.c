@@ -500,3 +500,141 @@ int or_partition(const void *x, int is_f32, const double *w, int64_t n, int d, i
     free(As);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Random initialization (Section 4.5): the first rounds of Algorithm 2 run  */
+/* on a random sample of the points that doubles after every round with     */
+/* center movement; then Algorithm 2 continues on all points.               */
+/*                                                                          */
+/* Readings: the random order of the points is an input (order, a           */
+/* permutation of the input indices; the sample of a round is its first m   */
+/* points, taken in curve order).  The paper's first sample is 100 points   */
+/* per process with as many processes as blocks (Section 5), so one         */
+/* process holding all points starts from m0 = 100 k (sample0 <= 0), and    */
+/* never from fewer than k points; the rounds number ceil(log2(n / m0)),    */
+/* the paper's count with n_local = n / k.  The rounds are the first        */
+/* iterations of Algorithm 2 (they count towards maxIter; at least one      */
+/* iteration on all points remains); a sample round always moves the        */
+/* centers (no convergence stop) and applies the erosion; its balance       */
+/* bound is that of the sample's own total weight.                          */
+/* ------------------------------------------------------------------------ */
+int64_t or_sample_first(int64_t n, int k, int64_t sample0) {
+    int64_t m0 = sample0 > 0 ? sample0 : 100 * (int64_t)k;
+    if (m0 < k) m0 = k;
+    return m0 < n ? m0 : n;
+}
+
+int or_sample_rounds(int64_t n, int64_t m0, int max_iter) {
+    int r = 0;
+    while (r < 62 && (m0 << r) < n) ++r;
+    if (r > max_iter - 1) r = max_iter - 1;
+    return r < 0 ? 0 : r;
+}
+
+int or_partition_sampled(const void *x, int is_f32, const double *w, int64_t n, int d, int k,
+                         double eps, const int64_t *order, int64_t sample0, const or_options *opt,
+                         int32_t *A_out, double *C_out, double *I_out, or_result *res) {
+    memset(res, 0, sizeof(*res));
+    if (n < 1 || k < 1 || k > n || (d != 2 && d != 3) || !(eps >= 0.0) || !order) {
+        res->status = OR_INVALID;
+        return OR_INVALID;
+    }
+    {   /* order must be a permutation of [0, n) */
+        unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+        int bad = 0;
+        for (int64_t i = 0; i < n && !bad; ++i) {
+            if (order[i] < 0 || order[i] >= n || seen[order[i]])
+                bad = 1;
+            else
+                seen[order[i]] = 1;
+        }
+        free(seen);
+        if (bad) {
+            res->status = OR_INVALID;
+            return OR_INVALID;
+        }
+    }
+    or_options dflt;
+    if (!opt) {
+        or_default_options(&dflt);
+        opt = &dflt;
+    }
+    double *xd = (double *)malloc((size_t)n * d * sizeof(double));
+    uint64_t *keys = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    int64_t *perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (is_f32) {
+        const float *xf = (const float *)x;
+        for (int64_t i = 0; i < n * d; ++i) xd[i] = (double)xf[i];
+        or_hilbert_keys_f32(xf, n, d, keys, NULL);
+    } else {
+        memcpy(xd, x, (size_t)n * d * sizeof(double));
+        or_hilbert_keys_f64(xd, n, d, keys, NULL);
+    }
+    or_sort_keys(keys, n, perm);
+    double *xs = (double *)malloc((size_t)n * d * sizeof(double));
+    double *ws = w ? (double *)malloc((size_t)n * sizeof(double)) : NULL;
+    int64_t *rank = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        for (int j = 0; j < d; ++j) xs[i * d + j] = xd[perm[i] * d + j];
+        if (ws) ws[i] = w[perm[i]];
+        rank[perm[i]] = i;
+    }
+    double *I = (double *)malloc((size_t)k * sizeof(double));
+    int32_t *As = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    or_sfc_centers(xs, n, d, k, C_out);
+    for (int c = 0; c < k; ++c) I[c] = 1.0;
+
+    const int64_t m0 = or_sample_first(n, k, sample0);
+    const int R = or_sample_rounds(n, m0, opt->max_iter);
+    unsigned char *mark = (unsigned char *)calloc((size_t)n, 1);
+    double *xr = (double *)malloc((size_t)n * d * sizeof(double));
+    double *wr = ws ? (double *)malloc((size_t)n * sizeof(double)) : NULL;
+    double *S = (double *)malloc((size_t)k * sizeof(double));
+    double *C_new = (double *)malloc((size_t)k * d * sizeof(double));
+    double *delta = (double *)malloc((size_t)k * sizeof(double));
+    int passes = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t m = m0 << r; /* < n: r < R */
+        memset(mark, 0, (size_t)n);
+        for (int64_t i = 0; i < m; ++i) mark[rank[order[i]]] = 1;
+        int64_t j = 0;
+        for (int64_t pos = 0; pos < n; ++pos) {
+            if (!mark[pos]) continue;
+            for (int a = 0; a < d; ++a) xr[j * d + a] = xs[pos * d + a];
+            if (wr) wr[j] = ws[pos];
+            ++j;
+        }
+        double imbalance = 0.0;
+        for (int bp = 0; bp < opt->max_balance_iter; ++bp) {
+            or_assign(xr, j, d, C_out, I, k, As, NULL, NULL, opt->threads);
+            const double W = or_block_weights(As, wr, j, k, S);
+            passes += 1;
+            if (or_balance_update(S, W, k, d, eps, I, &imbalance)) break;
+        }
+        double beta = 0.0;
+        or_move_centers(xr, wr, As, j, d, k, C_out, C_new, delta, &beta);
+        memcpy(C_out, C_new, (size_t)k * d * sizeof(double));
+        if (opt->erosion) or_erosion(delta, beta, k, I);
+    }
+    or_options rest = *opt;
+    rest.max_iter = opt->max_iter - R;
+    int st = or_balanced_kmeans(xs, ws, n, d, k, eps, &rest, C_out, I, I_out, NULL, As, res);
+    res->iterations += R;
+    res->balance_passes += passes;
+    for (int64_t i = 0; i < n; ++i) A_out[perm[i]] = As[i];
+    free(xd);
+    free(keys);
+    free(perm);
+    free(xs);
+    free(ws);
+    free(rank);
+    free(I);
+    free(As);
+    free(mark);
+    free(xr);
+    free(wr);
+    free(S);
+    free(C_new);
+    free(delta);
+    return st;
+}

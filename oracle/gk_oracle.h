@@ -120,6 +120,17 @@ int or_partition(const void *x, int is_f32, const double *w, int64_t n, int d, i
                  const or_options *opt, int32_t *A_out, double *C_out, double *I_out,
                  or_result *res);
 
+/* Section 4.5, random initialization: the first rounds of Algorithm 2 on a random
+ * sample of the points (round r: the first m0 * 2^r entries of order, a permutation of
+ * the input indices, in curve order), then Algorithm 2 on all points.  m0 =
+ * or_sample_first(n, k, sample0) (sample0 <= 0: 100 k; at least k; at most n);
+ * or_sample_rounds gives the number of sample rounds. */
+int64_t or_sample_first(int64_t n, int k, int64_t sample0);
+int or_sample_rounds(int64_t n, int64_t m0, int max_iter);
+int or_partition_sampled(const void *x, int is_f32, const double *w, int64_t n, int d, int k,
+                         double eps, const int64_t *order, int64_t sample0, const or_options *opt,
+                         int32_t *A_out, double *C_out, double *I_out, or_result *res);
+
 #ifdef __cplusplus
 }
 #endif

@@ -122,6 +122,12 @@ def uniform_weights(n: int, seed: int, lo: float = 1.0, hi: float = 10.0,
     return out
 
 
+def random_order(n: int, seed: int) -> np.ndarray:
+    """A uniformly random permutation of [0, n) as int64: the random order of the points
+    that the random initialization of Section 4.5 takes its samples from."""
+    return np.random.default_rng([seed, 19]).permutation(n).astype(np.int64)
+
+
 # --------------------------------------------------------------------------------
 # Named workloads.  Sizes and shapes of the partitioning benchmarks this library is
 # measured on; seeds fixed so that every run sees the same points.

@@ -428,3 +428,114 @@ def test_invalid_arguments_rejected():
     assert oracle.partition(x, None, 4, 0.03)["result"]["status"] == oracle.OR_INVALID
     assert oracle.partition(np.zeros((3, 4)), None, 2, 0.03)["result"]["status"] == oracle.OR_INVALID
     assert oracle.partition(x, None, 2, -0.1)["result"]["status"] == oracle.OR_INVALID
+
+
+# ----------------------------------------------------------------------------------------
+# Random initialization (Section 4.5): samples of the random order that double after
+# every round with center movement.
+# ----------------------------------------------------------------------------------------
+
+def test_sample_sizes_and_rounds_closed_forms():
+    # first sample: 100 per block (100 per process, as many processes as blocks), >= k, <= n
+    assert oracle.sample_first(10**7, 1024) == 102_400
+    assert oracle.sample_first(10**7, 1024, 5000) == 5000
+    assert oracle.sample_first(10**7, 1024, 10) == 1024
+    assert oracle.sample_first(5000, 1024) == 5000
+    # rounds = ceil(log2(n / m0)), the paper's count with n_local = n / k, at most maxIter-1
+    for n, m0 in [(10**7, 102_400), (2**20, 2**10), (2**20 + 1, 2**10), (3000, 1600),
+                  (1600, 1600), (100, 1600), (10**9, 1_638_400)]:
+        want = max(0, math.ceil(math.log2(n / m0) - 1e-12)) if n > m0 else 0
+        assert oracle.sample_rounds(n, m0, 10**6) == want, (n, m0)
+    assert oracle.sample_rounds(2**20, 2**10, 5) == 4
+
+
+def _gmm(n, d, seed):
+    rng = np.random.default_rng(seed)
+    mu = rng.random((6, d))
+    comp = rng.integers(0, 6, n)
+    return mu[comp] + 0.05 * rng.standard_normal((n, d))
+
+
+@pytest.mark.parametrize("sample0,max_iter", [(10**6, 50), (0, 1)])
+def test_sampled_without_rounds_is_the_plain_partition(sample0, max_iter):
+    """No sample round (first sample >= n, or maxIter 1): exactly Algorithm 2."""
+    x = _gmm(3000, 2, 7)
+    order = np.random.default_rng(1).permutation(len(x))
+    opt = oracle.default_options(max_iter=max_iter, threads=2)
+    a = oracle.partition_sampled(x, None, 8, 0.03, order, sample0, opt)
+    b = oracle.partition(x, None, 8, 0.03, opt)
+    assert np.array_equal(a["A"], b["A"]) and np.array_equal(a["C"], b["C"])
+    assert np.array_equal(a["I"], b["I"]) and a["result"] == b["result"]
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_sample_round_on_one_copy_of_doubled_points_is_a_full_iteration(weighted):
+    """Every point twice (same weight), the order listing one copy of each first, and the
+    first sample exactly those copies: a sample round sees the whole point set at half
+    weight, which gives the same assignment, balance decisions (k divides the sample, so
+    the bound scales exactly), centers, movement and erosion as a first iteration on all
+    points.  So the sampled run equals the plain run up to summation order."""
+    m, k = 1200, 8
+    x1 = _gmm(m, 2, 11)
+    x = np.concatenate([x1, x1])
+    w = None
+    if weighted:
+        w1 = np.random.default_rng(3).uniform(1, 10, m)
+        w = np.concatenate([w1, w1])
+    rng = np.random.default_rng(5)
+    order = np.concatenate([rng.permutation(m), m + rng.permutation(m)])
+    opt = oracle.default_options(max_iter=6, threads=2)
+    a = oracle.partition_sampled(x, w, k, 0.03, order, m, opt)
+    b = oracle.partition(x, w, k, 0.03, opt)
+    ra, rb = a["result"], b["result"]
+    assert oracle.sample_rounds(2 * m, m, 6) == 1
+    assert ra["iterations"] == rb["iterations"] and ra["balance_passes"] == rb["balance_passes"]
+    assert ra["balanced"] == rb["balanced"] and ra["converged"] == rb["converged"]
+    assert np.array_equal(a["A"], b["A"])
+    assert np.allclose(a["C"], b["C"], rtol=0, atol=1e-12)
+    assert np.allclose(a["I"], b["I"], rtol=1e-12, atol=0)
+
+
+def test_sampled_depends_on_the_order_only_through_the_sample_sets():
+    """Shuffling the order inside each round's new points keeps every sample set, and the
+    samples are taken in curve order: bit-identical results.  Moving one point from the
+    first sample to the second changes them."""
+    n, k, m0 = 5000, 10, 1000
+    x = _gmm(n, 3, 13)
+    rng = np.random.default_rng(17)
+    order = rng.permutation(n)
+    opt = oracle.default_options(max_iter=8, threads=2)
+    a = oracle.partition_sampled(x, None, k, 0.03, order, m0, opt)
+    o2 = order.copy()
+    for lo, hi in [(0, 1000), (1000, 2000), (2000, 4000), (4000, 5000)]:
+        o2[lo:hi] = rng.permutation(o2[lo:hi])
+    b = oracle.partition_sampled(x, None, k, 0.03, o2, m0, opt)
+    assert np.array_equal(a["A"], b["A"]) and np.array_equal(a["C"], b["C"])
+    assert a["result"] == b["result"]
+    o3 = order.copy()
+    o3[[0, 1500]] = o3[[1500, 0]]
+    c = oracle.partition_sampled(x, None, k, 0.03, o3, m0, opt)
+    assert not np.array_equal(a["C"], c["C"])
+
+
+def test_sampled_partition_meets_bound_and_is_weighted_voronoi():
+    x = _gmm(20_000, 2, 19)
+    k = 12
+    order = np.random.default_rng(2).permutation(len(x))
+    out = oracle.partition_sampled(x, None, k, 0.03, order, 0, oracle.default_options(threads=2))
+    res = out["result"]
+    assert res["balanced"] == 1
+    S, W = oracle.block_weights(out["A"], None, k)
+    assert S.max() <= 1.03 * math.ceil(W / k)
+    ref, b1, b2 = _effective_argmin(x, out["C"], out["I"])
+    clear = (b2 - b1) > 1e-10 * b1
+    assert np.array_equal(out["A"][clear], ref[clear])
+
+
+def test_sampled_rejects_an_order_that_is_not_a_permutation():
+    x = _gmm(500, 2, 23)
+    order = np.arange(500)
+    order[7] = 8
+    assert oracle.partition_sampled(x, None, 4, 0.03, order)["result"]["status"] == oracle.OR_INVALID
+    order[7] = 500
+    assert oracle.partition_sampled(x, None, 4, 0.03, order)["result"]["status"] == oracle.OR_INVALID
