@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-fp32-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sampled", action="store_true",
+                    help="skip the partition with random initialization (Section 4.5)")
     return ap.parse_args()
 
 
@@ -330,6 +332,12 @@ def main():
                 "assign_ms_per_pass": fp32_pass, "speedup_per_pass_vs_fp64": fp64_pass / fp32_pass,
                 "speedup_partition_vs_fp64": ms_per_step / float(np.mean(t32))}
 
+    # ---- random initialization (Section 4.5) on the same data -----------------------------
+    sampled = None
+    if not args.no_sampled:
+        sampled = _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, ms_per_step,
+                                max(1, min(3, args.steps)))
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x, w, spec, args.cpu_seconds)
@@ -347,7 +355,7 @@ def main():
                 "rechecked_points_per_step": last["rechecked_points"],
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "fp32_form": fp32, "cpu_baseline": cpu}
+                "fp32_form": fp32, "sampled_init": sampled, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -490,6 +498,40 @@ def _e2e(gk, x, w, spec, opts, stream, steps):
     d2h = n * 4 + k * d * 8 + k * 8
     return {"value": pp / (tot * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": tot / steps}
+
+
+def _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, plain_ms, steps):
+    """gk_partition_sampled on the device-resident workload with a seeded random order:
+    the sample rounds on doubling samples (first sample 100 k points), then the k-means
+    loop on all points.  Partition time against the plain gk_partition step."""
+    import torch
+    n, k, eps = int(xt.shape[0]), spec["k"], spec["eps"]
+    order = torch.from_numpy(synth.random_order(n, spec["seed"])).to(xt.device)
+    m0 = min(n, max(100 * k, k))
+    rounds = min(max(0, math.ceil(math.log2(n / m0) - 1e-12)) if n > m0 else 0,
+                 opts.max_iter - 1)
+
+    def call():
+        return gk.partition_sampled(xt, k, eps, order, 0, weights=wt, options=opts)
+
+    call()
+    torch.cuda.synchronize()
+    times, res = [], None
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, _, res = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    return {"ms_per_step": ms, "partition_time_s": ms / 1e3, "first_sample": m0,
+            "sample_rounds": rounds, "iterations": res["iterations"],
+            "balance_passes": res["balance_passes"], "balanced": res["balanced"],
+            "max_imbalance": res["max_imbalance"], "speedup_vs_plain": plain_ms / ms,
+            "order": "seeded uniform permutation (host-generated, device-resident)"}
 
 
 def _attach_traffic(roof, workload):

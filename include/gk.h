@@ -196,6 +196,30 @@ gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, i
                        int32_t *block_out, double *centers_out, double *influence_out,
                        gk_result *result, void *stream);
 
+/*
+ * gk_partition with the random initialization of Section 4.5: the first
+ * iterations of Algorithm 2 run on random samples of the points that double
+ * after every movement, then Algorithm 2 continues on all points.
+ *   order:   n int64 (host or device), a permutation of [0, n): the random order
+ *            of the points.  Round r's sample is the points order[0 .. m0*2^r),
+ *            taken in curve order; its balance bound is (1+eps)*ceil(W_r/k) with
+ *            W_r the sample's total weight; every round moves the centers and
+ *            applies the erosion, whatever their movement.
+ *   sample0: m0, the first sample's size; <= 0 selects 100*k (the paper's 100
+ *            points per process with as many processes as blocks); raised to k,
+ *            capped at n.
+ * The rounds number ceil(log2(n/m0)), at most max_iter - 1; they count as
+ * iterations (result->iterations and ->balance_passes include them) and the
+ * iterations on all points are at most max_iter minus the rounds.  An order that
+ * is not a permutation gives GK_ERR_INVALID_ARG, found on the device after the
+ * bootstrap.  Other arguments and outputs as gk_partition.
+ */
+gk_status gk_partition_sampled(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                               int32_t d, int32_t k, double eps, const int64_t *order,
+                               int64_t sample0, const gk_options *opt, int32_t *block_out,
+                               double *centers_out, double *influence_out, gk_result *result,
+                               void *stream);
+
 /* One problem of a batch (gk_partition_batched). */
 typedef struct gk_instance {
     const void *coords;     /* n x d row-major, dtype; device memory                 */

@@ -121,8 +121,10 @@ def lib():
         L.gk_move_centers.argtypes = [P, i32, P, i64, i32, i32, P, P, P, P, P, P]
         L.gk_balanced_kmeans.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P, P]
         L.gk_partition.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P, P]
+        L.gk_partition_sampled.argtypes = [P, i32, P, i64, i32, i32, dbl, P, i64, P, P, P, P,
+                                           P, P]
         for name in ("gk_hilbert_keys", "gk_sfc_init", "gk_assign", "gk_move_centers",
-                     "gk_balanced_kmeans", "gk_partition"):
+                     "gk_balanced_kmeans", "gk_partition", "gk_partition_sampled"):
             getattr(L, name).restype = i32
         L.gk_move_centers_noalloc.argtypes = [P, i32, P, i64, i32, i32, P, P, P, P, P, P]
         L.gk_move_centers_noalloc.restype = i32
@@ -316,6 +318,34 @@ def partition(coords, k: int, eps: float, weights=None, options: Options | None 
                             ctypes.byref(opt), _ptr(block), _ptr(centers), _ptr(infl),
                             ctypes.byref(res), _stream(coords, stream))
     _check(st, "gk_partition", allow=(GK_ERR_NOT_BALANCED,))
+    return block, centers, infl, res.as_dict()
+
+
+def partition_sampled(coords, k: int, eps: float, order, sample0: int = 0, weights=None,
+                      options: Options | None = None, stream=None, want_state: bool = True):
+    """The whole partitioner with the random initialization of Section 4.5.  order: n
+    int64, a permutation of [0, n) (the random order of the points; host or device);
+    sample0: first sample size (0: 100 k).  Returns (block, centers, influence, result)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    if _is_torch(order):
+        import torch
+        if order.dtype != torch.int64:
+            raise TypeError("order must be int64")
+    elif np.asarray(order).dtype != np.int64:
+        raise TypeError("order must be int64")
+    if int(order.shape[0]) != n or len(order.shape) != 1:
+        raise ValueError("order must have one entry per point")
+    block = _empty(coords, (n,), "i32")
+    centers = _empty(coords, (k, d), "f64") if want_state else None
+    infl = _empty(coords, (k,), "f64") if want_state else None
+    res = Result()
+    opt = options if options is not None else default_options()
+    st = lib().gk_partition_sampled(_ptr(coords), _dtype_code(coords), _ptr(weights), n, d, k,
+                                    eps, _ptr(order), int(sample0), ctypes.byref(opt), _ptr(block),
+                                    _ptr(centers), _ptr(infl), ctypes.byref(res),
+                                    _stream(coords, stream))
+    _check(st, "gk_partition_sampled", allow=(GK_ERR_NOT_BALANCED,))
     return block, centers, infl, res.as_dict()
 
 

@@ -36,6 +36,9 @@ struct Workspace {
     int batch_cap = 0;
     cudaGraphExec_t batch_exec = nullptr;
     std::vector<Prob> batch_key;
+    // the cached graph of the last call with random initialization
+    cudaGraphExec_t sample_exec = nullptr;
+    std::vector<unsigned char> sample_key;
 };
 Workspace g_ws;
 
@@ -46,6 +49,9 @@ void drop_graph() {
     if (g_ws.batch_exec) cudaGraphExecDestroy(g_ws.batch_exec);
     g_ws.batch_exec = nullptr;
     g_ws.batch_key.clear();
+    if (g_ws.sample_exec) cudaGraphExecDestroy(g_ws.sample_exec);
+    g_ws.sample_exec = nullptr;
+    g_ws.sample_key.clear();
 }
 
 void release_all() {
@@ -136,6 +142,54 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.sgdata = (float4 *)take((size_t)(p.nsgroups > 0 ? p.nsgroups : 1) * 32);
     b.block_stage = stage_block ? (int *)take((size_t)n * 4) : nullptr;
     b.perm_stage = perm_out ? (long long *)take((size_t)n * 8) : nullptr;
+    return off;
+}
+
+// Random initialization (Section 4.5): the round bytes, the selection scratch and
+// the point-side arrays of the largest sample (its center-side state is the main
+// problem's); the sample's own control block.
+struct SampleBufs {
+    long long m0 = 0, m_max = 0, nrho = 0;
+    int rounds = 0;
+    long long *order_stage = nullptr;
+    unsigned char *rho_in = nullptr, *rho = nullptr;
+    unsigned *counts = nullptr, *sp = nullptr;
+    Ctl *ctl = nullptr;
+    float *X32 = nullptr;
+    double *X64 = nullptr;
+    void *Ws = nullptr;
+    int *A = nullptr;
+    float4 *tiles = nullptr, *supers = nullptr, *trec = nullptr;
+    int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
+};
+
+size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *ptr = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return ptr;
+    };
+    const size_t es = p.dtype == 1 ? 8 : 4;
+    const long long np = (sb.m_max + kTile - 1) / kTile * kTile;
+    const long long nt = np / kTile, ns = (nt + kSuperTiles - 1) / kSuperTiles;
+    sb.nrho = sample_rho_entries(p.n);
+    sb.order_stage = stage_order ? (long long *)take((size_t)p.n * 8) : nullptr;
+    sb.rho_in = (unsigned char *)take((size_t)p.n);
+    sb.rho = (unsigned char *)take((size_t)sb.nrho);
+    sb.counts = (unsigned *)take((size_t)(sb.nrho / kSampleChunk + 1) * 4);
+    sb.sp = (unsigned *)take((size_t)sb.m_max * 4);
+    sb.ctl = (Ctl *)take(sizeof(Ctl));
+    sb.X32 = (float *)take((size_t)p.d * np * 4);
+    sb.X64 = p.dtype == 1 ? (double *)take((size_t)p.d * np * 8) : nullptr;
+    sb.Ws = p.weighted ? (void *)take((size_t)np * es) : nullptr;
+    sb.A = (int *)take((size_t)np * 4);
+    sb.tiles = (float4 *)take((size_t)nt * 32);
+    sb.supers = (float4 *)take((size_t)ns * 32);
+    sb.trec = (float4 *)take((size_t)nt * kRecF4 * 16);
+    sb.coop = (int *)take((size_t)nt * 4);
+    sb.bigs = (int *)take((size_t)ns * 12);
+    sb.blists = (int *)take((size_t)ns * kWarpList * 4);
     return off;
 }
 
@@ -268,8 +322,10 @@ struct Call {
         GK_CUDA(cudaMemsetAsync(p.BBhi, 0, (size_t)p.k * p.d * 8, s));
         return GK_OK;
     }
+    size_t main_bytes = 0;  // the problem's part of the workspace; `extra` bytes follow it
     gk_status init(const void *coords, int32_t dtype, const void *weights, int64_t n, int32_t d,
-                   int32_t k, bool sort, bool block_host, bool perm_out) {
+                   int32_t k, bool sort, bool block_host, bool perm_out,
+                   SampleBufs *sb = nullptr, bool stage_order = false) {
         gk_status st0 = setup(weights, n, d, k, dtype);
         if (st0 != GK_OK) return st0;
         int dev = 0;
@@ -282,10 +338,12 @@ struct Call {
         if (weights && kw == kDevice && ((uintptr_t)weights % es)) return GK_ERR_INVALID_ARG;
         coords_host = kc == kHost;
         weights_host = weights && kw == kHost;
-        size_t need = layout(p, b, nullptr, sort, coords_host, weights_host, block_host, perm_out);
+        main_bytes = align_up(layout(p, b, nullptr, sort, coords_host, weights_host, block_host, perm_out));
+        size_t need = main_bytes + (sb ? layout_sample(p, *sb, nullptr, stage_order) : 0);
         gk_status st = ensure_workspace(need);
         if (st != GK_OK) return st;
         layout(p, b, g_ws.dev, sort, coords_host, weights_host, block_host, perm_out);
+        if (sb) layout_sample(p, *sb, g_ws.dev + main_bytes, stage_order);
         p.coords = coords_host ? b.coords_stage : coords;
         p.weights = weights ? (weights_host ? b.weights_stage : weights) : nullptr;
         GK_CUDA(cudaEventRecord(g_ws.ev[0], s));
@@ -355,8 +413,8 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     if (!r) return;
     memset(r, 0, sizeof(*r));
     r->status = st;
-    r->iterations = c.iter;
-    r->balance_passes = c.passes;
+    r->iterations = c.iter + c.sample_iters;
+    r->balance_passes = c.passes + c.sample_passes;
     r->converged = c.converged;
     r->balanced = c.balanced;
     r->max_imbalance = c.max_imbalance;
@@ -467,6 +525,91 @@ gk_status run_loop(Call &cl, const gk_options &o) {
     return GK_OK;
 }
 
+// Random initialization: the Prob of sample round r (m points) and its selection.
+Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
+    Prob ps = p;
+    ps.n = m;
+    ps.n_pad = (m + kTile - 1) / kTile * kTile;
+    ps.ntiles = (int)(ps.n_pad / kTile);
+    ps.nsupers = (ps.ntiles + kSuperTiles - 1) / kSuperTiles;
+    ps.qmul = tile_order_multiplier(ps.ntiles);
+    ps.keys[0] = ps.keys[1] = nullptr;
+    ps.perm[0] = ps.perm[1] = nullptr;
+    ps.X32 = sb.X32;
+    ps.X64 = sb.X64;
+    ps.Ws = sb.Ws;
+    ps.A = sb.A;
+    ps.tiles = sb.tiles;
+    ps.supers = sb.supers;
+    ps.trec = sb.trec;
+    ps.coop = sb.coop;
+    ps.bigs = sb.bigs;
+    ps.blists = sb.blists;
+    ps.ctl = sb.ctl;
+    ps.max_iter = 1;
+    ps.final_balance_iter = 0;
+    return ps;
+}
+
+// Runs the sample rounds and then the main loop (p.max_iter already reduced by the
+// rounds): one cached graph, or host-driven with a readback per pass.
+gk_status run_sampled(Call &cl, const gk_options &o, const SampleBufs &sb, const unsigned *perm) {
+    Prob &p = cl.p;
+    cudaStream_t s = cl.s;
+    const int R = sb.rounds;
+    std::vector<Prob> ps(R);
+    std::vector<SampleSel> sel(R);
+    for (int r = 0; r < R; ++r) {
+        ps[r] = sample_prob(p, sb, sb.m0 << r);
+        memset(&sel[r], 0, sizeof(SampleSel));
+        sel[r].rho = sb.rho;
+        sel[r].perm = perm;
+        sel[r].counts = sb.counts;
+        sel[r].sp = sb.sp;
+        sel[r].n = p.n;
+        sel[r].nchunks = (int)(sb.nrho / kSampleChunk);
+        sel[r].round = r;
+    }
+    if (o.use_graph) {
+        std::vector<unsigned char> key(sizeof(Prob) * (1 + R) + sizeof(SampleSel) * R);
+        memcpy(key.data(), &p, sizeof(Prob));
+        if (R) {
+            memcpy(key.data() + sizeof(Prob), ps.data(), sizeof(Prob) * R);
+            memcpy(key.data() + sizeof(Prob) * (1 + R), sel.data(), sizeof(SampleSel) * R);
+        }
+        if (!(g_ws.sample_exec && g_ws.sample_key == key)) {
+            if (g_ws.sample_exec) cudaGraphExecDestroy(g_ws.sample_exec);
+            g_ws.sample_exec = nullptr;
+            g_ws.sample_key.clear();
+            cudaGraphExec_t ex = nullptr;
+            if (build_sampled_graph(p, ps.data(), sel.data(), R, &ex) != cudaSuccess) {
+                cudaGetLastError();
+                return GK_ERR_CUDA;
+            }
+            g_ws.sample_exec = ex;
+            g_ws.sample_key = key;
+        }
+        GK_CUDA(cudaGraphLaunch(g_ws.sample_exec, s));
+        return GK_OK;
+    }
+    Ctl *hc = g_ws.host_ctl;
+    for (int r = 0; r < R; ++r) {
+        GK_CUDA(launch_sample_select(ps[r], sel[r], s));
+        GK_CUDA(launch_init(ps[r], s));
+        for (int bp = 0; bp < o.max_balance_iter; ++bp) {
+            GK_CUDA(launch_pass(ps[r], 0, s));
+            GK_CUDA(cudaMemcpyAsync(hc, ps[r].ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            GK_CUDA(cudaStreamSynchronize(s));
+            if (!hc->cont_balance) break;
+        }
+        GK_CUDA(launch_move(ps[r], 3, s));
+        GK_CUDA(launch_sample_export(ps[r], p.ctl, s));
+    }
+    gk_options rest = o;
+    rest.max_iter = p.max_iter;
+    return run_loop(cl, rest);
+}
+
 gk_status check_options(const gk_options &o) {
     if (o.max_iter < 1 || o.max_balance_iter < 1 || o.final_balance_iter < 0 ||
         (o.assign_dtype != GK_F32 && o.assign_dtype != GK_F64) || !(o.delta_threshold == o.delta_threshold))
@@ -477,11 +620,13 @@ gk_status check_options(const gk_options &o) {
 }
 
 // Shared body of gk_partition (sort = true) and gk_balanced_kmeans (sort = false).
+// order != nullptr: random initialization (Section 4.5) with that order and first
+// sample size sample0 (<= 0: 100 k).
 gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, int64_t n,
                         int32_t d, int32_t k, double eps, const gk_options *opt, bool sort,
                         double *centers_io, double *influence_io, int32_t *block_out,
                         double *centers_out, double *influence_out, gk_result *result,
-                        void *stream) {
+                        void *stream, const int64_t *order = nullptr, int64_t sample0 = 0) {
     gk_status st = check_common(coords, dtype, n, d);
     if (st != GK_OK) return st;
     if (k < 1 || k > n || !(eps >= 0.0) || !block_out) return GK_ERR_INVALID_ARG;
@@ -493,14 +638,30 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     GK_CUDA(cudaGetDevice(&dev));
     if (ptr_kind(block_out, dev) == kForeign) return GK_ERR_INVALID_ARG;
     bool block_host = ptr_kind(block_out, dev) == kHost;
+    SampleBufs sb;
+    bool order_host = false;
+    if (order) {
+        PtrKind ko = ptr_kind(order, dev);
+        if (ko == kForeign || (ko == kDevice && ((uintptr_t)order % 8))) return GK_ERR_INVALID_ARG;
+        order_host = ko == kHost;
+        // first sample: 100 points per block (the paper's 100 per process, k = p), at
+        // least k, at most n; rounds until the sample would reach n, at most max_iter - 1
+        sb.m0 = sample0 > 0 ? sample0 : 100ll * k;
+        if (sb.m0 < k) sb.m0 = k;
+        if (sb.m0 > n) sb.m0 = n;
+        while (sb.rounds < 62 && (sb.m0 << sb.rounds) < n) ++sb.rounds;
+        if (sb.rounds > o.max_iter - 1) sb.rounds = o.max_iter - 1;
+        sb.m_max = sb.rounds > 0 ? sb.m0 << (sb.rounds - 1) : 1;
+    }
     Call cl;
     cl.s = (cudaStream_t)stream;
-    st = cl.init(coords, dtype, weights, n, d, k, sort, block_host, false);
+    st = cl.init(coords, dtype, weights, n, d, k, sort, block_host, false, order ? &sb : nullptr,
+                 order_host);
     if (st != GK_OK) return st;
     Prob &p = cl.p;
     p.eps = eps;
     p.assign_f64 = o.assign_dtype == GK_F64;
-    p.max_iter = o.max_iter;
+    p.max_iter = o.max_iter - sb.rounds;
     p.max_balance_iter = o.max_balance_iter;
     p.final_balance_iter = o.final_balance_iter;
     p.erosion = o.erosion;
@@ -521,8 +682,19 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
         GK_CUDA(cudaMemcpyAsync(p.C, centers_io, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
         GK_CUDA(cudaMemcpyAsync(p.Iin, influence_io, (size_t)k * 8, cudaMemcpyDefault, cl.s));
     }
+    if (order) {
+        const long long *ord = (const long long *)order;
+        if (order_host) {
+            GK_CUDA(cudaMemcpyAsync(sb.order_stage, order, (size_t)n * 8, cudaMemcpyHostToDevice, cl.s));
+            ord = sb.order_stage;
+        }
+        GK_CUDA(cudaMemsetAsync(sb.ctl, 0, sizeof(Ctl), cl.s));
+        GK_CUDA(launch_sample_rho(p, ord, sb.m0, perm, sb.rho_in, sb.rho, cl.s));
+        if ((st = cl.read_ctl()) != GK_OK) return st;
+        if (g_ws.host_ctl->bad_order) return GK_ERR_INVALID_ARG;
+    }
     GK_CUDA(cudaEventRecord(g_ws.ev[1], cl.s));
-    if ((st = run_loop(cl, o)) != GK_OK) return st;
+    if ((st = order ? run_sampled(cl, o, sb, perm) : run_loop(cl, o)) != GK_OK) return st;
     GK_CUDA(cudaEventRecord(g_ws.ev[2], cl.s));
     int *out = block_host ? cl.b.block_stage : block_out;
     GK_CUDA(launch_scatter(p, perm, out, cl.s));
@@ -851,6 +1023,16 @@ gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, i
                        gk_result *result, void *stream) {
     return kmeans_common(coords, dtype, weights, n, d, k, eps, opt, true, nullptr, nullptr,
                          block_out, centers_out, influence_out, result, stream);
+}
+
+gk_status gk_partition_sampled(const void *coords, int32_t dtype, const void *weights, int64_t n,
+                               int32_t d, int32_t k, double eps, const int64_t *order,
+                               int64_t sample0, const gk_options *opt, int32_t *block_out,
+                               double *centers_out, double *influence_out, gk_result *result,
+                               void *stream) {
+    if (!order) return GK_ERR_INVALID_ARG;
+    return kmeans_common(coords, dtype, weights, n, d, k, eps, opt, true, nullptr, nullptr,
+                         block_out, centers_out, influence_out, result, stream, order, sample0);
 }
 
 void gk_release(void) { release_all(); }

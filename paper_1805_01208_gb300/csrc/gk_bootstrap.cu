@@ -357,16 +357,16 @@ radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
 // Gather into curve order: SoA frame coordinates (FP32), raw FP64 coordinates,
 // sorted weights, and the total weight as a 128-bit fixed-point sum.
 // ------------------------------------------------------------------------------
+// perm: destination index -> input index (nullptr: identity); nsrc: input points.
 template <typename T>
-__global__ void gather_kernel(Prob p, const unsigned *perm) {
-    count_launch(p.ctl);
+__device__ __forceinline__ void gather_body(const Prob &p, const unsigned *perm, long long nsrc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const T *x = (const T *)p.coords;
     const T *w = (const T *)p.weights;
     unsigned long long wfix = 0;
     if (i < p.n_pad) {
         long long src = i < p.n ? (perm ? (long long)perm[i] : i) : 0;
-        bool ok = i < p.n && src < p.n;  // a permutation entry is always < n
+        bool ok = i < p.n && src < nsrc;  // a permutation entry is always < nsrc
         for (int j = 0; j < p.d; ++j) {
             T v = ok ? x[src * p.d + j] : (T)0;
             if (sizeof(T) == 8) {
@@ -389,6 +389,12 @@ __global__ void gather_kernel(Prob p, const unsigned *perm) {
         for (int o = 16; o; o >>= 1) wfix += __shfl_xor_sync(0xffffffffu, wfix, o);
         if ((threadIdx.x & 31) == 0 && wfix) atomic_add_u128(&p.ctl->wsum_lo, wfix);
     }
+}
+
+template <typename T>
+__global__ void gather_kernel(Prob p, const unsigned *perm) {
+    count_launch(p.ctl);
+    gather_body<T>(p, perm, p.n);
 }
 
 // Per tile: origin = centre of the bounding box of its frame coordinates, half
@@ -489,6 +495,141 @@ __global__ void perm_to_i64_kernel(const unsigned *perm, long long n, long long 
 }
 
 // ------------------------------------------------------------------------------
+// Random initialization (Section 4.5).  The random order of the points is an
+// input: order[r] = input index of the point of rank r.  Round byte of rank r:
+// the first round whose sample (the m0 * 2^j lowest ranks) holds it.  A sample
+// round then selects the curve positions with round byte <= j, in curve order.
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned char sample_round_of(long long rank, long long m0) {
+    int r = 0;
+    while (r < 254 && (m0 << r) <= rank) ++r;  // m0 >= 1 and rank < 2^32: r <= 32
+    return (unsigned char)r;
+}
+
+// rho_in[order[r]] = round byte of rank r (rho_in preset to 0xff); entries of
+// order outside [0, n) set bad_order.
+__global__ void order_round_kernel(const long long *order, long long n, long long m0,
+                                   unsigned char *rho_in, Ctl *ctl) {
+    count_launch(ctl);
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    long long o = order[r];
+    if (o < 0 || o >= n)
+        atomicOr(&ctl->bad_order, 1);
+    else
+        rho_in[o] = sample_round_of(r, m0);
+}
+
+// rho[pos] = round byte of the point at curve position pos, 0xff beyond n; an
+// input index that order never named (order is not a permutation) sets bad_order.
+__global__ void rho_kernel(const unsigned char *rho_in, const unsigned *perm, long long n,
+                           long long nrho, unsigned char *rho, Ctl *ctl) {
+    count_launch(ctl);
+    long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= nrho) return;
+    unsigned char v = 0xff;
+    if (pos < n) {
+        v = rho_in[perm[pos]];
+        if (v == 0xff) atomicOr(&ctl->bad_order, 1);
+    }
+    rho[pos] = v;
+}
+
+constexpr int kSelThreads = kSampleChunk / 16;  // 16 round bytes per thread (one uint4)
+
+// Selected positions among the 16 bytes of v: bytes <= round.
+__device__ __forceinline__ unsigned sel_mask16(uint4 v, unsigned rr) {
+    unsigned a = __vcmpleu4(v.x, rr), b = __vcmpleu4(v.y, rr), c = __vcmpleu4(v.z, rr),
+             d = __vcmpleu4(v.w, rr);
+    unsigned m = 0;
+    const unsigned w[4] = {a, b, c, d};
+    for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < 4; ++j) m |= ((w[q] >> (8 * j + 7)) & 1u) << (4 * q + j);
+    return m;
+}
+
+// Selection, part 1: selected positions per chunk; resets the sample's weight sum.
+__global__ void __launch_bounds__(kSelThreads) sample_count_kernel(Prob ps, SampleSel sel) {
+    count_launch(ps.ctl);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ps.ctl->wsum_lo = 0ull;
+        ps.ctl->wsum_hi = 0ull;
+    }
+    const unsigned rr = 0x01010101u * (unsigned)sel.round;
+    const uint4 v = ((const uint4 *)(sel.rho + (size_t)blockIdx.x * kSampleChunk))[threadIdx.x];
+    unsigned c = __popc(sel_mask16(v, rr));
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    __shared__ unsigned red[kSelThreads / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w) t += red[w];
+        sel.counts[blockIdx.x] = t;
+    }
+}
+
+// Selection, part 2 (one CTA): exclusive prefix sums of the chunk counts, in place.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) sample_scan_kernel(Prob ps, SampleSel sel) {
+    count_launch(ps.ctl);
+    __shared__ unsigned wsum[kScanThreads / 32];
+    const int per = (sel.nchunks + kScanThreads - 1) / kScanThreads;
+    const int b0 = threadIdx.x * per, b1 = min(sel.nchunks, b0 + per);
+    unsigned t = 0;
+    for (int b = b0; b < b1; ++b) t += sel.counts[b];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = t;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    unsigned run = before + x - t;
+    for (int b = b0; b < b1; ++b) {
+        unsigned c = sel.counts[b];
+        sel.counts[b] = run;
+        run += c;
+    }
+}
+
+// Selection, part 3: sp[offset of the position among the selected] = input index.
+__global__ void __launch_bounds__(kSelThreads) sample_write_kernel(Prob ps, SampleSel sel) {
+    count_launch(ps.ctl);
+    const unsigned rr = 0x01010101u * (unsigned)sel.round;
+    const uint4 v = ((const uint4 *)(sel.rho + (size_t)blockIdx.x * kSampleChunk))[threadIdx.x];
+    unsigned m = sel_mask16(v, rr);
+    const unsigned c = __popc(m);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __shared__ unsigned wsum[kSelThreads / 32];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    unsigned off = sel.counts[blockIdx.x] + x - c;
+    for (int w = 0; w < warp; ++w) off += wsum[w];
+    const long long pos0 = (long long)blockIdx.x * kSampleChunk + 16 * threadIdx.x;
+    while (m) {
+        int j = __ffs(m) - 1;
+        m &= m - 1;
+        sel.sp[off++] = sel.perm[pos0 + j];  // a selected position is < n
+    }
+}
+
+// Selection, part 4: the sample's sorted arrays (its own frame is the problem's).
+template <typename T>
+__global__ void sample_gather_kernel(Prob ps, SampleSel sel) {
+    count_launch(ps.ctl);
+    gather_body<T>(ps, sel.sp, sel.n);
+}
+
+// ------------------------------------------------------------------------------
 // Host launchers.
 // ------------------------------------------------------------------------------
 static int blocks_for(long long n, int threads) { return (int)((n + threads - 1) / threads); }
@@ -567,6 +708,47 @@ cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+long long sample_rho_entries(long long n) {
+    return (n + kSampleChunk - 1) / kSampleChunk * kSampleChunk;
+}
+
+cudaError_t launch_sample_rho(const Prob &p, const long long *order, long long m0,
+                              const unsigned *perm, unsigned char *rho_in, unsigned char *rho,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(rho_in, 0xff, (size_t)p.n, s);
+    if (e != cudaSuccess) return e;
+    order_round_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(order, p.n, m0, rho_in, p.ctl);
+    const long long nrho = sample_rho_entries(p.n);
+    rho_kernel<<<blocks_for(nrho, 256), 256, 0, s>>>(rho_in, perm, p.n, nrho, rho, p.ctl);
+    return cudaGetLastError();
+}
+
+int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out) {
+    int q = 0;
+    const dim3 cg((unsigned)sel.nchunks), cb(kSelThreads);
+    out[q++] = {(void *)sample_count_kernel, cg, cb};
+    out[q++] = {(void *)sample_scan_kernel, dim3(1), dim3(kScanThreads)};
+    out[q++] = {(void *)sample_write_kernel, cg, cb};
+    out[q++] = {ps.dtype == 1 ? (void *)sample_gather_kernel<double> : (void *)sample_gather_kernel<float>,
+                dim3((unsigned)blocks_for(ps.n_pad, 256)), dim3(256)};
+    out[q++] = {(void *)tile_box_kernel, dim3((unsigned)ps.ntiles), dim3(kTile)};
+    out[q++] = {(void *)super_box_kernel, dim3((unsigned)blocks_for(ps.nsupers, 128)), dim3(128)};
+    return q;
+}
+
+cudaError_t launch_sample_select(const Prob &ps, const SampleSel &sel, cudaStream_t s) {
+    KNode nodes[kSampleSelectNodes];
+    int q = sample_select_nodes(ps, sel, nodes);
+    Prob pa = ps;
+    SampleSel sa = sel;
+    void *args[] = {(void *)&pa, (void *)&sa};
+    for (int i = 0; i < q; ++i) {
+        cudaError_t e = cudaLaunchKernel(nodes[i].fn, nodes[i].grid, nodes[i].block, args, 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_centers(const Prob &p, cudaStream_t s) {

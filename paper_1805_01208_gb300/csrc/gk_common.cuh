@@ -64,6 +64,9 @@ struct Ctl {
     int nonfinite;                          // a coordinate or weight is NaN/Inf
     int nonpositive_w;                      // a weight is <= 0
     int bad_block;                          // a given block id is outside [0, k)
+    int bad_order;                          // the sample order is not a permutation
+    int sample_iters;                       // movement phases of the sample rounds
+    int sample_passes;                      // assignment passes of the sample rounds
     int status;                             // kOk or an error code
     int balanced;                           // last pass met the bound
     int converged;                          // movement below threshold
@@ -141,6 +144,20 @@ struct Prob {
     float4 *sgdata;             // 2 float4 per supergroup of kSuperGroup groups (current buffer)
     int nsgroups;               // 0: no supergroup level
     Ctl *ctl;
+};
+
+// Selection of one sample round of the random initialization (Section 4.5): the
+// curve positions whose round byte rho is <= round, in ascending position order.
+// rho has nchunks * kSampleChunk entries (0xff beyond n); counts has nchunks entries.
+constexpr int kSampleChunk = 4096;  // positions per CTA of the selection kernels
+struct SampleSel {
+    const unsigned char *rho;   // per curve position: first sample round holding it
+    const unsigned *perm;       // curve position -> input index
+    unsigned *counts;           // per chunk: selected positions, then their offsets
+    unsigned *sp;               // sample index -> input index
+    long long n;                // points of the whole problem
+    int nchunks;
+    int round;
 };
 
 // ------------------------------------------------------------------------------

@@ -18,6 +18,22 @@ cudaError_t launch_centers(const Prob &p, cudaStream_t s);
 cudaError_t launch_scatter(const Prob &p, const unsigned *perm, int *out, cudaStream_t s);
 cudaError_t launch_perm_out(const Prob &p, const unsigned *perm, long long *out, cudaStream_t s);
 
+// A kernel of a fixed launch sequence, for direct launches and graph nodes alike.
+struct KNode {
+    void *fn;
+    dim3 grid, block;
+};
+// Random initialization (Section 4.5): round bytes of the curve positions from the
+// caller's order (sets ctl->bad_order unless order is a permutation of [0, n)), and
+// the kernels that select and gather one sample round (arguments: {&ps, &sel}).
+long long sample_rho_entries(long long n);
+cudaError_t launch_sample_rho(const Prob &p, const long long *order, long long m0,
+                              const unsigned *perm, unsigned char *rho_in, unsigned char *rho,
+                              cudaStream_t s);
+constexpr int kSampleSelectNodes = 6;
+int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out);
+cudaError_t launch_sample_select(const Prob &ps, const SampleSel &sel, cudaStream_t s);
+
 // iteration (gk_kmeans.cu)
 cudaError_t launch_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s);
@@ -31,5 +47,12 @@ cudaError_t launch_final_begin(const Prob &p, cudaStream_t s);
 cudaError_t launch_export(const Prob &p, cudaStream_t s);
 // The whole loop of each of count problems as one graph (independent chains).
 cudaError_t build_loop_graph(const Prob *probs, int count, cudaGraphExec_t *exec_out);
+// Random initialization: forced movement closing a sample round (mode 3 of the
+// movement) and the hand-over of its influence and counters to the main problem.
+cudaError_t launch_sample_export(const Prob &ps, Ctl *main_ctl, cudaStream_t s);
+// Sample rounds ps[0..R) (each selected, run and handed over in turn), then the
+// loop of the main problem p, as one graph.
+cudaError_t build_sampled_graph(const Prob &p, const Prob *ps, const SampleSel *sel, int R,
+                                cudaGraphExec_t *exec_out);
 
 }  // namespace gk

@@ -1503,7 +1503,9 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
 // Center movement, part 2 (ceil(k/32) CTAs): C' = sum(w x) / sum(w) (empty block:
 // C' = C), delta_c = |C'_c - C_c|, and per-CTA partial sums of the block diagonals;
 // the last CTA forms beta (the mean diagonal of the non-empty blocks, summed in CTA
-// order), the convergence test and the loop decision.  mode 1: standalone.
+// order), the convergence test and the loop decision.  mode 1: standalone; mode 3:
+// a sample round of the random initialization (Section 4.5), which always moves the
+// centers and ends its loop.
 // ------------------------------------------------------------------------------
 __device__ __forceinline__ double bb_value(const Prob &p, unsigned long long key) {
     return p.dtype == 1 ? okey_to_f64(key) : (double)okey_to_f32((unsigned)key);
@@ -1579,15 +1581,15 @@ __global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
         ctl->maxd_key = 0ull;
         ctl->beta = n > 0 ? s / (double)n : 0.0;
         ctl->max_delta = m;
-        if (mode != 0) return;
+        if (mode == 1) return;
         ctl->iter += 1;
         int conv = m < ctl->thr;
         ctl->converged = conv;
-        int move = !conv && ctl->iter < p.max_iter && ctl->status == kOk;
+        int move = (mode == 3 || (!conv && ctl->iter < p.max_iter)) && ctl->status == kOk;
         ctl->cont_move = move;
         ctl->pass_in_phase = 0;
         ctl->cont_balance = 1;
-        if (h_move) cudaGraphSetConditional(h_move, (unsigned)move);
+        if (h_move) cudaGraphSetConditional(h_move, mode == 3 ? 0u : (unsigned)move);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
 }
@@ -1630,6 +1632,25 @@ __global__ void __launch_bounds__(kKThreads) finalize_b_kernel(Prob p) {
         }
     }
     write_group(p, p.gdata2 + (size_t)sel * 2 * p.ngroups, valid, hi, g32);
+}
+
+// End of a sample round (Section 4.5): the current influence (after the movement
+// and its erosion) becomes the next round's starting influence Iin, and the round's
+// counters and status move to the main problem's control block.
+__global__ void __launch_bounds__(kKThreads) sample_export_kernel(Prob ps, Ctl *main_ctl) {
+    count_launch(ps.ctl);
+    Ctl *ctl = ps.ctl;
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ps.k) ps.Iin[c] = ps.I2[(size_t)ctl->isel * ps.k + c];
+    if (last_block(ctl) && threadIdx.x == 0) {
+        main_ctl->sample_iters += ctl->iter;
+        main_ctl->sample_passes += ctl->passes;
+        main_ctl->launches += ctl->launches;
+        main_ctl->rechecks += ctl->rechecks;
+        ctl->launches = 0ull;
+        ctl->rechecks = 0ull;
+        if (ctl->status != kOk) main_ctl->status = ctl->status;
+    }
 }
 
 // ------------------------------------------------------------------------------
@@ -1729,7 +1750,7 @@ cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s) {
                                      dim3(kAssignWarps * 32), args1, 0, s);
     if (e != cudaSuccess) return e;
     finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
-    if (mode == 0) {
+    if (mode == 0 || mode == 3) {
         finalize_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
         launch_supergroups(p, s);
     }
@@ -1743,6 +1764,11 @@ cudaError_t launch_final_begin(const Prob &p, cudaStream_t s) {
 
 cudaError_t launch_export(const Prob &p, cudaStream_t s) {
     export_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_export(const Prob &ps, Ctl *main_ctl, cudaStream_t s) {
+    sample_export_kernel<<<kgrid(ps), kKThreads, 0, s>>>(ps, main_ctl);
     return cudaGetLastError();
 }
 
@@ -1787,9 +1813,10 @@ struct NodeAdder {
 };
 }  // namespace
 
-// Adds one problem's loop as an independent chain of graph g (its own conditional
-// handles).  The kernel parameters are copied when the nodes are created.
-cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
+// Adds one problem's loop to graph g (its own conditional handles), after node
+// `after` (nullptr: an independent chain).  The kernel parameters are copied when
+// the nodes are created.
+cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after = nullptr) {
     Prob p = pc;
     cudaGraphConditionalHandle h_move, h_bal, h_fin;
     cudaError_t e = cudaGraphConditionalHandleCreate(&h_move, g, 1, cudaGraphCondAssignDefault);
@@ -1810,6 +1837,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
     if (e == cudaSuccess) e = filter_config(p, fgrid, fsmem);
     if (e != cudaSuccess) return e;
     NodeAdder top{g};
+    top.last = after;
     top.kernel((void *)init_a_kernel, kg, kb, a_init);
     top.kernel((void *)init_b_kernel, kg, kb, a_p);
     const dim3 sgg(p.nsgroups > 0 ? p.nsgroups : 1), sgb(kSuperGroup);
@@ -1845,6 +1873,67 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc) {
         if (fl.err != cudaSuccess) top.err = fl.err;
     }
     return top.err;
+}
+
+// One sample round: selection and gather of the sample, initial state from Iin and
+// C, the balance loop, the forced movement with erosion, the hand-over.
+static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const SampleSel &selc,
+                                    Ctl *main_ctl) {
+    Prob ps = psc;
+    SampleSel sel = selc;
+    cudaGraphConditionalHandle h_bal;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_bal, top.g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle none = 0;
+    int mode0 = 0, mode3 = 3;
+    void *a_sel[] = {&ps, &sel};
+    void *a_p[] = {&ps};
+    void *a_init[] = {&ps, &none, &h_bal};
+    void *a_bal0[] = {&ps, &mode0, &h_bal};
+    void *a_fin[] = {&ps, &mode3, &none, &none};
+    void *a_exp[] = {&ps, &main_ctl};
+    KNode nodes[kSampleSelectNodes];
+    int q = sample_select_nodes(ps, sel, nodes);
+    for (int i = 0; i < q; ++i) top.kernel(nodes[i].fn, nodes[i].grid, nodes[i].block, a_sel);
+    const dim3 kg(kgrid(ps)), kb(kKThreads), tg(tile_warp_grid(ps)), tb(kAssignWarps * 32);
+    const dim3 sgg(ps.nsgroups > 0 ? ps.nsgroups : 1), sgb(kSuperGroup);
+    dim3 fgrid;
+    size_t fsmem = 0;
+    e = filter_config(ps, fgrid, fsmem);
+    if (e != cudaSuccess) return e;
+    top.kernel((void *)init_a_kernel, kg, kb, a_init);
+    top.kernel((void *)init_b_kernel, kg, kb, a_p);
+    if (ps.nsgroups > 0) top.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
+    cudaGraph_t body_bal = top.loop(h_bal);
+    if (body_bal) {
+        NodeAdder bl{body_bal};
+        bl.kernel(filter_fn(ps.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
+        bl.kernel(filter_big_fn(ps.d), filter_big_grid(ps), dim3(kFilterThreads), a_p);
+        bl.kernel(assign_fn(ps.d, ps.assign_f64), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p);
+        bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
+        if (ps.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
+        if (bl.err != cudaSuccess) top.err = bl.err;
+    }
+    top.kernel(centroid_fn(ps.d, ps.dtype), tg, tb, a_p);
+    top.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
+    top.kernel((void *)finalize_b_kernel, kg, kb, a_p);
+    if (ps.nsgroups > 0) top.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
+    top.kernel((void *)sample_export_kernel, kg, kb, a_exp);
+    return top.err;
+}
+
+cudaError_t build_sampled_graph(const Prob &p, const Prob *ps, const SampleSel *sel, int R,
+                                cudaGraphExec_t *exec_out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    e = prepare_assign(assign_fn(p.d, p.assign_f64));
+    NodeAdder top{g};
+    for (int r = 0; r < R && e == cudaSuccess; ++r) e = add_sample_round(top, ps[r], sel[r], p.ctl);
+    if (e == cudaSuccess) e = add_loop_chain(g, p, top.last);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec_out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
 }
 
 cudaError_t build_loop_graph(const Prob *probs, int count, cudaGraphExec_t *exec_out) {

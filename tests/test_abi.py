@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,7 +28,8 @@ def test_header_declares_the_entry_points():
     names = _declared()
     for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
-                 "gk_status_string", "gk_abi_version", "gk_partition_batched"):
+                 "gk_status_string", "gk_abi_version", "gk_partition_batched",
+                 "gk_partition_sampled"):
         assert want in names
 
 
@@ -61,6 +64,17 @@ def test_batched_rejects_empty_batch_before_any_launch(libgk):
     inst = (gk.Instance * 1)()
     assert L.gk_partition_batched(ctypes.cast(inst, ctypes.c_void_p), 0, None, None, None) == \
         gk.GK_ERR_INVALID_ARG
+
+
+def test_sampled_rejects_missing_order_before_any_launch(libgk):
+    import paper_1805_01208_gb300 as gk
+    L = gk.lib()
+    x = np.zeros((4, 2))
+    blk = np.zeros(4, dtype=np.int32)
+    st = L.gk_partition_sampled(x.ctypes.data_as(ctypes.c_void_p), gk.GK_F64, None, 4, 2, 2, 0.03,
+                                None, 0, None, blk.ctypes.data_as(ctypes.c_void_p), None, None,
+                                None, None)
+    assert st == gk.GK_ERR_INVALID_ARG
 
 
 def test_library_is_built_for_sm103a(libgk):
