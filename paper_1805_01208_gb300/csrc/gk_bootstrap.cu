@@ -8,6 +8,8 @@
 //   tile_box_kernel    per-tile bounding boxes for the candidate filter (Section 4.4)
 //   centers_kernel     C[i] = sorted point i*n/k + n/(2k), influence 1 (Algorithm 2)
 //   scatter_kernel     block ids back to input order
+#include <type_traits>
+
 #include "gk_common.cuh"
 #include "gk_internal.h"
 
@@ -40,20 +42,36 @@ __global__ void bbox_kernel(Prob p) {
         hi[j] = (T)-INFINITY;
     }
     int bad = 0, nonpos = 0;
-    long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
-        for (int j = 0; j < p.d; ++j) {
-            T v = x[i * p.d + j];
-            bad |= !finite_val<T>(v);
-            lo[j] = v < lo[j] ? v : lo[j];
-            hi[j] = v > hi[j] ? v : hi[j];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    constexpr int kPts = 4;  // points per thread and step: their loads are in flight together
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < p.n; i0 += kPts * stride) {
+        T v[kPts][3], wv[kPts];
+#pragma unroll
+        for (int u = 0; u < kPts; ++u) {
+            const long long i = i0 + u * stride;
+            const bool ok = i < p.n;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[u][j] = (ok && j < p.d) ? x[i * p.d + j] : (T)0;
+            wv[u] = (ok && w) ? w[i] : (T)1;
         }
-        if (w) {
-            T v = w[i];
-            bad |= !finite_val<T>(v);
-            nonpos |= !(v > (T)0);
-            wlo = v < wlo ? v : wlo;
-            whi = v > whi ? v : whi;
+#pragma unroll
+        for (int u = 0; u < kPts; ++u) {
+            if (i0 + u * stride >= p.n) break;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (j >= p.d) break;
+                const T a = v[u][j];
+                bad |= !finite_val<T>(a);
+                lo[j] = a < lo[j] ? a : lo[j];
+                hi[j] = a > hi[j] ? a : hi[j];
+            }
+            if (w) {
+                const T a = wv[u];
+                bad |= !finite_val<T>(a);
+                nonpos |= !(a > (T)0);
+                wlo = a < wlo ? a : wlo;
+                whi = a > whi ? a : whi;
+            }
         }
     }
     __shared__ double s_lo[3][32], s_hi[3][32], s_wlo[32], s_whi[32];
@@ -158,20 +176,20 @@ __host__ __device__ __forceinline__ unsigned long long spread3(unsigned v) {
     return x;
 }
 
-template <int D>
-__host__ __device__ __forceinline__ unsigned long long skilling_key(unsigned X[D], int b) {
+// B bits per axis (32 in 2-D, 21 in 3-D); the levels are unrolled, and each level's
+// "exchange the low bits of X[0] and X[i], or invert those of X[0]" is branch-free.
+template <int D, int B>
+__host__ __device__ __forceinline__ unsigned long long skilling_key(unsigned X[D]) {
     // inverse undo, coarse level first
-    for (int lev = b - 1; lev >= 1; --lev) {
-        unsigned Q = 1u << lev, P = Q - 1u;
+#pragma unroll
+    for (int lev = B - 1; lev >= 1; --lev) {
+        const unsigned P = (1u << lev) - 1u;
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            if (X[i] & Q) {
-                X[0] ^= P;
-            } else {
-                unsigned t = (X[0] ^ X[i]) & P;
-                X[0] ^= t;
-                X[i] ^= t;
-            }
+            const unsigned set = 0u - ((X[i] >> lev) & 1u);  // all ones if bit lev of X[i] is set
+            const unsigned t = (X[0] ^ X[i]) & P & ~set;       // low bits to exchange (clear bit)
+            X[0] ^= (P & set) | t;
+            if (i > 0) X[i] ^= t;
         }
     }
     // Gray encode
@@ -206,7 +224,7 @@ __global__ void keys_kernel(Prob p, unsigned long long *keys_out, unsigned *perm
             q[j] = quant_bits_f32(v, p.grid_m, p.bits);
         }
     }
-    keys_out[i] = skilling_key<D>(q, p.bits);
+    keys_out[i] = skilling_key<D, D == 2 ? 32 : 21>(q);
     if (perm_out) perm_out[i] = (unsigned)i;
 }
 
@@ -223,19 +241,45 @@ constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 
-__global__ void radix_upsweep(const unsigned long long *keys, long long n, int shift,
-                              int tiles_per_seg, int G, unsigned *hist, Ctl *ctl) {
+__global__ void __launch_bounds__(kSortThreads)
+radix_upsweep(const unsigned long long *keys, long long n, int shift, int tiles_per_seg, int G,
+              unsigned *hist, Ctl *ctl) {
     count_launch(ctl);
-    __shared__ unsigned cnt[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    __shared__ unsigned cnt[kSortWarps][256];  // per-warp counts (one atomic per distinct digit)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int w = 0; w < kSortWarps; ++w) cnt[w][tid] = 0;
     __syncthreads();
-    long long beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
+    const long long beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;  // even
     long long end = beg + (long long)tiles_per_seg * kSortTile;
     if (end > n) end = n;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x)
-        atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    auto count = [&](unsigned d) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && (peers & ((1u << lane) - 1u)) == 0u)
+            atomicAdd(&cnt[warp][d], (unsigned)__popc(peers));
+    };
+    // pairs of keys (16-byte loads), kLoads pairs in flight per thread
+    constexpr int kLoads = 4;
+    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(keys);
+    const long long pend = beg + ((end - beg) & ~1ll);  // end of the whole pairs
+    for (long long i0 = beg; i0 < pend; i0 += 2ll * kSortThreads * kLoads) {
+        ulonglong2 v[kLoads];
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const long long i = i0 + 2ll * (u * kSortThreads + tid);
+            v[u] = i < pend ? k2[i >> 1] : make_ulonglong2(~0ull, ~0ull);
+        }
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const long long i = i0 + 2ll * (u * kSortThreads + tid);
+            count(i < pend ? ((unsigned)(v[u].x >> shift) & 255u) : 256u);
+            count(i < pend ? ((unsigned)(v[u].y >> shift) & 255u) : 256u);
+        }
+    }
+    if (pend < end) count(tid == 0 ? ((unsigned)(keys[pend] >> shift) & 255u) : 256u);
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(long long)i * G + blockIdx.x] = cnt[i];
+    unsigned c = 0;
+    for (int w = 0; w < kSortWarps; ++w) c += cnt[w][tid];
+    hist[(long long)tid * G + blockIdx.x] = c;
 }
 
 // Row scan of the digit-major count table: CTA d turns hist[d][0..G) into exclusive
@@ -273,84 +317,138 @@ __global__ void __launch_bounds__(256) radix_scan(unsigned *hist, int G, unsigne
     if (t == 0) totals[blockIdx.x] = total;
 }
 
+// 16-byte asynchronous copy global -> shared of the first `bytes` bytes (the rest of
+// the 16 zero-filled); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Dynamic shared memory of the downsweep: the next tile (keys, values) while the
+// current one is ranked, and the current tile in digit order.
+constexpr size_t kDownsweepSmem = (size_t)kSortTile * (8 + 4) * 2;
+
 __global__ void __launch_bounds__(kSortThreads)
 radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
                 unsigned long long *keys_out, unsigned *vals_out, long long n, int shift,
                 int tiles_per_seg, int G, const unsigned *offs, const unsigned *totals, Ctl *ctl) {
     count_launch(ctl);
-    __shared__ unsigned run_off[256];
-    __shared__ unsigned whist[kSortWarps][256];
-    __shared__ unsigned wofs[kSortWarps][256];
-    __shared__ unsigned tcnt[256];
-    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    unsigned long long *stk = reinterpret_cast<unsigned long long *>(dsm);  // next tile
+    unsigned *stv = reinterpret_cast<unsigned *>(dsm + (size_t)kSortTile * 8);
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(dsm + (size_t)kSortTile * 12);
+    unsigned *sval = reinterpret_cast<unsigned *>(dsm + (size_t)kSortTile * 20);  // digit order
+    __shared__ unsigned run_off[256];               // output position of the digit's next item
+    __shared__ unsigned whist[kSortWarps][256];     // per-warp counts, then per-warp offsets
+    __shared__ unsigned tstart[256];                // start of each digit in the tile's order
+    __shared__ unsigned wsum[kSortWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     static_assert(kSortThreads == 256, "one thread per digit below");
-    {
-        // start of each digit: exclusive scan of the digit totals, plus this segment's
-        // prefix within the digit
-        const unsigned tot = totals[tid];
-        unsigned x = tot;
+    // exclusive scan over the 256 digits of v (thread tid holds digit tid's value)
+    auto digit_scan = [&](unsigned v) -> unsigned {
+        unsigned x = v;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, x, off);
             if (lane >= off) x += y;
         }
-        if (lane == 31) tcnt[warp] = x;
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
         unsigned before = 0;
-        for (int w = 0; w < warp; ++w) before += tcnt[w];
-        run_off[tid] = before + x - tot + offs[(long long)tid * G + blockIdx.x];
+        for (int w = 0; w < warp; ++w) before += wsum[w];
         __syncthreads();
-    }
-    for (int i = tid; i < kSortWarps * 256; i += kSortThreads) (&whist[0][0])[i] = 0;
-    __syncthreads();
-    unsigned lt_mask = (1u << lane) - 1u;
-    long long seg_beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
+        return before + x - v;
+    };
+    const long long seg_beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
+    // tile t of the segment into the stage (asynchronous copies, one commit group)
+    auto prefetch = [&](int t) {
+        const long long tb = seg_beg + (long long)t * kSortTile;
+        if (t < tiles_per_seg && tb < n) {
+            const int nt = (int)(n - tb < kSortTile ? n - tb : kSortTile);
+            for (int c = tid; c < kSortTile / 2; c += kSortThreads) {
+                const int b = min(16, nt * 8 - c * 16);
+                if (b > 0) cp_async16(stk + 2 * c, keys_in + tb + 2 * c, b);
+            }
+            for (int c = tid; c < kSortTile / 4; c += kSortThreads) {
+                const int b = min(16, nt * 4 - c * 16);
+                if (b > 0) cp_async16(stv + 4 * c, vals_in + tb + 4 * c, b);
+            }
+        }
+        cp_async_commit();
+    };
+    prefetch(0);
+    // start of each digit: exclusive scan of the digit totals, plus this segment's prefix
+    // within the digit
+    run_off[tid] = digit_scan(totals[tid]) + offs[(long long)tid * G + blockIdx.x];
+    for (int w = 0; w < kSortWarps; ++w) whist[w][tid] = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
     for (int t = 0; t < tiles_per_seg; ++t) {
-        long long tile_beg = seg_beg + (long long)t * kSortTile;
+        const long long tile_beg = seg_beg + (long long)t * kSortTile;
         if (tile_beg >= n) break;
+        const int nt = (int)(n - tile_beg < kSortTile ? n - tile_beg : kSortTile);
+        cp_async_wait_all();
+        __syncthreads();
         unsigned long long k[kSortItems];
         unsigned v[kSortItems], dig[kSortItems], loc[kSortItems];
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
-            long long i = tile_beg + warp * (32 * kSortItems) + r * 32 + lane;
-            bool ok = i < n;
-            k[r] = ok ? keys_in[i] : 0ull;
-            v[r] = ok ? vals_in[i] : 0u;
+            const int li = warp * (32 * kSortItems) + r * 32 + lane;
+            k[r] = li < nt ? stk[li] : 0ull;
+            v[r] = li < nt ? stv[li] : 0u;
+        }
+        __syncthreads();  // the stage is free: bring in the next tile while this one is ranked
+        prefetch(t + 1);
+        // ranks inside the warp: items of a warp in order, equal digits counted with match_any
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            const int li = warp * (32 * kSortItems) + r * 32 + lane;
+            const bool ok = li < nt;
             dig[r] = ok ? ((unsigned)(k[r] >> shift) & 255u) : 256u;
-            unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
-            unsigned base = ok ? whist[warp][dig[r]] : 0u;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+            const unsigned base = ok ? whist[warp][dig[r]] : 0u;
             loc[r] = base + __popc(peers & lt_mask);
             __syncwarp();
             if (ok && (peers & lt_mask) == 0u) whist[warp][dig[r]] = base + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
-        for (int dgt = tid; dgt < 256; dgt += kSortThreads) {
-            unsigned acc = 0;
-            for (int w = 0; w < kSortWarps; ++w) {
-                wofs[w][dgt] = acc;
-                acc += whist[w][dgt];
-            }
-            tcnt[dgt] = acc;
+        // thread = digit: per-warp offsets (in place), the tile's count and its start
+        unsigned tc = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            const unsigned c = whist[w][tid];
+            whist[w][tid] = tc;
+            tc += c;
         }
+        tstart[tid] = digit_scan(tc);
         __syncthreads();
+        // the tile in digit order in shared memory
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             if (dig[r] < 256u) {
-                unsigned dst = run_off[dig[r]] + wofs[warp][dig[r]] + loc[r];
-                if (dst < (unsigned long long)n) {  // always true when counts are consistent
-                    keys_out[dst] = k[r];
-                    vals_out[dst] = v[r];
-                }
+                const unsigned pos = tstart[dig[r]] + whist[warp][dig[r]] + loc[r];
+                skey[pos] = k[r];
+                sval[pos] = v[r];
             }
         }
         __syncthreads();
-        for (int dgt = tid; dgt < 256; dgt += kSortThreads) {
-            run_off[dgt] += tcnt[dgt];
-            for (int w = 0; w < kSortWarps; ++w) whist[w][dgt] = 0;
+        // write-out in tile order: runs of equal digits go to consecutive addresses
+        for (int i = tid; i < nt; i += kSortThreads) {
+            const unsigned long long kk = skey[i];
+            const unsigned d = (unsigned)(kk >> shift) & 255u;
+            const unsigned dst = run_off[d] + (unsigned)i - tstart[d];
+            if (dst < (unsigned long long)n) {  // always true when counts are consistent
+                keys_out[dst] = kk;
+                vals_out[dst] = sval[i];
+            }
         }
         __syncthreads();
+        run_off[tid] += tc;
+        for (int w = 0; w < kSortWarps; ++w) whist[w][tid] = 0;
     }
+    cp_async_wait_all();  // no copy outlives the kernel
 }
 
 // ------------------------------------------------------------------------------
@@ -367,8 +465,23 @@ __device__ __forceinline__ void gather_body(const Prob &p, const unsigned *perm,
     if (i < p.n_pad) {
         long long src = i < p.n ? (perm ? (long long)perm[i] : i) : 0;
         bool ok = i < p.n && src < nsrc;  // a permutation entry is always < nsrc
-        for (int j = 0; j < p.d; ++j) {
-            T v = ok ? x[src * p.d + j] : (T)0;
+        T xv[3] = {(T)0, (T)0, (T)0};
+        if (ok) {
+            if (p.d == 2 && ((uintptr_t)x % (2 * sizeof(T))) == 0) {  // one 2-element load
+                using V2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+                const V2 q = reinterpret_cast<const V2 *>(x)[src];
+                xv[0] = q.x;
+                xv[1] = q.y;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < p.d) xv[j] = x[src * p.d + j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= p.d) break;
+            T v = xv[j];
             if (sizeof(T) == 8) {
                 double dv = (double)v;
                 p.X64[j * p.n_pad + i] = dv;
@@ -399,47 +512,48 @@ __global__ void gather_kernel(Prob p, const unsigned *perm) {
 
 // Per tile: origin = centre of the bounding box of its frame coordinates, half
 // extents and radius rounded upwards so that every point of the tile lies inside.
-__global__ void tile_box_kernel(Prob p) {
+// One warp per tile (lane l: points 8l..8l+7), kTileBoxWarps tiles per CTA.
+constexpr int kTileBoxWarps = 8;
+__global__ void __launch_bounds__(kTileBoxWarps * 32) tile_box_kernel(Prob p) {
     count_launch(p.ctl);
-    int t = blockIdx.x;
-    long long i = (long long)t * kTile + threadIdx.x;
-    bool ok = i < p.n;
+    const int lane = threadIdx.x & 31;
+    const long long t = (long long)blockIdx.x * kTileBoxWarps + (threadIdx.x >> 5);
+    if (t >= p.ntiles) return;
+    const long long i0 = t * kTile + lane * 8;
     float lo[3], hi[3];
     for (int j = 0; j < 3; ++j) {
-        float v = (ok && j < p.d) ? p.X32[j * p.n_pad + i] : 0.0f;
-        lo[j] = ok ? v : INFINITY;
-        hi[j] = ok ? v : -INFINITY;
+        lo[j] = INFINITY;
+        hi[j] = -INFINITY;
     }
-    __shared__ float s[6][kTile / 32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = 0; j < 3; ++j) {
+    for (int j = 0; j < p.d; ++j) {
+        const float4 *src = reinterpret_cast<const float4 *>(p.X32 + (size_t)j * p.n_pad + i0);
+        const float4 a = src[0], b = src[1];  // inside the padded plane
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (i0 + q < p.n) {
+                lo[j] = fminf(lo[j], v[q]);
+                hi[j] = fmaxf(hi[j], v[q]);
+            }
+        }
         for (int o = 16; o; o >>= 1) {
             lo[j] = fminf(lo[j], __shfl_xor_sync(0xffffffffu, lo[j], o));
             hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
         }
-        if (lane == 0) {
-            s[j][warp] = lo[j];
-            s[3 + j][warp] = hi[j];
-        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         float o[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
         float r2 = 0.0f;
         for (int j = 0; j < p.d; ++j) {
-            float l = s[j][0], u = s[3 + j][0];
-            for (int q = 1; q < kTile / 32; ++q) {
-                l = fminf(l, s[j][q]);
-                u = fmaxf(u, s[3 + j][q]);
-            }
-            o[j] = 0.5f * l + 0.5f * u;
-            h[j] = fmaxf(__fsub_ru(u, o[j]), __fsub_ru(o[j], l));
+            o[j] = 0.5f * lo[j] + 0.5f * hi[j];
+            h[j] = fmaxf(__fsub_ru(hi[j], o[j]), __fsub_ru(o[j], lo[j]));
             r2 = __fadd_ru(r2, __fmul_ru(h[j], h[j]));
         }
         p.tiles[2 * t] = make_float4(o[0], o[1], o[2], __fsqrt_ru(r2));
         p.tiles[2 * t + 1] = make_float4(h[0], h[1], h[2], 0.0f);
     }
 }
+static int tile_box_grid(int ntiles) { return (ntiles + kTileBoxWarps - 1) / kTileBoxWarps; }
 
 // Initial centers on the curve (raw coordinates, FP64) and influence 1.
 __global__ void centers_kernel(Prob p) {
@@ -681,12 +795,16 @@ cudaError_t launch_radix_sort(const Prob &p, int key_bits, unsigned *hist, int *
     if (tps < 1) tps = 1;
     int G = (int)((ntiles + tps - 1) / tps);
     if (G < 1) G = 1;
+    // static + dynamic shared memory of the downsweep exceeds the default 48 KB
+    cudaError_t e = cudaFuncSetAttribute(radix_downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDownsweepSmem);
+    if (e != cudaSuccess) return e;
     int cur = 0;
     for (int shift = 0; shift < key_bits; shift += 8) {
         radix_upsweep<<<G, 256, 0, s>>>(p.keys[cur], n, shift, tps, G, hist, p.ctl);
         unsigned *totals = hist + (size_t)256 * G;
         radix_scan<<<256, 256, 0, s>>>(hist, G, totals, p.ctl);
-        radix_downsweep<<<G, kSortThreads, 0, s>>>(p.keys[cur], p.perm[cur], p.keys[cur ^ 1],
+        radix_downsweep<<<G, kSortThreads, kDownsweepSmem, s>>>(p.keys[cur], p.perm[cur], p.keys[cur ^ 1],
                                                     p.perm[cur ^ 1], n, shift, tps, G, hist, totals,
                                                     p.ctl);
         cur ^= 1;
@@ -703,7 +821,7 @@ cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
         gather_kernel<float><<<grid, 256, 0, s>>>(p, perm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    tile_box_kernel<<<p.ntiles, kTile, 0, s>>>(p);
+    tile_box_kernel<<<tile_box_grid(p.ntiles), kTileBoxWarps * 32, 0, s>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
@@ -733,7 +851,7 @@ int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out) {
     out[q++] = {(void *)sample_write_kernel, cg, cb};
     out[q++] = {ps.dtype == 1 ? (void *)sample_gather_kernel<double> : (void *)sample_gather_kernel<float>,
                 dim3((unsigned)blocks_for(ps.n_pad, 256)), dim3(256)};
-    out[q++] = {(void *)tile_box_kernel, dim3((unsigned)ps.ntiles), dim3(kTile)};
+    out[q++] = {(void *)tile_box_kernel, dim3((unsigned)tile_box_grid(ps.ntiles)), dim3(kTileBoxWarps * 32)};
     out[q++] = {(void *)super_box_kernel, dim3((unsigned)blocks_for(ps.nsupers, 128)), dim3(128)};
     return q;
 }

@@ -1048,7 +1048,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             cnt = 0;
             return;
         }
-        tile = (int)((unsigned long long)pos * (unsigned long long)p.qmul % (unsigned long long)p.ntiles);
+        tile = tile_of(p, pos);
         cnt = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4].x));
     };
     auto mark = [&](int tile, int cnt) -> int {  // kPass for a cooperative tile
@@ -1416,7 +1416,7 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     const int pos = blockIdx.x * kAssignWarps + w;
     if (pos >= p.ntiles) return;
     // the tile order of the assignment: neighbouring warps take tiles of different blocks
-    const int t = (int)((unsigned long long)pos * (unsigned long long)p.qmul % (unsigned long long)p.ntiles);
+    const int t = tile_of(p, pos);
     const long long i0 = (long long)t * kTile + lane * 8;
     long long nv = p.n - i0;
     const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
