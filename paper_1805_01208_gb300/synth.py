@@ -128,6 +128,52 @@ def random_order(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng([seed, 19]).permutation(n).astype(np.int64)
 
 
+def lattice_mesh(dims, seed: int, grading: float = 2.0, jitter: float = 0.5, dtype=np.float64):
+    """A graded, jittered lattice mesh standing in for the paper's simulation meshes in
+    the quality measures of Section 5.  dims = (nx, ny) or (nx, ny, nz) vertices per axis.
+    Vertex (i, j[, l]) sits at ((i + 0.5 + jitter U(-1/2, 1/2)) / nx) ** grading per axis
+    (grading > 1 refines the mesh towards the origin, as adaptive refinement does); edges
+    join lattice neighbours along each axis and, in 2-D, along the (+1, +1) diagonal (a
+    triangulated grid, degree 6 inside).  The vertices are returned in a random order.
+    Returns (points (n, d), row_ptr (n + 1,) int64, col int32) with every edge stored in
+    both of its rows."""
+    dims = tuple(int(v) for v in dims)
+    d = len(dims)
+    n = int(np.prod(dims))
+    rng = np.random.default_rng([seed, 20])
+    idx = np.indices(dims).reshape(d, -1)  # lattice coordinates of lattice vertex L
+    u = (idx + 0.5 + jitter * (rng.random((d, n)) - 0.5)) / np.array(dims)[:, None]
+    pts_lattice = (u ** grading).T
+    # stencil of lattice neighbours (both directions of every edge direction)
+    steps = [tuple(1 if a == b else 0 for b in range(d)) for a in range(d)]
+    if d == 2:
+        steps.append((1, 1))
+    steps = steps + [tuple(-c for c in st) for st in steps]
+    strides = np.array([int(np.prod(dims[a + 1:])) for a in range(d)], dtype=np.int64)
+    L = np.arange(n, dtype=np.int64)
+    nbr = np.empty((n, len(steps)), dtype=np.int64)
+    valid = np.ones((n, len(steps)), dtype=bool)
+    for q, st in enumerate(steps):
+        for a in range(d):
+            c = idx[a] + st[a]
+            valid[:, q] &= (c >= 0) & (c < dims[a])
+        nbr[:, q] = L + int(np.dot(st, strides))
+    cnt_lat = valid.sum(1)
+    rp_lat = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt_lat, out=rp_lat[1:])
+    col_lat = nbr[valid]  # row-major: the rows stay grouped
+    # random vertex order: input position p holds lattice vertex order[p]
+    order = rng.permutation(n)
+    pos = np.empty(n, dtype=np.int64)
+    pos[order] = np.arange(n, dtype=np.int64)
+    cnt = cnt_lat[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt, out=row_ptr[1:])
+    src_start = np.repeat(rp_lat[order] - row_ptr[:-1], cnt)
+    b = pos[col_lat[src_start + np.arange(row_ptr[-1], dtype=np.int64)]]
+    return pts_lattice[order].astype(dtype), row_ptr, b.astype(np.int32)
+
+
 # --------------------------------------------------------------------------------
 # Named workloads.  Sizes and shapes of the partitioning benchmarks this library is
 # measured on; seeds fixed so that every run sees the same points.
