@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sampled", action="store_true",
                     help="skip the partition with random initialization (Section 4.5)")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the edge cut / communication volume comparison on a mesh")
     return ap.parse_args()
 
 
@@ -338,6 +340,11 @@ def main():
         sampled = _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, ms_per_step,
                                 max(1, min(3, args.steps)))
 
+    # ---- partition quality (Section 5 measures) on a mesh of the same scale ---------------
+    quality = None
+    if not args.no_quality and rank == 0:
+        quality = _quality(gk, synth, spec, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x, w, spec, args.cpu_seconds)
@@ -355,7 +362,8 @@ def main():
                 "rechecked_points_per_step": last["rechecked_points"],
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "fp32_form": fp32, "sampled_init": sampled, "cpu_baseline": cpu}
+                "fp32_form": fp32, "sampled_init": sampled, "quality": quality,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -532,6 +540,37 @@ def _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, plain_ms, steps)
             "balance_passes": res["balance_passes"], "balanced": res["balanced"],
             "max_imbalance": res["max_imbalance"], "speedup_vs_plain": plain_ms / ms,
             "order": "seeded uniform permutation (host-generated, device-resident)"}
+
+
+def _quality(gk, synth, spec, stream):
+    """Edge cut and communication volume (gk_partition_quality) of balanced k-means and of
+    the plain curve split (the i-th n/k points on the Hilbert curve form block i) on a
+    graded 3-D lattice mesh with as many vertices as the workload has points (at most
+    200^3), the workload's k and eps."""
+    import torch
+    side = int(round(min(spec["n"], 200 ** 3) ** (1.0 / 3.0)))
+    x, rp, col = synth.lattice_mesh((side, side, side), spec["seed"])
+    n, k = len(x), spec["k"]
+    xt = torch.from_numpy(x).cuda()
+    rpt, colt = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
+    block, _, _, res = gk.partition(xt, k, spec["eps"])
+    perm, _ = gk.sfc_init(xt, k)
+    sfc = torch.empty(n, dtype=torch.int32, device=xt.device)
+    sfc[perm] = (torch.arange(n, device=xt.device, dtype=torch.int64) * k // n).to(torch.int32)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    qk, _, _ = gk.partition_quality(rpt, colt, block, k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    qs, _, _ = gk.partition_quality(rpt, colt, sfc, k)
+    return {"mesh": f"graded 3-D lattice {side}^3 (6-neighbour), random vertex order",
+            "vertices": n, "edges": int(rp[-1]) // 2, "k": k, "kmeans": qk, "sfc_split": qs,
+            "kmeans_balanced": res["balanced"], "kmeans_partition_ms": res["time_total_ms"],
+            "quality_ms": e0.elapsed_time(e1),
+            "cut_ratio_kmeans_over_sfc": qk["edge_cut"] / max(1, qs["edge_cut"]),
+            "max_comm_ratio_kmeans_over_sfc": qk["max_comm_volume"] / max(1, qs["max_comm_volume"])}
 
 
 def _attach_traffic(roof, workload):

@@ -252,6 +252,34 @@ typedef struct gk_instance {
 gk_status gk_partition_batched(const gk_instance *inst, int32_t count, const gk_options *opt,
                                gk_result *results, void *stream);
 
+/* Quality of a partition (Section 5 measures). */
+typedef struct gk_quality {
+    int64_t edge_cut;           /* edges whose ends lie in different blocks                  */
+    int64_t total_comm_volume;  /* sum over blocks of comm(V_i)                              */
+    int64_t max_comm_volume;    /* max over blocks of comm(V_i)                              */
+    int64_t max_ext;            /* max over blocks of ext(V_i)                               */
+    int64_t boundary_vertices;  /* vertices with a neighbour in another block                */
+} gk_quality;
+
+/*
+ * Edge cut and communication volume of a partition of a graph (Section 5): for block
+ * V_i, ext(V_i) = edges {u, v} with u in V_i and v outside, and comm(V_i) = sum over
+ * v in V_i of the number of blocks other than V_i holding a neighbour of v (the printed
+ * definition does not exclude V_i; counting it would add the block's size); the edge
+ * cut is sum_i ext(V_i) / 2.
+ *   row_ptr: n + 1 int64 offsets into col (row_ptr[0] = 0, row_ptr[n] = nnz);
+ *   col:     nnz int32 neighbours in [0, n); every undirected edge stored in both rows
+ *            (self-loops are ignored, repeated entries count as parallel edges);
+ *   block:   n int32 block ids in [0, k);
+ *   ext_out, comm_out: k int64 each (nullable);  quality: nullable.
+ * Every pointer may be host or device memory.  Malformed input (row ranges outside
+ * [0, nnz], neighbours outside [0, n), block ids outside [0, k)) is found on the device
+ * and gives GK_ERR_INVALID_ARG.  Requires 1 <= n < 2^31, nnz >= 0, k >= 1.
+ */
+gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
+                               const int32_t *block, int32_t k, int64_t *ext_out,
+                               int64_t *comm_out, gk_quality *quality, void *stream);
+
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);
 

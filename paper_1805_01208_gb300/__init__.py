@@ -100,6 +100,20 @@ class Instance(ctypes.Structure):
     ]
 
 
+class Quality(ctypes.Structure):
+    """gk_quality (include/gk.h)."""
+    _fields_ = [
+        ("edge_cut", ctypes.c_int64),
+        ("total_comm_volume", ctypes.c_int64),
+        ("max_comm_volume", ctypes.c_int64),
+        ("max_ext", ctypes.c_int64),
+        ("boundary_vertices", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -123,6 +137,8 @@ def lib():
         L.gk_partition.argtypes = [P, i32, P, i64, i32, i32, dbl, P, P, P, P, P, P]
         L.gk_partition_sampled.argtypes = [P, i32, P, i64, i32, i32, dbl, P, i64, P, P, P, P,
                                            P, P]
+        L.gk_partition_quality.argtypes = [P, P, i64, i64, P, i32, P, P, P, P]
+        L.gk_partition_quality.restype = i32
         for name in ("gk_hilbert_keys", "gk_sfc_init", "gk_assign", "gk_move_centers",
                      "gk_balanced_kmeans", "gk_partition", "gk_partition_sampled"):
             getattr(L, name).restype = i32
@@ -347,6 +363,21 @@ def partition_sampled(coords, k: int, eps: float, order, sample0: int = 0, weigh
                                     _stream(coords, stream))
     _check(st, "gk_partition_sampled", allow=(GK_ERR_NOT_BALANCED,))
     return block, centers, infl, res.as_dict()
+
+
+def partition_quality(row_ptr, col, block, k: int, stream=None):
+    """Edge cut and communication volume (Section 5) of a partition of a graph given as
+    a symmetric CSR adjacency (row_ptr int64 n+1, col int32).  Returns (dict, ext, comm)
+    with the per-block ext and comm as int64 arrays on the side of `block`."""
+    n = int(block.shape[0])
+    nnz = int(col.shape[0])
+    ext = _empty(block, (k,), "i64")
+    comm = _empty(block, (k,), "i64")
+    q = Quality()
+    st = lib().gk_partition_quality(_ptr(row_ptr), _ptr(col), n, nnz, _ptr(block), k, _ptr(ext),
+                                    _ptr(comm), ctypes.byref(q), _stream(block, stream))
+    _check(st, "gk_partition_quality")
+    return q.as_dict(), ext, comm
 
 
 def partition_batched(problems, options: Options | None = None, stream=None):

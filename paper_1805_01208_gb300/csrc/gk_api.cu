@@ -1037,6 +1037,68 @@ gk_status gk_partition_sampled(const void *coords, int32_t dtype, const void *we
                          block_out, centers_out, influence_out, result, stream, order, sample0);
 }
 
+gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
+                               const int32_t *block, int32_t k, int64_t *ext_out,
+                               int64_t *comm_out, gk_quality *quality, void *stream) {
+    if (!row_ptr || (!col && nnz > 0) || !block || n < 1 || n >= (1ll << 31) || nnz < 0 || k < 1)
+        return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    const void *in[3] = {row_ptr, col, block};
+    const size_t in_bytes[3] = {(size_t)(n + 1) * 8, (size_t)nnz * 4, (size_t)n * 4};
+    const size_t align[3] = {8, 4, 4};
+    PtrKind kind[3];
+    size_t need = 0;
+    for (int i = 0; i < 3; ++i) {
+        kind[i] = in[i] ? ptr_kind(in[i], dev) : kDevice;
+        if (kind[i] == kForeign || (kind[i] == kDevice && ((uintptr_t)in[i] % align[i])))
+            return GK_ERR_INVALID_ARG;
+        if (kind[i] == kHost) need += align_up(in_bytes[i]);
+    }
+    if ((ext_out && ptr_kind(ext_out, dev) == kForeign) || (comm_out && ptr_kind(comm_out, dev) == kForeign))
+        return GK_ERR_INVALID_ARG;
+    need += 2 * align_up((size_t)k * 8) + align_up(5 * 8) + align_up(sizeof(int));
+    gk_status st = ensure_workspace(need);
+    if (st != GK_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = g_ws.dev;
+    const void *dptr[3];
+    for (int i = 0; i < 3; ++i) {
+        if (kind[i] == kHost) {
+            GK_CUDA(cudaMemcpyAsync(ws, in[i], in_bytes[i], cudaMemcpyHostToDevice, s));
+            dptr[i] = ws;
+            ws += align_up(in_bytes[i]);
+        } else {
+            dptr[i] = in[i];
+        }
+    }
+    unsigned long long *ext = (unsigned long long *)ws;
+    ws += align_up((size_t)k * 8);
+    unsigned long long *comm = (unsigned long long *)ws;
+    ws += align_up((size_t)k * 8);
+    unsigned long long *out = (unsigned long long *)ws;
+    ws += align_up(5 * 8);
+    int *bad = (int *)ws;
+    GK_CUDA(launch_quality((const long long *)dptr[0], (const int *)dptr[1], n, nnz,
+                           (const int *)dptr[2], k, ext, comm, out, bad, s));
+    if (ext_out) GK_CUDA(cudaMemcpyAsync(ext_out, ext, (size_t)k * 8, cudaMemcpyDefault, s));
+    if (comm_out) GK_CUDA(cudaMemcpyAsync(comm_out, comm, (size_t)k * 8, cudaMemcpyDefault, s));
+    unsigned long long h[5];
+    int hbad = 0;
+    GK_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return GK_ERR_INVALID_ARG;
+    if (quality) {
+        quality->edge_cut = (int64_t)h[0];
+        quality->total_comm_volume = (int64_t)h[1];
+        quality->max_comm_volume = (int64_t)h[2];
+        quality->max_ext = (int64_t)h[3];
+        quality->boundary_vertices = (int64_t)h[4];
+    }
+    return GK_OK;
+}
+
 void gk_release(void) { release_all(); }
 
 }  // extern "C"

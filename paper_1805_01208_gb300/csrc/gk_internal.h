@@ -34,6 +34,13 @@ constexpr int kSampleSelectNodes = 6;
 int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out);
 cudaError_t launch_sample_select(const Prob &ps, const SampleSel &sel, cudaStream_t s);
 
+// partition quality (gk_quality.cu): ext and comm per block (k entries each), out[0..4] =
+// edge cut, total comm, max comm, max ext, boundary vertices; *bad set on malformed input
+cudaError_t launch_quality(const long long *row_ptr, const int *col, long long n, long long nnz,
+                           const int *block, int k, unsigned long long *ext,
+                           unsigned long long *comm, unsigned long long *out, int *bad,
+                           cudaStream_t s);
+
 // iteration (gk_kmeans.cu)
 cudaError_t launch_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s);

@@ -29,7 +29,7 @@ def test_header_declares_the_entry_points():
     for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
                  "gk_status_string", "gk_abi_version", "gk_partition_batched",
-                 "gk_partition_sampled"):
+                 "gk_partition_sampled", "gk_partition_quality"):
         assert want in names
 
 
@@ -75,6 +75,21 @@ def test_sampled_rejects_missing_order_before_any_launch(libgk):
                                 None, 0, None, blk.ctypes.data_as(ctypes.c_void_p), None, None,
                                 None, None)
     assert st == gk.GK_ERR_INVALID_ARG
+
+
+def test_quality_rejects_bad_arguments_before_any_launch(libgk):
+    import paper_1805_01208_gb300 as gk
+    L = gk.lib()
+    assert ctypes.sizeof(gk.Quality) == 40
+    rp = np.zeros(3, dtype=np.int64)
+    blk = np.zeros(2, dtype=np.int32)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert L.gk_partition_quality(None, None, 2, 0, P(blk), 1, None, None, None, None) == \
+        gk.GK_ERR_INVALID_ARG
+    assert L.gk_partition_quality(P(rp), None, 2, 0, P(blk), 0, None, None, None, None) == \
+        gk.GK_ERR_INVALID_ARG
+    assert L.gk_partition_quality(P(rp), None, 2, 4, P(blk), 1, None, None, None, None) == \
+        gk.GK_ERR_INVALID_ARG
 
 
 def test_library_is_built_for_sm103a(libgk):
