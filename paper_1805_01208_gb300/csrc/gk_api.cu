@@ -298,7 +298,7 @@ struct Call {
         p.ntiles = (int)(p.n_pad / kTile);
         p.nsupers = (p.ntiles + kSuperTiles - 1) / kSuperTiles;
         p.qmul = tile_order_multiplier(p.ntiles);
-        p.inv_ntiles = 1.0 / (double)p.ntiles;
+        p.tile_magic = ~0ull / (unsigned long long)p.ntiles;
         p.bits = d == 2 ? 32 : 21;
         int dev = 0;
         GK_CUDA(cudaGetDevice(&dev));
@@ -534,7 +534,7 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.ntiles = (int)(ps.n_pad / kTile);
     ps.nsupers = (ps.ntiles + kSuperTiles - 1) / kSuperTiles;
     ps.qmul = tile_order_multiplier(ps.ntiles);
-    ps.inv_ntiles = 1.0 / (double)ps.ntiles;
+    ps.tile_magic = ~0ull / (unsigned long long)ps.ntiles;
     ps.keys[0] = ps.keys[1] = nullptr;
     ps.perm[0] = ps.perm[1] = nullptr;
     ps.X32 = sb.X32;

@@ -19,40 +19,51 @@ namespace gk {
 // Bounding box.  Per-thread extremes in the input precision, CTA reduction, then
 // one ordered-key atomic per CTA and axis.
 // ------------------------------------------------------------------------------
+// The extremes are taken on ordered keys (integer min / max: no FP64 pipe work, which
+// is scarce on this GPU); a NaN or infinity sets nonfinite, a weight <= 0 nonpositive_w.
 template <typename T>
-__device__ __forceinline__ bool finite_val(T v);
+struct KeyBits;
 template <>
-__device__ __forceinline__ bool finite_val<float>(float v) {
-    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
-}
+struct KeyBits<float> {
+    using K = unsigned;
+    __device__ static K bits(float v) { return __float_as_uint(v); }
+    __device__ static bool nonfinite(K b) { return (b & 0x7f800000u) == 0x7f800000u; }
+    __device__ static bool nonpositive(K b) { return (b >> 31) || b == 0u; }
+    __device__ static K key(K b) { return (b >> 31) ? ~b : (b | 0x80000000u); }
+    __device__ static unsigned long long key64(K k) { return okey_f64((double)okey_to_f32(k)); }
+};
 template <>
-__device__ __forceinline__ bool finite_val<double>(double v) {
-    return (((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
-}
+struct KeyBits<double> {
+    using K = unsigned long long;
+    __device__ static K bits(double v) { return (K)__double_as_longlong(v); }
+    __device__ static bool nonfinite(K b) { return ((b >> 52) & 0x7ff) == 0x7ff; }
+    __device__ static bool nonpositive(K b) { return (b >> 63) || b == 0ull; }
+    __device__ static K key(K b) { return (b >> 63) ? ~b : (b | 0x8000000000000000ull); }
+    __device__ static unsigned long long key64(K k) { return k; }
+};
 
 template <typename T>
 __global__ void bbox_kernel(Prob p) {
     count_launch(p.ctl);
-    const T *x = (const T *)p.coords;
-    const T *w = (const T *)p.weights;
-    T lo[3], hi[3];
-    T wlo = (T)INFINITY, whi = (T)-INFINITY;
-    for (int j = 0; j < 3; ++j) {
-        lo[j] = (T)INFINITY;
-        hi[j] = (T)-INFINITY;
-    }
+    using KB = KeyBits<T>;
+    using K = typename KB::K;
+    const K kmin0 = ~(K)0, kmax0 = (K)0;
+    const K *x = (const K *)p.coords;
+    const K *w = (const K *)p.weights;
+    K lo[3] = {kmin0, kmin0, kmin0}, hi[3] = {kmax0, kmax0, kmax0};
+    K wlo = kmin0, whi = kmax0;
     int bad = 0, nonpos = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     constexpr int kPts = 4;  // points per thread and step: their loads are in flight together
     for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < p.n; i0 += kPts * stride) {
-        T v[kPts][3], wv[kPts];
+        K v[kPts][3], wv[kPts];
 #pragma unroll
         for (int u = 0; u < kPts; ++u) {
             const long long i = i0 + u * stride;
             const bool ok = i < p.n;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) v[u][j] = (ok && j < p.d) ? x[i * p.d + j] : (T)0;
-            wv[u] = (ok && w) ? w[i] : (T)1;
+            for (int j = 0; j < 3; ++j) v[u][j] = (ok && j < p.d) ? x[i * p.d + j] : (K)0;
+            wv[u] = (ok && w) ? w[i] : (K)0;
         }
 #pragma unroll
         for (int u = 0; u < kPts; ++u) {
@@ -60,37 +71,39 @@ __global__ void bbox_kernel(Prob p) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 if (j >= p.d) break;
-                const T a = v[u][j];
-                bad |= !finite_val<T>(a);
-                lo[j] = a < lo[j] ? a : lo[j];
-                hi[j] = a > hi[j] ? a : hi[j];
+                const K b = v[u][j];
+                bad |= KB::nonfinite(b);
+                const K key = KB::key(b);
+                lo[j] = min(lo[j], key);
+                hi[j] = max(hi[j], key);
             }
             if (w) {
-                const T a = wv[u];
-                bad |= !finite_val<T>(a);
-                nonpos |= !(a > (T)0);
-                wlo = a < wlo ? a : wlo;
-                whi = a > whi ? a : whi;
+                const K b = wv[u];
+                bad |= KB::nonfinite(b);
+                nonpos |= KB::nonpositive(b);
+                const K key = KB::key(b);
+                wlo = min(wlo, key);
+                whi = max(whi, key);
             }
         }
     }
-    __shared__ double s_lo[3][32], s_hi[3][32], s_wlo[32], s_whi[32];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ K s_lo[3][32], s_hi[3][32], s_wlo[32], s_whi[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = 0; j < 3; ++j) {
-        double a = (double)lo[j], b = (double)hi[j];
+        K a = lo[j], b = hi[j];
         for (int o = 16; o; o >>= 1) {
-            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            a = min(a, (K)__shfl_xor_sync(0xffffffffu, a, o));
+            b = max(b, (K)__shfl_xor_sync(0xffffffffu, b, o));
         }
         if (lane == 0) {
             s_lo[j][warp] = a;
             s_hi[j][warp] = b;
         }
     }
-    double a = (double)wlo, b = (double)whi;
+    K a = wlo, b = whi;
     for (int o = 16; o; o >>= 1) {
-        a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        a = min(a, (K)__shfl_xor_sync(0xffffffffu, a, o));
+        b = max(b, (K)__shfl_xor_sync(0xffffffffu, b, o));
     }
     if (lane == 0) {
         s_wlo[warp] = a;
@@ -100,22 +113,22 @@ __global__ void bbox_kernel(Prob p) {
     nonpos = __syncthreads_or(nonpos);
     if (threadIdx.x == 0) {
         for (int j = 0; j < p.d; ++j) {
-            double l = s_lo[j][0], h = s_hi[j][0];
+            K l = s_lo[j][0], h = s_hi[j][0];
             for (int q = 1; q < nw; ++q) {
-                l = fmin(l, s_lo[j][q]);
-                h = fmax(h, s_hi[j][q]);
+                l = min(l, s_lo[j][q]);
+                h = max(h, s_hi[j][q]);
             }
-            atomicMin(&p.ctl->bb_lo[j], okey_f64(l));
-            atomicMax(&p.ctl->bb_hi[j], okey_f64(h));
+            if (l != kmin0) atomicMin(&p.ctl->bb_lo[j], KB::key64(l));
+            if (h != kmax0) atomicMax(&p.ctl->bb_hi[j], KB::key64(h));
         }
         if (w) {
-            double l = s_wlo[0], h = s_whi[0];
+            K l = s_wlo[0], h = s_whi[0];
             for (int q = 1; q < nw; ++q) {
-                l = fmin(l, s_wlo[q]);
-                h = fmax(h, s_whi[q]);
+                l = min(l, s_wlo[q]);
+                h = max(h, s_whi[q]);
             }
-            atomicMin(&p.ctl->w_lo, okey_f64(l));
-            atomicMax(&p.ctl->w_hi, okey_f64(h));
+            if (l != kmin0) atomicMin(&p.ctl->w_lo, KB::key64(l));
+            if (h != kmax0) atomicMax(&p.ctl->w_hi, KB::key64(h));
         }
         if (bad) atomicOr(&p.ctl->nonfinite, 1);
         if (nonpos) atomicOr(&p.ctl->nonpositive_w, 1);

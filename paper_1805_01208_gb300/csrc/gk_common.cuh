@@ -108,7 +108,7 @@ struct Prob {
     int d, k, dtype, weighted, assign_f64;
     int ntiles, nsupers;
     int qmul;                   // tile order of the assignment: t = pos * qmul mod ntiles
-    double inv_ntiles;          // 1 / ntiles (rounded), for that reduction
+    unsigned long long tile_magic;  // floor((2^64 - 1) / ntiles), for that reduction
     int bits, grid_m;           // Hilbert bits per axis and the scaling exponent b - E
     int Fw, Fx;                 // fixed-point exponents of weights and coordinate sums
     double origin[3];           // frame: (x - origin) * scale
@@ -147,17 +147,15 @@ struct Prob {
     Ctl *ctl;
 };
 
-// Tile at position pos of the permuted tile order: pos * qmul mod ntiles, with the
-// quotient from the FP64 reciprocal (pos, qmul < ntiles < 2^24: the product is exact in
-// FP64 and the quotient is off by at most one, which the two corrections remove).
+// Tile at position pos of the permuted tile order: pos * qmul mod ntiles by a Barrett
+// reduction with m = floor((2^64 - 1) / ntiles) (integer pipe only).  pos, qmul < ntiles
+// < 2^24, so the product is below 2^48 and the quotient estimate floor(prod m / 2^64) is
+// low by at most one: one conditional subtraction completes the remainder.
 __device__ __forceinline__ int tile_of(const Prob &p, long long pos) {
     const unsigned long long prod = (unsigned long long)pos * (unsigned long long)p.qmul;
-    const unsigned long long q = (unsigned long long)((double)prod * p.inv_ntiles);
-    long long r = (long long)(prod - q * (unsigned long long)p.ntiles);
-    if (r < 0)
-        r += p.ntiles;
-    else if (r >= p.ntiles)
-        r -= p.ntiles;
+    const unsigned long long q = __umul64hi(prod, p.tile_magic);
+    unsigned long long r = prod - q * (unsigned long long)p.ntiles;
+    if (r >= (unsigned long long)p.ntiles) r -= (unsigned long long)p.ntiles;
     return (int)r;
 }
 
