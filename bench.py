@@ -58,6 +58,8 @@ def _args():
                     help="skip the partition with random initialization (Section 4.5)")
     ap.add_argument("--no-quality", action="store_true",
                     help="skip the edge cut / communication volume comparison on a mesh")
+    ap.add_argument("--no-bounds", action="store_true",
+                    help="skip the partition with per-point bounds (gk_options.bounds = 1)")
     return ap.parse_args()
 
 
@@ -340,6 +342,11 @@ def main():
         sampled = _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, ms_per_step,
                                 max(1, min(3, args.steps)))
 
+    # ---- per-point bounds (Section 4.3 in spirit; gk_options.bounds) ---------------------
+    bounds = None
+    if not args.no_bounds:
+        bounds = _bounds_leg(gk, xt, wt, spec, stream, flush, ms_per_step, max(1, min(3, args.steps)))
+
     # ---- partition quality (Section 5 measures) on a mesh of the same scale ---------------
     quality = None
     if not args.no_quality and rank == 0:
@@ -362,7 +369,7 @@ def main():
                 "rechecked_points_per_step": last["rechecked_points"],
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "fp32_form": fp32, "sampled_init": sampled, "quality": quality,
+                "fp32_form": fp32, "sampled_init": sampled, "bounds": bounds, "quality": quality,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
@@ -540,6 +547,31 @@ def _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, plain_ms, steps)
             "balance_passes": res["balance_passes"], "balanced": res["balanced"],
             "max_imbalance": res["max_imbalance"], "speedup_vs_plain": plain_ms / ms,
             "order": "seeded uniform permutation (host-generated, device-resident)"}
+
+
+def _bounds_leg(gk, xt, wt, spec, stream, flush, plain_ms, steps):
+    """The same partition with per-point bounds: identical results, the fraction of point
+    evaluations that remain, and the time against the plain step."""
+    import torch
+    n, k, eps = int(xt.shape[0]), spec["k"], spec["eps"]
+    o = gk.default_options(assign_dtype=spec["assign"], bounds=1)
+    gk.partition(xt, k, eps, weights=wt, options=o)
+    torch.cuda.synchronize()
+    times, res = [], None
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, _, res = gk.partition(xt, k, eps, weights=wt, options=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    return {"ms_per_step": ms, "balance_passes": res["balance_passes"],
+            "evaluated_fraction": res["evaluated_points"] / (n * res["balance_passes"]),
+            "assign_ms_per_pass": res["assign_live_ms"] / max(1, res["assign_live_launches"]),
+            "speedup_vs_plain": plain_ms / ms}
 
 
 def _quality(gk, synth, spec, stream):

@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
         ("assign_dtype", ctypes.c_int32),
         ("use_graph", ctypes.c_int32),
         ("timing", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("bounds", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -77,6 +78,7 @@ class Result(ctypes.Structure):
         ("move_launches", ctypes.c_int64),
         ("assign_live_ms", ctypes.c_double),
         ("assign_live_launches", ctypes.c_int64),
+        ("evaluated_points", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -121,7 +121,7 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
     p.coop = (int *)take((size_t)p.ntiles * 4);
-    p.bigs = (int *)take((size_t)p.nsupers * 12);
+    p.bigs = (int *)take((size_t)p.nsupers * 16);
     p.blists = (int *)take((size_t)p.nsupers * kWarpList * 4);
     p.C = (double *)take((size_t)k * d * 8);
     p.Cm = (double *)take((size_t)k * d * 8);
@@ -135,6 +135,11 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.SXfix = (unsigned long long *)take((size_t)k * d * 16);
     p.BBlo = (unsigned long long *)take((size_t)k * d * 8);
     p.BBhi = (unsigned long long *)take((size_t)k * d * 8);
+    p.lg = (float *)take((size_t)kSkipHist * k * 4);
+    p.cumm = (double *)take((size_t)kSkipHist * 8);
+    p.dm = (float *)take((size_t)kSkipHist * 4);
+    p.lq = (float *)take((size_t)np * 4);
+    p.t1 = (unsigned char *)take((size_t)np);
     p.cdata2 = (float4 *)take((size_t)2 * k * 32);
     p.ngroups = (int)((k + kGroup - 1) / kGroup);
     p.gdata2 = (float4 *)take((size_t)2 * p.ngroups * 32);
@@ -161,6 +166,8 @@ struct SampleBufs {
     int *A = nullptr;
     float4 *tiles = nullptr, *supers = nullptr, *trec = nullptr;
     int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
+    float *prho = nullptr;            // per-point bounds of the sample
+    unsigned char *pt1 = nullptr;
 };
 
 size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order) {
@@ -188,8 +195,10 @@ size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order
     sb.supers = (float4 *)take((size_t)ns * 32);
     sb.trec = (float4 *)take((size_t)nt * kRecF4 * 16);
     sb.coop = (int *)take((size_t)nt * 4);
-    sb.bigs = (int *)take((size_t)ns * 12);
+    sb.bigs = (int *)take((size_t)ns * 16);
     sb.blists = (int *)take((size_t)ns * kWarpList * 4);
+    sb.prho = (float *)take((size_t)np * 4);
+    sb.pt1 = (unsigned char *)take((size_t)np);
     return off;
 }
 
@@ -439,6 +448,7 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     r->move_launches = cl.n_move;
     r->assign_live_ms = (double)c.assign_ns * 1e-6;
     r->assign_live_launches = (int64_t)c.assign_cnt;
+    r->evaluated_points = (int64_t)c.evaluated;
 }
 
 gk_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
@@ -547,6 +557,8 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.coop = sb.coop;
     ps.bigs = sb.bigs;
     ps.blists = sb.blists;
+    ps.lq = sb.prho;
+    ps.t1 = sb.pt1;
     ps.ctl = sb.ctl;
     ps.max_iter = 1;
     ps.final_balance_iter = 0;
@@ -616,7 +628,8 @@ gk_status check_options(const gk_options &o) {
     if (o.max_iter < 1 || o.max_balance_iter < 1 || o.final_balance_iter < 0 ||
         (o.assign_dtype != GK_F32 && o.assign_dtype != GK_F64) || !(o.delta_threshold == o.delta_threshold))
         return GK_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    if (o.bounds != 0 && o.bounds != 1) return GK_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
         if (o.reserved[i] != 0) return GK_ERR_INVALID_ARG;
     return GK_OK;
 }
@@ -667,6 +680,7 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     p.max_balance_iter = o.max_balance_iter;
     p.final_balance_iter = o.final_balance_iter;
     p.erosion = o.erosion;
+    p.bounds = o.bounds;
     if ((st = cl.geometry(o.delta_threshold)) != GK_OK) return st;
     GK_CUDA(cudaMemcpyAsync(&p.ctl->thr, &cl.thr, sizeof(double), cudaMemcpyHostToDevice, cl.s));
     const unsigned *perm = nullptr;
@@ -777,6 +791,7 @@ gk_status partition_batched(const gk_instance *inst, int32_t count, const gk_opt
         p.max_balance_iter = o.max_balance_iter;
         p.final_balance_iter = o.final_balance_iter;
         p.erosion = o.erosion;
+        p.bounds = o.bounds;
         if ((st = cl[i].upload_state(&hc[i])) != GK_OK) return st;
         GK_CUDA(launch_bbox(p, s));
     }
@@ -864,6 +879,7 @@ void gk_default_options(gk_options *opt) {
     opt->delta_threshold = -1.0;
     opt->assign_dtype = GK_F64;
     opt->use_graph = 1;
+    opt->bounds = 0;
 }
 
 const char *gk_status_string(int32_t status) {

@@ -11,7 +11,8 @@
 //   supers the same per supertile of kSuperTiles tiles.
 //   per tile record (written by the filter every pass, kRecF4 float4): header
 //          {count (int32; -1 = overflow: scan all centers), largest g of the tile's
-//          candidates, 0, 0}, {tile origin xyz, tile radius}, then up to kCap candidates
+//          candidates, lower bound of the E of every center left out of the list, 0},
+//          {tile origin xyz, tile radius}, then up to kCap candidates
 //          of 2 float4: {q xyz, g}, {center id (int32 bits), 0, 0, 0}; q = frame center
 //          relative to the tile origin, g = scaled 1/I^2, ascending center order.
 //   coop   the tiles with more than kFastCands candidates (or an overflowed list), taken
@@ -51,6 +52,7 @@ static_assert(kGroup == kKThreads, "a group record is written by one CTA of the 
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
 constexpr int kStripes = 64;        // striped counters for per-pass statistics
 constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers
+constexpr int kSkipHist = 64;       // passes of a phase with per-point bounds (then a fresh pass)
 
 // Error codes mirrored from gk.h (device code does not include the C header).
 constexpr int kOk = 0;
@@ -67,6 +69,10 @@ struct Ctl {
     int bad_order;                          // the sample order is not a permutation
     int sample_iters;                       // movement phases of the sample rounds
     int sample_passes;                      // assignment passes of the sample rounds
+    int phase_pass;                         // passes since the centers last moved (bounds)
+    unsigned int min_lr_key;                // ordered keys of the pass's smallest and largest
+    unsigned int max_lr_key;                //   log2 g ratio over the centers (bounds)
+    unsigned long long evaluated;           // points whose assignment was evaluated (bounds)
     int status;                             // kOk or an error code
     int balanced;                           // last pass met the bound
     int converged;                          // movement below threshold
@@ -131,7 +137,8 @@ struct Prob {
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;
     int *coop;                  // tiles of the cooperative path (ntiles entries)
-    int *bigs;                  // per long-list supertile: index, list length, largest g (bits)
+    int *bigs;                  // per long-list supertile: index, list length, largest g, smallest
+                                // dropped lower bound (bits)
     int *blists;                // their candidate lists, kWarpList entries each
     int nsm;                    // streaming multiprocessors of the device
     // per-center state
@@ -144,6 +151,15 @@ struct Prob {
     int ngroups;
     float4 *sgdata;             // 2 float4 per supergroup of kSuperGroup groups (current buffer)
     int nsgroups;               // 0: no supergroup level
+    // per-point bounds across the passes of a phase (centers fixed, influences change)
+    int bounds;                 // 1: skip points whose assignment provably holds
+    float *lg;                  // kSkipHist x k: log2 of each center's g at each pass of the phase
+    double *cumm;               // kSkipHist: running sum over the passes of (smallest - largest)
+                                // log2 g ratio, each lowered by the rounding margin
+    float *dm;                  // kSkipHist: for the current pass t, cumm[t] - cumm[t1] rounded down
+    float *lq;                  // n_pad: per point, log2 of a lower bound of E_other / E_own at its
+                                // last evaluation, plus log2 g of its own center then (rounded down)
+    unsigned char *t1;          // n_pad: phase pass of that evaluation
     Ctl *ctl;
 };
 

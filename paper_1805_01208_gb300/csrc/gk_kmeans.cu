@@ -51,6 +51,13 @@ __device__ __forceinline__ float scaled_g32(double g, int gshift) {
     return __double2float_rn(ldexp(g, -gshift));
 }
 
+// log2 of a center's g for the per-point bounds (FP32; error far below kLgMargin).  An
+// infinite or zero g gives +-inf, which makes every threshold that uses it NaN or infinite,
+// so that no point is skipped on it.
+constexpr float kLgMargin = 6.103515625e-5f;   // 2^-14: covers the rounding of two log2 values
+constexpr float kLqMargin = 2.44140625e-4f;    // 2^-12: that and two fast log2 of the bound
+__device__ __forceinline__ float lg_of(double g) { return log2f(__double2float_rn(g)); }
+
 // Record of the group of kGroup consecutive centers handled by this CTA (called by all
 // of its threads; lanes without a center pass valid = false): the box of the centers'
 // FP32 frame coordinates, rounded outwards and widened by 8 u R (the lo parts and the
@@ -162,6 +169,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         g = 1.0 / (I * I);
         p.I2[c] = I;
         p.g64_2[c] = g;
+        if (p.bounds) p.lg[c] = lg_of(g);
         float hi[3], lo[3];
         frame_center(p, c, hi, lo);
         for (int b = 0; b < 2; ++b) {
@@ -201,6 +209,13 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->nonempty = 0;
         ctl->coop_cnt = 0u;
         ctl->big_cnt = 0u;
+        ctl->phase_pass = 0;
+        ctl->min_lr_key = 0xffffffffu;
+        ctl->max_lr_key = 0u;
+        if (p.bounds) {
+            p.cumm[0] = 0.0;
+            p.dm[0] = 0.0f;
+        }
         if (h_move) cudaGraphSetConditional(h_move, 1u);
         if (h_bal) cudaGraphSetConditional(h_bal, 1u);
     }
@@ -304,10 +319,12 @@ __device__ __forceinline__ void group_bounds(const float4 &gm, const float4 &gh,
 constexpr int kGroupRegs = 8;   // group chunks whose bounds stay in registers
 constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in registers
 
+// lamS gets the smallest lower bound of the supergroups, groups and centers the level
+// drops (+inf when none): every center outside the list has E >= lamS on the supertile.
 template <int D>
 __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4 *cd, const float4 *gd,
                                               int *list, float4 *lcd, int *glist, int *sglist,
-                                              int *glist_out, float &gall) {
+                                              int *glist_out, float &gall, float &lamS) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ng = p.ngroups;
@@ -400,6 +417,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         tg = fminf(tg, t1);
     }
     const float tauG = __fmul_ru(tg, 1.0f + 256.0f * kU);
+    float lam = INFINITY, lamg = INFINITY;  // dropped supergroups / centers, dropped groups
     // chunks of 32 groups to test: all groups, or those of the kept supergroups
     int nchunk = (ng + 31) / 32;
     bool by_sg = false;
@@ -415,6 +433,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
                     group_bounds<D>(__ldg(&p.sgdata[2 * si]), __ldg(&p.sgdata[2 * si + 1]), so, sh, lb, ub);
                 }
                 keep = !(lb > tauG);
+                if (!keep) lamg = fminf(lamg, lb);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             const int pos = nks + __popc(bal & lt);
@@ -425,6 +444,8 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         if (nks <= kWarpSG) {
             by_sg = true;
             nchunk = nks;
+        } else {
+            lamg = INFINITY;  // every group is tested below
         }
     }
     int ngk = 0;  // kept groups, ascending
@@ -442,6 +463,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
                 group_bounds<D>(__ldg(&gd[2 * gi]), __ldg(&gd[2 * gi + 1]), so, sh, lb, ub);
             }
             keep = !(lb > tauG);
+            if (!keep) lamg = fminf(lamg, lb);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = ngk + __popc(bal & lt);
@@ -450,6 +472,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
     }
     __syncwarp();
     const bool gover = ngk > kWarpGroups;  // too many groups: sweep every center
+    if (!gover) lam = lamg;                // (a sweep of every center tests them one by one)
     // tau of the supertile over the centers of the kept groups (lane = center of the group)
     float tc = INFINITY;
     float clb[kCenterRegs];
@@ -485,6 +508,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
                 box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
             }
             keep = !(lb > tauS);
+            if (!keep) lam = fminf(lam, lb);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = L + __popc(bal & lt);
@@ -497,17 +521,23 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         L += __popc(bal);
     }
     __syncwarp();
+    for (int off = 16; off; off >>= 1) lam = fminf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+    lamS = lam;
     return L;
 }
 
 // Header of tile t's record (count, -1: scan all centers; the largest g the tile can
 // meet) and, for a tile with more than kCoopCands candidates, its entry in the
 // cooperative list (one thread per tile).
+// lam: smallest lower bound of the centers left out of the tile's list, which the
+// record keeps lowered by 16 u (the rounding of the bound's own arithmetic), as a lower
+// bound of every left-out center's E on the tile (+inf when all centers are evaluated).
 __device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float gkept, float gall,
-                                            const float4 &tb0) {
+                                            const float4 &tb0, float lam) {
     const bool over = cnt > kCap;
     float4 *rec = p.trec + (size_t)t * kRecF4;
-    rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, 0.f, 0.f);
+    const float lamr = over ? INFINITY : __fmul_rd(lam, 1.0f - 16.0f * kU);
+    rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, lamr, 0.f);
     rec[1] = tb0;
     const bool coop = over || cnt > kCoopCands;
     if (coop) p.coop[atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
@@ -544,16 +574,17 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         tb0 = p.tiles[2 * t];
         tb1 = p.tiles[2 * t + 1];
     }
-    float gall;
+    float gall, lamS;
     int *gl_out = p.blists + (size_t)s * kWarpList;
     const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp], s_sg[warp],
-                                    gl_out, gall);
+                                    gl_out, gall, lamS);
     if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
             const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
-            p.bigs[3 * slot] = s;
-            p.bigs[3 * slot + 1] = L;
-            p.bigs[3 * slot + 2] = __float_as_int(gall);
+            p.bigs[4 * slot] = s;
+            p.bigs[4 * slot + 1] = L;
+            p.bigs[4 * slot + 2] = __float_as_int(gall);
+            p.bigs[4 * slot + 3] = __float_as_int(L > kWarpList ? INFINITY : lamS);
         }
         return;
     }
@@ -572,13 +603,14 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         }
         const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
         int cnt = 0;
-        float gkept = 0.0f;
+        float gkept = 0.0f, lamT = lamS;
         float4 *rec = p.trec + (size_t)t * kRecF4;
         for (int i = 0; i < L; ++i) {
             const int c = list[i];
             const float4 ch = lcd[2 * i], cl = lcd[2 * i + 1];
             float lb, ub;
             box_bounds<D>(ch, cl, o, h, lb, ub);
+            if (lb > tauT) lamT = fminf(lamT, lb);
             if (!(lb > tauT)) {  // L <= kLaneMax <= kCap: always stored
                 const float q0 = (ch.x - o[0]) + cl.x;
                 const float q1 = (ch.y - o[1]) + cl.y;
@@ -589,7 +621,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
                 ++cnt;
             }
         }
-        finish_tile(p, t, cnt, gkept, gall, tb0);
+        finish_tile(p, t, cnt, gkept, gall, tb0, lamT);
     }
 }
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
@@ -609,8 +641,9 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
     const int TW = gridDim.x * kFilterWarps;
     for (int item = blockIdx.x * kFilterWarps + (threadIdx.x >> 5); item < total; item += TW) {
         const int slot = item / kSuperTiles;
-        const int s = p.bigs[3 * slot], Lr = p.bigs[3 * slot + 1];
-        const float gall = __int_as_float(p.bigs[3 * slot + 2]);
+        const int s = p.bigs[4 * slot], Lr = p.bigs[4 * slot + 1];
+        const float gall = __int_as_float(p.bigs[4 * slot + 2]);
+        float lamT = __int_as_float(p.bigs[4 * slot + 3]);
         const int t = s * kSuperTiles + item % kSuperTiles;
         if (t >= p.ntiles) continue;
         const bool all = Lr > kWarpList;
@@ -648,6 +681,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
                 float lb, ub;
                 box_bounds<D>(ch, cl, o, h, lb, ub);
                 keep = !(lb > tauT);
+                if (lb > tauT) lamT = fminf(lamT, lb);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
             const int pos = cnt + __popc(bal & lt);
@@ -661,8 +695,11 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             if (keep) gkept = fmaxf(gkept, ch.w);
             cnt += __popc(bal);
         }
-        for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
-        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0);
+        for (int off = 16; off; off >>= 1) {
+            gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
+            lamT = fminf(lamT, __shfl_xor_sync(0xffffffffu, lamT, off));
+        }
+        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0, lamT);
     }
 }
 
@@ -754,6 +791,25 @@ __device__ __forceinline__ void tile_histogram(const Prob &p, long long i0, int 
     seg_flush_u64(cur, acc, p.Sfix, p.weighted != 0);
 }
 
+// The per-point bound recorded at an evaluation: rho = (lower bound of every other
+// center's E) / (upper bound of the own center's E) -- from the runner-up E2 of the
+// tile's list less its error bound B and the filter's bound lamT of the centers left
+// out, over E1 plus B (FP32 form: B = 0 and a 2^-20 margin on each side for the rounding
+// of E) -- stored as log2(rho) lowered by kLqMargin (the two fast logarithms).  A
+// re-decided point (recheck) gets -inf: it is evaluated again in the next pass.
+// log2 through the hardware approximation, whose error (at most 2^-22.6 absolute on
+// [0.5, 2], 2 ulp elsewhere, i.e. below 2^-15 for finite FP32 inputs) kLqMargin covers.
+template <bool F64MODE>
+__device__ __forceinline__ float bound_lq(float E1, float E2, float B, float lamT, unsigned recheck) {
+    if (recheck) return -INFINITY;
+    const float U1 = F64MODE ? __fadd_ru(E1, B) : __fmul_ru(E1, 1.0f + 9.5367431640625e-7f);
+    float L1 = F64MODE ? (E2 < INFINITY ? __fsub_rd(E2, B) : INFINITY) : __fmul_rd(E2, 1.0f - 9.5367431640625e-7f);
+    L1 = fminf(L1, lamT);
+    if (!(L1 > 0.0f)) return -INFINITY;  // also NaN
+    const float v = __fsub_rd(__fsub_rd(__log2f(L1), __log2f(U1)), kLqMargin);
+    return v == v ? v : -INFINITY;
+}
+
 // ------------------------------------------------------------------------------
 // Cooperative tile: a tile with more candidates than one warp finishes in the time
 // the others take (more than kCoopCands, or all k centers when its list overflowed)
@@ -765,9 +821,9 @@ __device__ __forceinline__ void tile_histogram(const Prob &p, long long i0, int 
 // the block weights.  Called by every thread of the CTA; scratch holds at least
 // 3 * kAWarps * kTile words.
 // ------------------------------------------------------------------------------
-template <int D, bool F64MODE>
+template <int D, bool F64MODE, bool BOUNDS>
 __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int nwarps,
-                                       unsigned long long *nre) {
+                                       unsigned long long *nre, int pp, unsigned long long *nevl) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float4 *grec = p.trec + (size_t)t * kRecF4;
     const float4 hdr = grec[0], ob = grec[1];
@@ -867,6 +923,10 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
                 }
             }
         }
+        float Bq[8];
+        unsigned flag = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Bq[q] = 0.0f;
         if (F64MODE) {
             const float gl = hdr.y, sg = sqrtf(gl);
             const float R = p.R, sd = sqrtf((float)D);
@@ -880,7 +940,6 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
                 xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
             }
             const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
-            unsigned flag = 0;
             float thr[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -888,6 +947,7 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
                 const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
                 const bool okq = single || (E2[q] - E1[q]) > 2.0f * B;
                 thr[q] = E1[q] + 2.0f * B;
+                Bq[q] = B;
                 if (q < nval && !okq) flag |= 1u << q;
             }
             // FP64 re-decision, one flagged point at a time: lanes take 32 candidates at
@@ -963,6 +1023,16 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
             }
             *nre += __popc(flag);
         }
+        if constexpr (BOUNDS) {  // every point of a cooperative tile is evaluated: its bound
+            const float lamT = hdr.z;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nval) continue;
+                p.lq[i0 + q] = bound_lq<F64MODE>(E1[q], E2[q], Bq[q], lamT, (flag >> q) & 1u);
+                p.t1[i0 + q] = (unsigned char)pp;
+            }
+        }
+        if (lane == 0) *nevl += (unsigned long long)(p.n - (long long)t * kTile < kTile ? p.n - (long long)t * kTile : kTile);
         if (nval == 8) {
             int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
             dst[0] = make_int4(best[0], best[1], best[2], best[3]);
@@ -983,17 +1053,34 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
 constexpr int kAWarps = 4;
 constexpr int kAMinBlocks = 5;     // CTAs per SM of the FP32 form
 constexpr int kAMinBlocks64 = 4;   // FP64 mode: more registers for the certification
+// A stage: the tile's record head and its coordinate planes and, with per-point bounds,
+// the per-point state (block id, bound, pass of the bound), all by bulk copy.
+template <int D, bool BOUNDS>
 struct AStage {
     float4 rec[2 + 2 * kFastCands];
-    float x[3][kTile];
+    float x[D][kTile];
 };
-static_assert(sizeof(AStage) * 2 * kAWarps >= 3 * kAWarps * kTile * 4, "scratch of the cooperative tiles");
+template <int D>
+struct AStage<D, true> {
+    float4 rec[2 + 2 * kFastCands];
+    float x[D][kTile];
+    int a[kTile];             // block ids: the previous ones, then this pass's
+    float lq[kTile];          // log2 of the bound, at t1
+    unsigned char t1[kTile];
+};
+static_assert(sizeof(AStage<2, false>) * 2 * kAWarps >= 3 * kAWarps * kTile * 4,
+              "scratch of the cooperative tiles");
+template <int D, bool BOUNDS>
+constexpr size_t assign_smem() { return sizeof(AStage<D, BOUNDS>) * 2 * kAWarps; }
 
-template <int D, bool F64MODE>
+// BOUNDS: per-point bounds across the passes of a phase (gk_options.bounds); without
+// them every point is evaluated every pass.
+template <int D, bool F64MODE, bool BOUNDS>
 __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinBlocks) assign_kernel(Prob p) {
     count_launch(p.ctl);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_assign0 = globaltimer_ns();
-    __shared__ __align__(128) AStage st[kAWarps][2];
+    extern __shared__ __align__(128) unsigned char a_dsm[];
+    AStage<D, BOUNDS> (*st)[2] = reinterpret_cast<AStage<D, BOUNDS> (*)[2]>(a_dsm);
     __shared__ __align__(8) unsigned long long bar[kAWarps][2];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
@@ -1003,14 +1090,23 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     }
     __syncwarp();
     const int sel = p.ctl->isel;
-    const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4);
-    unsigned long long nre = 0;
+    unsigned long long nre = 0, nevl = 0;
+    // per-point bounds: this pass's index in the phase; a fresh pass evaluates every point
+    const int pp = BOUNDS ? p.ctl->phase_pass : 0;
+    const bool fresh = !BOUNDS || pp == 0;
+    const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4) + (fresh ? 0u : (unsigned)(kTile * 9));
+    __shared__ float dm_s[kSkipHist];
+    __shared__ unsigned char s_act[kAWarps][kTile];  // the points the warp evaluates
+    if (!fresh)
+        for (int i = threadIdx.x; i <= pp; i += kAWarps * 32) dm_s[i] = p.dm[i];
+    __syncthreads();
     {
         // cooperative tiles first (the stages serve as scratch; no copy is in flight yet)
         const int HC = (int)p.ctl->coop_cnt;
         float *scratch = reinterpret_cast<float *>(&st[0][0]);
         for (int ci = blockIdx.x; ci < HC; ci += gridDim.x) {
-            coop_tile<D, F64MODE>(p, p.coop[ci], scratch, kAWarps, &nre);
+            coop_tile<D, F64MODE, BOUNDS>(p, p.coop[ci], scratch, kAWarps, &nre, pp, &nevl);
+            fence_proxy_async();  // the scratch writes precede the stages' bulk copies
             __syncthreads();
         }
     }
@@ -1022,6 +1118,13 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             for (int j = 0; j < D; ++j)
                 bulk_g2s(st[w][b].x[j], p.X32 + (size_t)j * p.n_pad + (size_t)t * kTile, kTile * 4,
                          &bar[w][b]);
+            if constexpr (BOUNDS) {
+                if (!fresh) {
+                    bulk_g2s(st[w][b].a, p.A + (size_t)t * kTile, kTile * 4, &bar[w][b]);
+                    bulk_g2s(st[w][b].lq, p.lq + (size_t)t * kTile, kTile * 4, &bar[w][b]);
+                    bulk_g2s(st[w][b].t1, p.t1 + (size_t)t * kTile, kTile, &bar[w][b]);
+                }
+            }
         }
     };
     // Tiles come from kQueues interleaved queues: queue q serves positions q, q + kQueues,
@@ -1103,175 +1206,363 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             return;
         }
         if (b) ph1 ^= 1u; else ph0 ^= 1u;
-        const AStage &S = st[w][b];
+        AStage<D, BOUNDS> &S = st[w][b];
         const int ncand = __float_as_int(S.rec[0].x);  // 0 < ncand <= kFastCands
-        const float gl = S.rec[0].y;  // largest g among the tile's candidates
+        const float gl = S.rec[0].y;    // largest g among the tile's candidates
+        const float lamT = S.rec[0].z;  // lower bound of the E of every center left out
         const float sg = sqrtf(gl);
         const float4 ob = S.rec[1];
         const float o[3] = {ob.x, ob.y, ob.z};
-        const long long i0 = (long long)t * kTile + lane * 8;
+        const long long t0 = (long long)t * kTile;
+        const long long i0 = t0 + lane * 8;
         long long nv = p.n - i0;
         const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-
-        float2 xp[3][4];
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            const float4 *src = reinterpret_cast<const float4 *>(&S.x[j][lane * 8]);
-            float4 a = src[0], c4 = src[1];
-            xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
-            xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
-            xp[j][2] = make_float2(c4.x - o[j], c4.y - o[j]);
-            xp[j][3] = make_float2(c4.z - o[j], c4.w - o[j]);
-        }
-        float E1[8], E2[8];
+        // error-bound constants of the FP64 mode (see the comment above); the coordinate
+        // term with the tile's radius (rounded up), which bounds |x'| of all its points
+        const float sd = sqrtf((float)D);
+        const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
+        const float e0 = sd * kU * (p.R + 8.0f * __fmul_ru(ob.w, 1.0f + 9.5367431640625e-7f));
         int best[8];
+        if (fresh) {
+            // every point is evaluated: lane l takes points 8l..8l+7
+            nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
+            float2 xp[3][4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            E1[q] = INFINITY;
-            E2[q] = INFINITY;
-            best[q] = 0;
-        }
-        // candidates from the stage (shared-memory broadcast), two at a time
-        auto consume = [&](const float4 &qg, int c) {
-            const float2 g2 = make_float2(qg.w, qg.w), nqx = make_float2(-qg.x, -qg.x),
-                         nqy = make_float2(-qg.y, -qg.y), nqz = make_float2(-qg.z, -qg.z);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float2 dx = __fadd2_rn(xp[0][q], nqx);
-                const float2 dy = __fadd2_rn(xp[1][q], nqy);
-                float2 ss = __fmul2_rn(dx, dx);
-                ss = __ffma2_rn(dy, dy, ss);
-                if (D == 3) {
-                    const float2 dz = __fadd2_rn(xp[2][q], nqz);
-                    ss = __ffma2_rn(dz, dz, ss);
-                }
-                const float2 E = __fmul2_rn(g2, ss);
-                argmin_update<F64MODE>(E.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
-                argmin_update<F64MODE>(E.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
+            for (int j = 0; j < D; ++j) {
+                const float4 *src = reinterpret_cast<const float4 *>(&S.x[j][lane * 8]);
+                float4 a = src[0], c4 = src[1];
+                xp[j][0] = make_float2(a.x - o[j], a.y - o[j]);
+                xp[j][1] = make_float2(a.z - o[j], a.w - o[j]);
+                xp[j][2] = make_float2(c4.x - o[j], c4.y - o[j]);
+                xp[j][3] = make_float2(c4.z - o[j], c4.w - o[j]);
             }
-        };
-        int jj = 0;
-        for (; jj + 1 < ncand; jj += 2) {
-            const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
-            const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
-            consume(qa, ca);
-            consume(qb, cb);
-        }
-        if (jj < ncand) {
-            const float4 qa = S.rec[2 + 2 * jj];
-            consume(qa, __float_as_int(S.rec[3 + 2 * jj].x));
-        }
-        if (F64MODE) {
-            // error-bound constants; see the comment above
-            const float R = p.R;
-            const float sd = sqrtf((float)D);
-            const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
-            // coordinate term with the largest |x'| of the lane's points
-            float xn2 = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
-                xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
-            }
-            const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
-            // B grows with E: one bound at the lane's largest finite runner-up certifies
-            // most points; a point it does not certify gets its own bound
-            float e2max = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (E2[q] < INFINITY) e2max = fmaxf(e2max, E2[q]);
-            const float Bl = cert_bound(e0, sg, gl, beta2, e2max);
-            unsigned flag = 0;
-            float thr[8];
+            float E1[8], E2[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
-                bool okq = single || (E2[q] - E1[q]) > 2.0f * Bl;
-                thr[q] = INFINITY;
-                if (!okq) {
-                    const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
-                    okq = (E2[q] - E1[q]) > 2.0f * B;
-                    thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
-                }
-                if (q < nval && !okq) flag |= 1u << q;
+                E1[q] = INFINITY;
+                E2[q] = INFINITY;
+                best[q] = 0;
             }
-            // FP64 re-decision, one flagged point at a time: lane j takes candidate j,
-            // screens it with the FP32 value (every possible FP64 winner has E_fp32 <=
-            // thr) and evaluates a survivor in FP64 from the raw coordinates; the warp
-            // keeps the smallest value, the lowest center index on ties.
-            const double *g64 = p.g64_2 + (size_t)sel * p.k;
-            unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
-            while (lanes) {
-                const int Lf = __ffs(lanes) - 1;
-                lanes &= lanes - 1;
-                unsigned fl = __shfl_sync(0xffffffffu, flag, Lf);
-                while (fl) {
-                    const int q = __ffs(fl) - 1;
-                    fl &= fl - 1;
-                    float mx[3] = {0.f, 0.f, 0.f}, mt = 0.f;
+            // candidates from the stage (shared-memory broadcast), two at a time
+            auto consume = [&](const float4 &qg, int c) {
+                const float2 g2 = make_float2(qg.w, qg.w), nqx = make_float2(-qg.x, -qg.x),
+                             nqy = make_float2(-qg.y, -qg.y), nqz = make_float2(-qg.z, -qg.z);
 #pragma unroll
-                    for (int qq = 0; qq < 8; ++qq) {
-                        if (qq == q) {
-#pragma unroll
-                            for (int j = 0; j < D; ++j) mx[j] = (qq & 1) ? xp[j][qq >> 1].y : xp[j][qq >> 1].x;
-                            mt = thr[qq];
-                        }
+                for (int q = 0; q < 4; ++q) {
+                    const float2 dx = __fadd2_rn(xp[0][q], nqx);
+                    const float2 dy = __fadd2_rn(xp[1][q], nqy);
+                    float2 ss = __fmul2_rn(dx, dx);
+                    ss = __ffma2_rn(dy, dy, ss);
+                    if (D == 3) {
+                        const float2 dz = __fadd2_rn(xp[2][q], nqz);
+                        ss = __ffma2_rn(dz, dz, ss);
                     }
+                    const float2 E = __fmul2_rn(g2, ss);
+                    argmin_update<F64MODE || BOUNDS>(E.x, c, E1[2 * q], E2[2 * q], best[2 * q]);
+                    argmin_update<F64MODE || BOUNDS>(E.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
+                }
+            };
+            int jj = 0;
+            for (; jj + 1 < ncand; jj += 2) {
+                const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
+                const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
+                consume(qa, ca);
+                consume(qb, cb);
+            }
+            if (jj < ncand) {
+                const float4 qa = S.rec[2 + 2 * jj];
+                consume(qa, __float_as_int(S.rec[3 + 2 * jj].x));
+            }
+            unsigned flag = 0;
+            float Bl = 0.0f;
+            if (F64MODE) {
+                // error-bound constants; see the comment above
+                const float R = p.R;
+                const float sd = sqrtf((float)D);
+                const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
+                // coordinate term with the largest |x'| of the lane's points
+                float xn2 = 0.0f;
 #pragma unroll
-                    for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, mx[j], Lf);
-                    mt = __shfl_sync(0xffffffffu, mt, Lf);
-                    const long long ip = (long long)t * kTile + Lf * 8 + q;
-                    double bE = INFINITY;
-                    int bc = 0x7fffffff;
-                    if (lane < ncand) {
-                        const float4 qg = S.rec[2 + 2 * lane];
-                        const int c = __float_as_int(S.rec[3 + 2 * lane].x);
-                        const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
-                        const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
-                        const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
-                        if (E32 <= mt) {
-                            double s2 = 0.0;
+                for (int q = 0; q < 4; ++q) {
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                            for (int j = 0; j < D; ++j) {
-                                const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip]
-                                                               : (double)p.X32[(size_t)j * p.n_pad + ip];
-                                const double df = xj - p.C[c * D + j];
-                                s2 += df * df;
+                    for (int j = 0; j < D; ++j) acc = __ffma2_rn(xp[j][q], xp[j][q], acc);
+                    xn2 = fmaxf(xn2, fmaxf(acc.x, acc.y));
+                }
+                const float e0 = sd * kU * (R + 8.0f * __fsqrt_ru(__fmul_ru(xn2, 1.0f + 4.0f * kU)));
+                // B grows with E: one bound at the lane's largest finite runner-up certifies
+                // most points; a point it does not certify gets its own bound
+                float e2max = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (E2[q] < INFINITY) e2max = fmaxf(e2max, E2[q]);
+                Bl = cert_bound(e0, sg, gl, beta2, e2max);
+                float thr[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
+                    bool okq = single || (E2[q] - E1[q]) > 2.0f * Bl;
+                    thr[q] = INFINITY;
+                    if (!okq) {
+                        const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
+                        okq = (E2[q] - E1[q]) > 2.0f * B;
+                        thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
+                    }
+                    if (q < nval && !okq) flag |= 1u << q;
+                }
+                // FP64 re-decision, one flagged point at a time: lane j takes candidate j,
+                // screens it with the FP32 value (every possible FP64 winner has E_fp32 <=
+                // thr) and evaluates a survivor in FP64 from the raw coordinates; the warp
+                // keeps the smallest value, the lowest center index on ties.
+                const double *g64 = p.g64_2 + (size_t)sel * p.k;
+                unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
+                while (lanes) {
+                    const int Lf = __ffs(lanes) - 1;
+                    lanes &= lanes - 1;
+                    unsigned fl = __shfl_sync(0xffffffffu, flag, Lf);
+                    while (fl) {
+                        const int q = __ffs(fl) - 1;
+                        fl &= fl - 1;
+                        float mx[3] = {0.f, 0.f, 0.f}, mt = 0.f;
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            if (qq == q) {
+#pragma unroll
+                                for (int j = 0; j < D; ++j) mx[j] = (qq & 1) ? xp[j][qq >> 1].y : xp[j][qq >> 1].x;
+                                mt = thr[qq];
                             }
-                            bE = s2 * g64[c];
-                            bc = c;
                         }
-                    }
-                    for (int off = 16; off; off >>= 1) {
-                        const double oE = __shfl_xor_sync(0xffffffffu, bE, off);
-                        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
-                        if (oE < bE || (oE == bE && oc < bc)) {
-                            bE = oE;
-                            bc = oc;
-                        }
-                    }
-                    if (lane == Lf && bc != 0x7fffffff) {
 #pragma unroll
-                        for (int qq = 0; qq < 8; ++qq)
-                            if (qq == q) best[qq] = bc;
+                        for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, mx[j], Lf);
+                        mt = __shfl_sync(0xffffffffu, mt, Lf);
+                        const long long ip = (long long)t * kTile + Lf * 8 + q;
+                        double bE = INFINITY;
+                        int bc = 0x7fffffff;
+                        if (lane < ncand) {
+                            const float4 qg = S.rec[2 + 2 * lane];
+                            const int c = __float_as_int(S.rec[3 + 2 * lane].x);
+                            const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
+                            const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
+                            const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                            if (E32 <= mt) {
+                                double s2 = 0.0;
+#pragma unroll
+                                for (int j = 0; j < D; ++j) {
+                                    const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip]
+                                                                   : (double)p.X32[(size_t)j * p.n_pad + ip];
+                                    const double df = xj - p.C[c * D + j];
+                                    s2 += df * df;
+                                }
+                                bE = s2 * g64[c];
+                                bc = c;
+                            }
+                        }
+                        for (int off = 16; off; off >>= 1) {
+                            const double oE = __shfl_xor_sync(0xffffffffu, bE, off);
+                            const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                            if (oE < bE || (oE == bE && oc < bc)) {
+                                bE = oE;
+                                bc = oc;
+                            }
+                        }
+                        if (lane == Lf && bc != 0x7fffffff) {
+#pragma unroll
+                            for (int qq = 0; qq < 8; ++qq)
+                                if (qq == q) best[qq] = bc;
+                        }
                     }
                 }
+                nre += __popc(flag);
             }
-            nre += __popc(flag);
-        }
-        __syncwarp();  // every lane is done with stage b
-        refill(b);
-        // block ids
-        if (nval == 8) {
-            int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
-            dst[0] = make_int4(best[0], best[1], best[2], best[3]);
-            dst[1] = make_int4(best[4], best[5], best[6], best[7]);
-        } else {
+            if constexpr (BOUNDS) {  // each point's bound for the next passes of the phase
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < nval) p.A[i0 + q] = best[q];
+                for (int q = 0; q < 8; ++q) {
+                    if (q >= nval) continue;
+                    p.lq[i0 + q] = bound_lq<F64MODE>(E1[q], E2[q], Bl, lamT, (flag >> q) & 1u);
+                    p.t1[i0 + q] = (unsigned char)pp;
+                }
+            }
+            __syncwarp();  // every lane is done with stage b
+            refill(b);
+            if (nval == 8) {
+                int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+                dst[0] = make_int4(best[0], best[1], best[2], best[3]);
+                dst[1] = make_int4(best[4], best[5], best[6], best[7]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (q < nval) p.A[i0 + q] = best[q];
+            }
+        } else {
+            if constexpr (BOUNDS) {
+                int *blk = S.a;  // old block ids (bounds), then this pass's
+                unsigned char *alist = s_act[w];
+                // 1. the lane's points to evaluate: a point keeps its block when rho exceeds the
+                //    largest growth of any center's g since its last evaluation t1 over the smallest
+                //    (rho: the ratio of the other centers' smallest E to its own E then, stored as
+                //    lq = log2 rho rounded down; dm[t1] = log2 of a lower bound of that smallest
+                //    over that largest growth): then its own E stays below every other center's.
+                unsigned act = nval >= 8 ? 0xffu : ((1u << nval) - 1u);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nval) {
+                        const int pi = lane * 8 + q;
+                        const int t1q = min((int)S.t1[pi], pp);
+                        if (__fadd_rd(S.lq[pi], dm_s[t1q]) > 0.0f) act &= ~(1u << q);
+                    }
+                }
+                // 2. the warp's list of points to evaluate, in tile order
+                const unsigned cl = __popc(act);
+                unsigned pre = cl;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned y = __shfl_up_sync(0xffffffffu, pre, off);
+                    if (lane >= off) pre += y;
+                }
+                const int nact = (int)__shfl_sync(0xffffffffu, pre, 31);
+                {
+                    unsigned pos = pre - cl;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if ((act >> q) & 1u) alist[pos++] = (unsigned char)(lane * 8 + q);
+                }
+                __syncwarp();
+                nevl += (unsigned long long)nact;
+                // 3. the points of the list, two per lane and round (packed f32x2)
+                for (int r0 = 0; r0 < nact; r0 += 64) {
+                    const int a0 = r0 + lane, a1 = r0 + 32 + lane;
+                    const bool vq[2] = {a0 < nact, a1 < nact};
+                    const int pi[2] = {vq[0] ? (int)alist[a0] : 0, vq[1] ? (int)alist[a1] : 0};
+                    float2 xp[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) xp[j] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) xp[j] = make_float2(S.x[j][pi[0]] - o[j], S.x[j][pi[1]] - o[j]);
+                    float E1[2] = {INFINITY, INFINITY}, E2[2] = {INFINITY, INFINITY};
+                    int best[2] = {0, 0};
+                    auto consume = [&](const float4 &qg, int c) {
+                        const float2 g2 = make_float2(qg.w, qg.w);
+                        const float2 dx = __fadd2_rn(xp[0], make_float2(-qg.x, -qg.x));
+                        const float2 dy = __fadd2_rn(xp[1], make_float2(-qg.y, -qg.y));
+                        float2 ss = __fmul2_rn(dx, dx);
+                        ss = __ffma2_rn(dy, dy, ss);
+                        if (D == 3) {
+                            const float2 dz = __fadd2_rn(xp[2], make_float2(-qg.z, -qg.z));
+                            ss = __ffma2_rn(dz, dz, ss);
+                        }
+                        const float2 E = __fmul2_rn(g2, ss);
+                        argmin_update<true>(E.x, c, E1[0], E2[0], best[0]);
+                        argmin_update<true>(E.y, c, E1[1], E2[1], best[1]);
+                    };
+                    int jj = 0;
+                    for (; jj + 1 < ncand; jj += 2) {
+                        const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
+                        const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
+                        consume(qa, ca);
+                        consume(qb, cb);
+                    }
+                    if (jj < ncand) consume(S.rec[2 + 2 * jj], __float_as_int(S.rec[3 + 2 * jj].x));
+                    float Bq[2] = {0.0f, 0.0f};
+                    unsigned flag = 0;
+                    if (F64MODE) {
+                        float e2max = 0.0f;
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+                            if (E2[q] < INFINITY) e2max = fmaxf(e2max, E2[q]);
+                        const float Bl = cert_bound(e0, sg, gl, beta2, e2max);
+                        float thr[2];
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const bool single = E2[q] == INFINITY && E1[q] < INFINITY;
+                            bool okq = single || (E2[q] - E1[q]) > 2.0f * Bl;
+                            Bq[q] = Bl;
+                            thr[q] = INFINITY;
+                            if (!okq) {
+                                const float B = cert_bound(e0, sg, gl, beta2, E2[q]);
+                                okq = (E2[q] - E1[q]) > 2.0f * B;
+                                thr[q] = E1[q] + 2.0f * B;  // every possible FP64 winner has E_fp32 <= thr
+                                Bq[q] = B;
+                            }
+                            if (vq[q] && !okq) flag |= 1u << q;
+                        }
+                        // FP64 re-decision, one flagged point at a time: lane j takes candidate j,
+                        // screens it with the FP32 value (every possible FP64 winner has E_fp32 <=
+                        // thr) and evaluates a survivor in FP64 from the raw coordinates; the warp
+                        // keeps the smallest value, the lowest center index on ties.
+                        const double *g64 = p.g64_2 + (size_t)sel * p.k;
+                        unsigned lanes = __ballot_sync(0xffffffffu, flag != 0u);
+                        while (lanes) {
+                            const int Lf = __ffs(lanes) - 1;
+                            lanes &= lanes - 1;
+                            unsigned fl = __shfl_sync(0xffffffffu, flag, Lf);
+                            while (fl) {
+                                const int q = __ffs(fl) - 1;
+                                fl &= fl - 1;
+                                float mx[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                                for (int j = 0; j < D; ++j) mx[j] = __shfl_sync(0xffffffffu, q ? xp[j].y : xp[j].x, Lf);
+                                const float mt = __shfl_sync(0xffffffffu, q ? thr[1] : thr[0], Lf);
+                                const int pq = __shfl_sync(0xffffffffu, q ? pi[1] : pi[0], Lf);
+                                const long long ip = t0 + pq;
+                                double bE = INFINITY;
+                                int bc = 0x7fffffff;
+                                if (lane < ncand) {
+                                    const float4 qg = S.rec[2 + 2 * lane];
+                                    const int c = __float_as_int(S.rec[3 + 2 * lane].x);
+                                    const float d0 = mx[0] - qg.x, d1 = mx[1] - qg.y;
+                                    const float d2 = D == 3 ? mx[2] - qg.z : 0.0f;
+                                    const float E32 = qg.w * fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+                                    if (E32 <= mt) {
+                                        double s2 = 0.0;
+#pragma unroll
+                                        for (int j = 0; j < D; ++j) {
+                                            const double xj = p.dtype == 1 ? p.X64[(size_t)j * p.n_pad + ip]
+                                                                           : (double)p.X32[(size_t)j * p.n_pad + ip];
+                                            const double df = xj - p.C[c * D + j];
+                                            s2 += df * df;
+                                        }
+                                        bE = s2 * g64[c];
+                                        bc = c;
+                                    }
+                                }
+                                for (int off = 16; off; off >>= 1) {
+                                    const double oE = __shfl_xor_sync(0xffffffffu, bE, off);
+                                    const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+                                    if (oE < bE || (oE == bE && oc < bc)) {
+                                        bE = oE;
+                                        bc = oc;
+                                    }
+                                }
+                                if (lane == Lf && bc != 0x7fffffff) {
+                                    if (q)
+                                        best[1] = bc;
+                                    else
+                                        best[0] = bc;
+                                }
+                            }
+                        }
+                        nre += __popc(flag);
+                    }
+                    // block ids, and each point's bound for the next passes: rho = (lower bound of
+                    // every other center's E) / (upper bound of E_own), rounded down; a re-decided
+                    // point gets 0 (it is evaluated again next pass)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        if (!vq[q]) continue;
+                        blk[pi[q]] = best[q];
+                        p.A[t0 + pi[q]] = best[q];
+                        p.lq[t0 + pi[q]] = bound_lq<F64MODE>(E1[q], E2[q], Bq[q], lamT, (flag >> q) & 1u);
+                        p.t1[t0 + pi[q]] = (unsigned char)pp;
+                    }
+                }
+                __syncwarp();  // every lane is done with the list and has written its block ids
+                // block ids of the lane's points
+#pragma unroll
+                for (int q = 0; q < 8; ++q) best[q] = q < nval ? blk[lane * 8 + q] : 0;
+                fence_proxy_async();  // the stage's block ids were written: order before its refill
+                __syncwarp();         // every lane is done with stage b
+                refill(b);
+                    }
         }
         tile_histogram(p, i0, nval, best);
     }
@@ -1279,6 +1570,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
         if (lane == 0 && nre) atomicAdd(&p.ctl->rechecks, nre);
     }
+    if (lane == 0 && nevl) atomicAdd(&p.ctl->evaluated, nevl);  // nevl is the same in every lane
 }
 
 // ------------------------------------------------------------------------------
@@ -1316,6 +1608,12 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
     const int sel = ctl->isel, nsel = sel ^ 1;
     const int gshift = ctl->gshift;
     const double target = ctl->target;
+    // per-point bounds: this pass's index in the phase and the next one's (a wrap starts
+    // a fresh pass, with the new g as its reference)
+    const bool bnd = p.bounds && mode != 2;
+    const int pp = ctl->phase_pass;
+    const bool wrap = pp + 1 >= kSkipHist;
+    float lr = INFINITY, lrh = -INFINITY;  // log2 of this center's g ratio, rounded down / up
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     double S = 0.0, gnew = 0.0;
     float4 hc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1339,6 +1637,19 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
             gnew = 1.0 / (In * In);
             p.I2[(size_t)nsel * p.k + c] = In;
             p.g64_2[(size_t)nsel * p.k + c] = gnew;
+            if (bnd) {
+                const float lgn = lg_of(gnew);
+                p.lg[(size_t)(wrap ? 0 : pp + 1) * p.k + c] = lgn;
+                if (!wrap) {
+                    const float lgo = p.lg[(size_t)pp * p.k + c];
+                    lr = __fsub_rd(lgn, lgo);
+                    lrh = __fsub_ru(lgn, lgo);
+                    if (lr != lr || lrh != lrh) {  // NaN: no bound
+                        lr = -INFINITY;
+                        lrh = INFINITY;
+                    }
+                }
+            }
             hc = p.cdata2[(size_t)sel * 2 * p.k + 2 * c];
             hc.w = scaled_g32(gnew, gshift);
             p.cdata2[(size_t)nsel * 2 * p.k + 2 * c] = hc;
@@ -1353,12 +1664,21 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
     for (int off = 16; off; off >>= 1) {
         mS = fmax(mS, __shfl_xor_sync(0xffffffffu, mS, off));
         mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, off));
+        lr = fminf(lr, __shfl_xor_sync(0xffffffffu, lr, off));
+        lrh = fmaxf(lrh, __shfl_xor_sync(0xffffffffu, lrh, off));
     }
     if (threadIdx.x == 0) {
         atomicMax(&ctl->maxS_key, okey_f64(mS));
         if (mode != 2) atomicMax(&ctl->maxg_key, okey_f64(mg));
+        if (bnd && !wrap) {
+            atomicMin(&ctl->min_lr_key, okey_f32(lr));
+            atomicMax(&ctl->max_lr_key, okey_f32(lrh));
+        }
     }
-    if (last_block(ctl) && threadIdx.x == 0) {
+    const bool last = last_block(ctl);
+    __shared__ int s_newpp;
+    if (last && threadIdx.x == 0) s_newpp = -1;
+    if (last && threadIdx.x == 0) {
         double maxS = okey_to_f64(atomicOr(&ctl->maxS_key, 0ull));
         double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
         ctl->maxS_key = 0ull;
@@ -1379,6 +1699,19 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
             ctl->isel = nsel;
             ctl->gshift = exponent_above(maxg);
         }
+        if (bnd) {
+            // the next pass continues the phase: the running sum of the passes' (smallest -
+            // largest) log2 g ratio, lowered by the margin for the rounding of the logs
+            const float m = okey_to_f32(ctl->min_lr_key), M = okey_to_f32(ctl->max_lr_key);
+            ctl->min_lr_key = 0xffffffffu;
+            ctl->max_lr_key = 0u;
+            if (!bal) {
+                const int np = wrap ? 0 : pp + 1;
+                p.cumm[np] = wrap ? 0.0 : p.cumm[pp] + ((double)m - (double)M - 2.0 * (double)kLgMargin);
+                ctl->phase_pass = np;
+                s_newpp = np;
+            }
+        }
         int cont;
         if (mode == 0)
             cont = !bal && ctl->pass_in_phase < p.max_balance_iter;
@@ -1390,6 +1723,16 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         else
             ctl->cont_final = cont;
         if (h) cudaGraphSetConditional(h, (unsigned)cont);
+    }
+    if (last) {
+        // dm[t1] = cumm[t] - cumm[t1] rounded down, for every earlier pass t1 of the phase
+        __syncwarp();
+        const int np = s_newpp;
+        if (np >= 0) {
+            const double ct = __ldcg(&p.cumm[np]);
+            for (int t1 = threadIdx.x; t1 <= np; t1 += blockDim.x)
+                p.dm[t1] = __double2float_rd(ct - __ldcg(&p.cumm[t1]));
+        }
     }
 }
 
@@ -1587,6 +1930,13 @@ __global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
         ctl->converged = conv;
         int move = (mode == 3 || (!conv && ctl->iter < p.max_iter)) && ctl->status == kOk;
         ctl->cont_move = move;
+        if (move && p.bounds) {  // new centers: the next pass is a fresh one
+            ctl->phase_pass = 0;
+            ctl->min_lr_key = 0xffffffffu;
+            ctl->max_lr_key = 0u;
+            p.cumm[0] = 0.0;
+            p.dm[0] = 0.0f;
+        }
         ctl->pass_in_phase = 0;
         ctl->cont_balance = 1;
         if (h_move) cudaGraphSetConditional(h_move, mode == 3 ? 0u : (unsigned)move);
@@ -1623,6 +1973,7 @@ __global__ void __launch_bounds__(kKThreads) finalize_b_kernel(Prob p) {
         }
         double g = 1.0 / (I * I);
         p.g64_2[(size_t)sel * p.k + c] = g;
+        if (p.bounds) p.lg[c] = lg_of(g);
         g32 = scaled_g32(g, ctl->gshift);
         frame_center(p, c, hi, lo);
         for (int b = 0; b < 2; ++b) {
@@ -1669,9 +2020,13 @@ static dim3 filter_big_grid(const Prob &p) {
     const long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * 8;
     return dim3((unsigned)(need < cap ? need : cap));
 }
-static void *assign_fn(int d, int f64) {
-    if (d == 2) return f64 ? (void *)assign_kernel<2, true> : (void *)assign_kernel<2, false>;
-    return f64 ? (void *)assign_kernel<3, true> : (void *)assign_kernel<3, false>;
+static void *assign_fn(const Prob &p) {
+    if (p.bounds) {
+        if (p.d == 2) return p.assign_f64 ? (void *)assign_kernel<2, true, true> : (void *)assign_kernel<2, false, true>;
+        return p.assign_f64 ? (void *)assign_kernel<3, true, true> : (void *)assign_kernel<3, false, true>;
+    }
+    if (p.d == 2) return p.assign_f64 ? (void *)assign_kernel<2, true, false> : (void *)assign_kernel<2, false, false>;
+    return p.assign_f64 ? (void *)assign_kernel<3, true, false> : (void *)assign_kernel<3, false, false>;
 }
 static void *centroid_fn(int d, int dtype) {
     if (dtype == 1) return d == 2 ? (void *)centroid_kernel<double, 2> : (void *)centroid_kernel<double, 3>;
@@ -1711,18 +2066,26 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
 }
 static int assign_grid(const Prob &p) {
     int need = (p.ntiles + kAWarps - 1) / kAWarps;
-    int cap = (p.nsm > 0 ? p.nsm : 152) * (p.assign_f64 ? kAMinBlocks64 : kAMinBlocks);
+    // resident CTAs per SM: registers (FP64 mode) or the stages' shared memory (3-D)
+    const int per_sm = p.assign_f64 ? kAMinBlocks64 : ((p.bounds && p.d == 3) ? 4 : kAMinBlocks);
+    int cap = (p.nsm > 0 ? p.nsm : 152) * per_sm;
     return need < cap ? need : cap;
 }
-static cudaError_t prepare_assign(void *fn) {
-    return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+static size_t assign_smem_of(const Prob &p) {
+    if (p.bounds) return p.d == 2 ? assign_smem<2, true>() : assign_smem<3, true>();
+    return p.d == 2 ? assign_smem<2, false>() : assign_smem<3, false>();
+}
+static cudaError_t prepare_assign(void *fn, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 cudaError_t launch_assign(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    void *fn = assign_fn(p.d, p.assign_f64);
-    cudaError_t e = prepare_assign(fn);
+    void *fn = assign_fn(p);
+    cudaError_t e = prepare_assign(fn, assign_smem_of(p));
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernel(fn, dim3(assign_grid(p)), dim3(kAWarps * 32), args1, 0, s);
+    return cudaLaunchKernel(fn, dim3(assign_grid(p)), dim3(kAWarps * 32), args1, assign_smem_of(p), s);
 }
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s) {
     balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0);
@@ -1831,7 +2194,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
     void *a_fin[] = {&p, &mode0, &h_move, &h_bal};
     void *a_fb[] = {&p, &h_fin};
     const dim3 kg(kgrid(p)), kb(kKThreads), tg(tile_warp_grid(p)), tb(kAssignWarps * 32);
-    e = prepare_assign(assign_fn(p.d, p.assign_f64));
+    e = prepare_assign(assign_fn(p), assign_smem_of(p));
     dim3 fgrid;
     size_t fsmem = 0;
     if (e == cudaSuccess) e = filter_config(p, fgrid, fsmem);
@@ -1850,7 +2213,8 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
             NodeAdder bl{body_bal};
             bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
             bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
-            bl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
+            bl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
+                      assign_smem_of(p));
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
             if (p.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
             if (bl.err != cudaSuccess) mv.err = bl.err;
@@ -1867,7 +2231,8 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
         NodeAdder fl{body_fin};
         fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
-        fl.kernel(assign_fn(p.d, p.assign_f64), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p);
+        fl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
+                  assign_smem_of(p));
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
         if (p.nsgroups > 0) fl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
         if (fl.err != cudaSuccess) top.err = fl.err;
@@ -1909,7 +2274,8 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
         NodeAdder bl{body_bal};
         bl.kernel(filter_fn(ps.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         bl.kernel(filter_big_fn(ps.d), filter_big_grid(ps), dim3(kFilterThreads), a_p);
-        bl.kernel(assign_fn(ps.d, ps.assign_f64), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p);
+        bl.kernel(assign_fn(ps), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p,
+                  assign_smem_of(ps));
         bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
         if (ps.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
         if (bl.err != cudaSuccess) top.err = bl.err;
@@ -1927,7 +2293,7 @@ cudaError_t build_sampled_graph(const Prob &p, const Prob *ps, const SampleSel *
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
-    e = prepare_assign(assign_fn(p.d, p.assign_f64));
+    e = prepare_assign(assign_fn(p), assign_smem_of(p));
     NodeAdder top{g};
     for (int r = 0; r < R && e == cudaSuccess; ++r) e = add_sample_round(top, ps[r], sel[r], p.ctl);
     if (e == cudaSuccess) e = add_loop_chain(g, p, top.last);

@@ -118,3 +118,13 @@ def test_batched_workload_64_instances(gk):
         idx = rng.choice(len(x), min(len(x), 2000), replace=False)
         A_ref, _, _ = oracle.assign(x[idx].astype(np.float64), C, I, threads=THREADS)
         assert (A[idx] != A_ref).mean() <= 1e-3
+
+
+def test_batched_with_bounds_equals_without(gk):
+    data = _problems(MIXED)
+    with_b, st1 = _run(gk, data, bounds=1)
+    without, st0 = _run(gk, data, bounds=0)
+    assert st1 == st0
+    for (A1, C1, I1, r1), (A0, C0, I0, r0) in zip(with_b, without):
+        assert np.array_equal(A1, A0) and np.array_equal(C1, C0) and np.array_equal(I1, I0)
+        assert r1["balance_passes"] == r0["balance_passes"]

@@ -450,3 +450,44 @@ def test_full_size_radial2d_1e8_k4096_fp32_form(gk):
 @pytest.mark.slow
 def test_full_size_spots2d_1e9_k16384_fp32_form(gk):
     _full_size_fp32_form(gk, "spots2d_1e9_k16384_f32", 50_000)
+
+
+# ----------------------------------------------------------------------------------------
+# Per-point bounds (gk_options.bounds): the same results as evaluating every point
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,d,dtype,n,k,assign,weighted", [
+    ("gmm", 3, "f64", 60_000, 48, "f64", False),
+    ("radial", 2, "f64", 50_000, 37, "f64", True),
+    ("gmm", 3, "f32", 80_000, 64, "f32", False),
+    ("spots", 2, "f32", 120_000, 300, "f32", True),
+    ("uniform", 2, "f64", 30_000, 2500, "f64", False),
+])
+def test_bounds_give_identical_results(gk, shape, d, dtype, n, k, assign, weighted):
+    x = _points(shape, n, d, 59, dtype)
+    w = synth.uniform_weights(n, 59, dtype=x.dtype) if weighted else None
+    out = []
+    for bounds in (1, 0):
+        o = gk.default_options(assign_dtype=assign, bounds=bounds)
+        block, C, I, res = gk.partition(_dev(x), k, 0.03, weights=None if w is None else _dev(w),
+                                        options=o)
+        out.append((_np(block), _np(C), _np(I), res))
+    (b1, C1, I1, r1), (b0, C0, I0, r0) = out
+    assert np.array_equal(b1, b0)
+    assert np.array_equal(C1, C0) and np.array_equal(I1, I0)
+    assert r1["balance_passes"] == r0["balance_passes"] and r1["iterations"] == r0["iterations"]
+    assert r0["evaluated_points"] == n * r0["balance_passes"]
+    assert r1["evaluated_points"] < r0["evaluated_points"]
+
+
+def test_bounds_over_many_passes_wrap_to_fresh_passes(gk):
+    """A phase longer than the bound history (64 passes): every 64th pass evaluates all
+    points again; the result stays that of evaluating every point."""
+    x = _points("gmm", 40_000, 3, 61, "f64")
+    out = []
+    for bounds in (1, 0):
+        o = gk.default_options(bounds=bounds, max_iter=2, max_balance_iter=150,
+                               final_balance_iter=150)
+        block, C, I, res = gk.partition(_dev(x), 37, 0.0, options=o)
+        out.append((_np(block), _np(C), _np(I), res))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+    assert out[0][3]["balance_passes"] == out[1][3]["balance_passes"] > 64

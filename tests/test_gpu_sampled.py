@@ -208,3 +208,16 @@ def test_full_size_sampled_gmm3d_1e7_k1024(gk):
     Cn, delta, beta = gk.move_centers(xt, _dev(A), _dev(C))
     Cr, dr, br = oracle.move_centers(x, None, A, C)
     assert _rel_center_err(_np(Cn), Cr, x) < 1e-10
+
+
+def test_sampled_with_bounds_is_identical(gk):
+    x = synth.make_points("gmm", 80_000, 3, 103, "f64")
+    order = synth.random_order(len(x), 103)
+    out = []
+    for bounds in (1, 0):
+        block, C, I, res = gk.partition_sampled(_dev(x), 40, 0.03, _dev(order), 2000,
+                                                options=gk.default_options(bounds=bounds))
+        out.append((_np(block), _np(C), _np(I), res))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    assert out[0][3]["balance_passes"] == out[1][3]["balance_passes"]
