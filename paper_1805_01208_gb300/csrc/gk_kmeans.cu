@@ -513,14 +513,21 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = L + __popc(bal & lt);
         if (keep && pos < kWarpList) glist_out[pos] = c;
-        if (keep && pos < kLaneMax) {
-            list[pos] = c;
-            lcd[2 * pos] = __ldg(&cd[2 * c]);
-            lcd[2 * pos + 1] = __ldg(&cd[2 * c + 1]);
-        }
+        if (keep && pos < kLaneMax) list[pos] = c;
         L += __popc(bal);
     }
     __syncwarp();
+    // the center data of the short list, copied after the pass so that the loads of all
+    // its entries are in flight together
+    if (L <= kLaneMax) {
+        for (int i = lane; i < L; i += 32) {
+            const int c = list[i];
+            const float4 ch = __ldg(&cd[2 * c]), cl = __ldg(&cd[2 * c + 1]);
+            lcd[2 * i] = ch;
+            lcd[2 * i + 1] = cl;
+        }
+        __syncwarp();
+    }
     for (int off = 16; off; off >>= 1) lam = fminf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
     lamS = lam;
     return L;
