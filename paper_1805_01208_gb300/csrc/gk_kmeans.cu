@@ -759,6 +759,19 @@ __device__ __forceinline__ void argmin_update(float E, int c, float &E1, float &
     best = lt ? c : best;
     E1 = lt ? E : E1;
 }
+// The same for two candidates ca < cb at once: their smaller value and its index (ca on
+// ties) do not depend on the running state, which shortens its dependency chain; the
+// runner-up is the second smallest of {E1, E2, Ea, Eb}.
+template <bool F64MODE>
+__device__ __forceinline__ void argmin_update2(float Ea, int ca, float Eb, int cb, float &E1, float &E2,
+                                               int &best) {
+    const float lo = fminf(Ea, Eb);
+    const int cab = lo == Ea ? ca : cb;
+    if (F64MODE) E2 = fminf(fminf(fmaxf(E1, lo), E2), fmaxf(Ea, Eb));
+    const bool lt = lo < E1;
+    best = lt ? cab : best;
+    E1 = lt ? lo : E1;
+}
 
 // Error-bound terms of the FP64-mode certification (see the comment above): the
 // bound on |E_fp32 - E_exact| for a point whose coordinate term is e0, against
@@ -1269,12 +1282,29 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
                     argmin_update<F64MODE || BOUNDS>(E.y, c, E1[2 * q + 1], E2[2 * q + 1], best[2 * q + 1]);
                 }
             };
+            // two candidates at a time (ascending center ids)
+            auto dist2 = [&](const float4 &qg, int q) -> float2 {
+                const float2 dx = __fadd2_rn(xp[0][q], make_float2(-qg.x, -qg.x));
+                const float2 dy = __fadd2_rn(xp[1][q], make_float2(-qg.y, -qg.y));
+                float2 ss = __fmul2_rn(dx, dx);
+                ss = __ffma2_rn(dy, dy, ss);
+                if (D == 3) {
+                    const float2 dz = __fadd2_rn(xp[2][q], make_float2(-qg.z, -qg.z));
+                    ss = __ffma2_rn(dz, dz, ss);
+                }
+                return __fmul2_rn(make_float2(qg.w, qg.w), ss);
+            };
             int jj = 0;
             for (; jj + 1 < ncand; jj += 2) {
                 const float4 qa = S.rec[2 + 2 * jj], qb = S.rec[4 + 2 * jj];
                 const int ca = __float_as_int(S.rec[3 + 2 * jj].x), cb = __float_as_int(S.rec[5 + 2 * jj].x);
-                consume(qa, ca);
-                consume(qb, cb);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 Ea = dist2(qa, q), Eb = dist2(qb, q);
+                    argmin_update2<F64MODE || BOUNDS>(Ea.x, ca, Eb.x, cb, E1[2 * q], E2[2 * q], best[2 * q]);
+                    argmin_update2<F64MODE || BOUNDS>(Ea.y, ca, Eb.y, cb, E1[2 * q + 1], E2[2 * q + 1],
+                                                      best[2 * q + 1]);
+                }
             }
             if (jj < ncand) {
                 const float4 qa = S.rec[2 + 2 * jj];
