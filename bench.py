@@ -296,8 +296,9 @@ def main():
     # algorithmic bytes of one balance pass: every point's coordinates (and weight) read
     # once; writing the block ids is not counted (only the last pass of a loop needs it)
     bytes_per_launch = n * (d * es + sw)
-    # what this assignment kernel itself streams: FP32 frame coordinates, block ids
-    kernel_bytes = n * (d * 4 + 4 + sw)
+    # what this assignment kernel itself streams: FP32 frame coordinates, block ids (16
+    # bits when k <= 65535)
+    kernel_bytes = n * (d * 4 + (2 if k <= 65535 else 4) + sw)
     peak, peak_kind = _peaks()
     achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -117,6 +117,7 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.X64 = p.dtype == 1 ? (double *)take((size_t)d * np * 8) : nullptr;
     p.Ws = p.weighted ? (void *)take((size_t)np * es) : nullptr;
     p.A = (int *)take((size_t)np * 4);
+    p.A16 = (unsigned short *)take((size_t)np * 2);
     p.tiles = (float4 *)take((size_t)p.ntiles * 32);
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
@@ -164,6 +165,7 @@ struct SampleBufs {
     double *X64 = nullptr;
     void *Ws = nullptr;
     int *A = nullptr;
+    unsigned short *A16 = nullptr;
     float4 *tiles = nullptr, *supers = nullptr, *trec = nullptr;
     int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
     float *prho = nullptr;            // per-point bounds of the sample
@@ -191,6 +193,7 @@ size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order
     sb.X64 = p.dtype == 1 ? (double *)take((size_t)p.d * np * 8) : nullptr;
     sb.Ws = p.weighted ? (void *)take((size_t)np * es) : nullptr;
     sb.A = (int *)take((size_t)np * 4);
+    sb.A16 = (unsigned short *)take((size_t)np * 2);
     sb.tiles = (float4 *)take((size_t)nt * 32);
     sb.supers = (float4 *)take((size_t)ns * 32);
     sb.trec = (float4 *)take((size_t)nt * kRecF4 * 16);
@@ -551,6 +554,7 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.X64 = sb.X64;
     ps.Ws = sb.Ws;
     ps.A = sb.A;
+    ps.A16 = sb.A16;
     ps.tiles = sb.tiles;
     ps.supers = sb.supers;
     ps.trec = sb.trec;
@@ -681,6 +685,7 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     p.final_balance_iter = o.final_balance_iter;
     p.erosion = o.erosion;
     p.bounds = o.bounds;
+    p.a16 = k <= 65535 && !o.bounds;
     if ((st = cl.geometry(o.delta_threshold)) != GK_OK) return st;
     GK_CUDA(cudaMemcpyAsync(&p.ctl->thr, &cl.thr, sizeof(double), cudaMemcpyHostToDevice, cl.s));
     const unsigned *perm = nullptr;
@@ -792,6 +797,7 @@ gk_status partition_batched(const gk_instance *inst, int32_t count, const gk_opt
         p.final_balance_iter = o.final_balance_iter;
         p.erosion = o.erosion;
         p.bounds = o.bounds;
+        p.a16 = p.k <= 65535 && !o.bounds;
         if ((st = cl[i].upload_state(&hc[i])) != GK_OK) return st;
         GK_CUDA(launch_bbox(p, s));
     }

@@ -605,13 +605,13 @@ __global__ void super_box_kernel(Prob p) {
     p.supers[2 * s + 1] = make_float4(h[0], h[1], h[2], 0.0f);
 }
 
-__global__ void scatter_kernel(const int *A_sorted, const unsigned *perm, long long n, int *out,
-                               Ctl *ctl) {
+__global__ void scatter_kernel(const int *A_sorted, const unsigned short *A16_sorted, const unsigned *perm,
+                               long long n, int *out, Ctl *ctl) {
     count_launch(ctl);
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         long long j = perm ? (long long)perm[i] : i;
-        if (j < n) out[j] = A_sorted[i];
+        if (j < n) out[j] = A16_sorted ? (int)A16_sorted[i] : A_sorted[i];
     }
 }
 
@@ -888,7 +888,7 @@ cudaError_t launch_centers(const Prob &p, cudaStream_t s) {
 }
 
 cudaError_t launch_scatter(const Prob &p, const unsigned *perm, int *out, cudaStream_t s) {
-    scatter_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(p.A, perm, p.n, out, p.ctl);
+    scatter_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(p.A, p.a16 ? p.A16 : nullptr, perm, p.n, out, p.ctl);
     return cudaGetLastError();
 }
 

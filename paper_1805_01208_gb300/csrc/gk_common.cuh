@@ -6,7 +6,8 @@
 //          bounding box; FP32 inputs: the raw coordinates).  Padding entries are 0.
 //   X64    d planes of n_pad FP64: curve-sorted raw coordinates (FP64 inputs only).
 //   Ws     n_pad sorted weights in the input dtype (weighted problems only).
-//   A      n_pad int32 block ids in sorted order.
+//   A      n_pad int32 block ids in sorted order (A16: the same as 16 bits, which the
+//          k-means loop uses instead when k <= 65535: 2 B per point written per pass).
 //   tiles  2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -};
 //   supers the same per supertile of kSuperTiles tiles.
 //   per tile record (written by the filter every pass, kRecF4 float4): header
@@ -133,6 +134,8 @@ struct Prob {
     double *X64;
     void *Ws;
     int *A;
+    unsigned short *A16;        // the block ids as 16 bits (a16: k <= 65535, no bounds)
+    int a16;
     float4 *tiles, *supers;
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;

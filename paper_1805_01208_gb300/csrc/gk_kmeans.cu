@@ -783,6 +783,32 @@ __device__ __forceinline__ float cert_bound(float e0, float sgl, float glv, floa
     return 2.0f * (beta0 + beta1 * sqrtf(Estar) + beta2 * Estar);
 }
 
+// The block ids of a lane's 8 points (16 bits when p.a16).
+__device__ __forceinline__ void store_blocks(const Prob &p, long long i0, int nval, const int best[8]) {
+    if (p.a16) {
+        if (nval == 8) {
+            uint4 v;
+            v.x = (unsigned)best[0] | ((unsigned)best[1] << 16);
+            v.y = (unsigned)best[2] | ((unsigned)best[3] << 16);
+            v.z = (unsigned)best[4] | ((unsigned)best[5] << 16);
+            v.w = (unsigned)best[6] | ((unsigned)best[7] << 16);
+            *reinterpret_cast<uint4 *>(p.A16 + i0) = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < nval) p.A16[i0 + q] = (unsigned short)best[q];
+        }
+    } else if (nval == 8) {
+        int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+        dst[0] = make_int4(best[0], best[1], best[2], best[3]);
+        dst[1] = make_int4(best[4], best[5], best[6], best[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nval) p.A[i0 + q] = best[q];
+    }
+}
+
 // Block weights of one tile's assignment: runs inside the lane, then a segmented
 // reduction over lanes (unit weights: 64-bit counts; weights: 128-bit fixed point).
 __device__ __forceinline__ void tile_histogram(const Prob &p, long long i0, int nval, const int best[8]) {
@@ -1053,15 +1079,7 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
             }
         }
         if (lane == 0) *nevl += (unsigned long long)(p.n - (long long)t * kTile < kTile ? p.n - (long long)t * kTile : kTile);
-        if (nval == 8) {
-            int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
-            dst[0] = make_int4(best[0], best[1], best[2], best[3]);
-            dst[1] = make_int4(best[4], best[5], best[6], best[7]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < nval) p.A[i0 + q] = best[q];
-        }
+        store_blocks(p, i0, nval, best);
         tile_histogram(p, i0, nval, best);
     }
 }
@@ -1421,15 +1439,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             }
             __syncwarp();  // every lane is done with stage b
             refill(b);
-            if (nval == 8) {
-                int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
-                dst[0] = make_int4(best[0], best[1], best[2], best[3]);
-                dst[1] = make_int4(best[4], best[5], best[6], best[7]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    if (q < nval) p.A[i0 + q] = best[q];
-            }
+            store_blocks(p, i0, nval, best);
         } else {
             if constexpr (BOUNDS) {
                 int *blk = S.a;  // old block ids (bounds), then this pass's
@@ -1812,7 +1822,7 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     }
     int bad = 0;
     for (int q = 0; q < nval; ++q) {
-        int b = p.A[i0 + q];
+        int b = p.a16 ? (int)p.A16[i0 + q] : p.A[i0 + q];
         if ((unsigned)b >= (unsigned)p.k) {
             bad = 1;
             continue;
