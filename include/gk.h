@@ -31,6 +31,7 @@
 #ifndef GK_H
 #define GK_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -294,6 +295,20 @@ gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64
 
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);
+
+/*
+ * Caller-supplied device memory for the library's workspace (for instance a framework's
+ * caching allocator).  alloc(bytes, ctx) returns device memory of the current device,
+ * 256-byte aligned (anything else counts as a failed allocation: GK_ERR_OOM), or NULL;
+ * free(ptr, bytes, ctx) takes back a block alloc returned.  The library synchronises the
+ * device before it calls free.  Passing NULL for both restores cudaMalloc / cudaFree;
+ * passing exactly one NULL gives GK_ERR_INVALID_ARG.  The current workspace is released
+ * first, to whoever provided it.  The pinned host control block and the scratch of
+ * gk_move_centers_noalloc do not come from this allocator.
+ */
+typedef void *(*gk_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*gk_free_fn)(void *ptr, size_t bytes, void *ctx);
+gk_status gk_set_allocator(gk_alloc_fn alloc, gk_free_fn free_fn, void *ctx);
 
 /* Largest k accepted by gk_move_centers_noalloc. */
 #define GK_NOALLOC_MAX_K 4096

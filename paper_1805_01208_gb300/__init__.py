@@ -116,6 +116,10 @@ class Quality(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_alloc_refs: dict = {}  # the registered callbacks, kept alive while the library may call them
+
 _lib = None
 
 
@@ -149,6 +153,8 @@ def lib():
         L.gk_partition_batched.argtypes = [P, i32, P, P, P]
         L.gk_partition_batched.restype = i32
         L.gk_release.argtypes = []
+        L.gk_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.gk_set_allocator.restype = i32
         _lib = L
     return _lib
 
@@ -380,6 +386,48 @@ def partition_quality(row_ptr, col, block, k: int, stream=None):
                                     _ptr(comm), ctypes.byref(q), _stream(block, stream))
     _check(st, "gk_partition_quality")
     return q.as_dict(), ext, comm
+
+
+def set_allocator(alloc=None, free=None):
+    """Device memory for the library's workspace from the caller: alloc(nbytes) returns a
+    device pointer (int, 256-byte aligned; 0 on failure), free(ptr, nbytes) takes it back.
+    set_allocator() returns to cudaMalloc.  The current workspace is released first."""
+    L = lib()
+    if alloc is None and free is None:
+        st = L.gk_set_allocator(None, None, None)
+        _alloc_refs.clear()
+        _check(st, "gk_set_allocator")
+        return
+    if alloc is None or free is None:
+        raise ValueError("give both alloc and free, or neither")
+    a = _ALLOC_FN(lambda nbytes, ctx: alloc(int(nbytes)) or None)
+    f = _FREE_FN(lambda ptr, nbytes, ctx: free(int(ptr), int(nbytes)))
+    st = L.gk_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None)
+    _check(st, "gk_set_allocator")
+    _alloc_refs.clear()
+    _alloc_refs.update(alloc=a, free=f)
+
+
+def use_torch_allocator():
+    """Route the workspace through PyTorch's caching allocator (current device).  Returns
+    the dict of live blocks (device pointer -> tensor), for inspection."""
+    import torch
+    blocks: dict = {}
+
+    def alloc(nbytes):
+        try:
+            t = torch.empty(nbytes + 255, dtype=torch.uint8, device="cuda")
+        except RuntimeError:
+            return 0
+        ptr = (t.data_ptr() + 255) & ~255
+        blocks[ptr] = t
+        return ptr
+
+    def free(ptr, nbytes):
+        blocks.pop(ptr, None)
+
+    set_allocator(alloc, free)
+    return blocks
 
 
 def partition_batched(problems, options: Options | None = None, stream=None):

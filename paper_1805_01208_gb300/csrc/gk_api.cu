@@ -42,6 +42,43 @@ struct Workspace {
 };
 Workspace g_ws;
 
+// Where the workspace comes from: cudaMalloc, or the caller's allocator
+// (gk_set_allocator).  The memory is returned to whoever provided it.
+struct Allocator {
+    gk_alloc_fn alloc = nullptr;
+    gk_free_fn free = nullptr;
+    void *ctx = nullptr;
+};
+Allocator g_alloc;
+
+bool dev_alloc(char **ptr, size_t bytes) {
+    if (g_alloc.alloc) {
+        void *q = g_alloc.alloc(bytes, g_alloc.ctx);
+        if (q && ((uintptr_t)q % 256) != 0) {  // the layout needs 256-byte alignment
+            g_alloc.free(q, bytes, g_alloc.ctx);
+            q = nullptr;
+        }
+        *ptr = (char *)q;
+        return q != nullptr;
+    }
+    if (cudaMalloc((void **)ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return false;
+    }
+    return true;
+}
+
+void dev_free(char *ptr, size_t bytes) {
+    if (!ptr) return;
+    if (g_alloc.free) {
+        cudaDeviceSynchronize();  // no kernel of this library may still use the memory
+        g_alloc.free(ptr, bytes, g_alloc.ctx);
+    } else {
+        cudaFree(ptr);
+    }
+}
+
 void drop_graph() {
     if (g_ws.exec) cudaGraphExecDestroy(g_ws.exec);
     g_ws.exec = nullptr;
@@ -56,7 +93,7 @@ void drop_graph() {
 
 void release_all() {
     drop_graph();
-    if (g_ws.dev) cudaFree(g_ws.dev);
+    dev_free(g_ws.dev, g_ws.dev_bytes);
     if (g_ws.host_ctl) cudaFreeHost(g_ws.host_ctl);
     if (g_ws.batch_ctl) cudaFreeHost(g_ws.batch_ctl);
     for (auto &e : g_ws.ev)
@@ -222,16 +259,12 @@ gk_status ensure_workspace(size_t bytes) {
     }
     if (g_ws.dev_bytes >= bytes) return GK_OK;
     drop_graph();
-    if (g_ws.dev) cudaFree(g_ws.dev);
+    dev_free(g_ws.dev, g_ws.dev_bytes);
     g_ws.dev = nullptr;
     g_ws.dev_bytes = 0;
     size_t want = bytes + bytes / 8;
-    if (cudaMalloc((void **)&g_ws.dev, want) != cudaSuccess) {
-        cudaGetLastError();
-        if (cudaMalloc((void **)&g_ws.dev, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return GK_ERR_OOM;
-        }
+    if (!dev_alloc(&g_ws.dev, want)) {
+        if (!dev_alloc(&g_ws.dev, bytes)) return GK_ERR_OOM;
         want = bytes;
     }
     g_ws.dev_bytes = want;
@@ -1122,5 +1155,14 @@ gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64
 }
 
 void gk_release(void) { release_all(); }
+
+gk_status gk_set_allocator(gk_alloc_fn alloc, gk_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) return GK_ERR_INVALID_ARG;
+    release_all();  // the current workspace goes back to whoever provided it
+    g_alloc.alloc = alloc;
+    g_alloc.free = free_fn;
+    g_alloc.ctx = ctx;
+    return GK_OK;
+}
 
 }  // extern "C"

@@ -29,7 +29,7 @@ def test_header_declares_the_entry_points():
     for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
                  "gk_status_string", "gk_abi_version", "gk_partition_batched",
-                 "gk_partition_sampled", "gk_partition_quality"):
+                 "gk_partition_sampled", "gk_partition_quality", "gk_set_allocator"):
         assert want in names
 
 
@@ -91,6 +91,16 @@ def test_quality_rejects_bad_arguments_before_any_launch(libgk):
         gk.GK_ERR_INVALID_ARG
     assert L.gk_partition_quality(P(rp), None, 2, 4, P(blk), 1, None, None, None, None) == \
         gk.GK_ERR_INVALID_ARG
+
+
+def test_set_allocator_needs_both_callbacks(libgk):
+    import paper_1805_01208_gb300 as gk
+    L = gk.lib()
+    alloc = gk._ALLOC_FN(lambda nbytes, ctx: None)
+    assert L.gk_set_allocator(ctypes.cast(alloc, ctypes.c_void_p), None, None) == gk.GK_ERR_INVALID_ARG
+    assert L.gk_set_allocator(None, None, None) == gk.GK_OK
+    with pytest.raises(ValueError):
+        gk.set_allocator(alloc=lambda n: 0)
 
 
 def test_library_is_built_for_sm103a(libgk):

@@ -491,3 +491,23 @@ def test_bounds_over_many_passes_wrap_to_fresh_passes(gk):
         out.append((_np(block), _np(C), _np(I), res))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
     assert out[0][3]["balance_passes"] == out[1][3]["balance_passes"] > 64
+
+
+# ----------------------------------------------------------------------------------------
+# Workspace from the caller's allocator (gk_set_allocator)
+# ----------------------------------------------------------------------------------------
+def test_workspace_from_torch_allocator(gk):
+    x = _points("gmm", 40_000, 3, 67, "f64")
+    gk.release()
+    b0, C0, I0, r0 = gk.partition(_dev(x), 30, 0.03)
+    blocks = gk.use_torch_allocator()
+    try:
+        b1, C1, I1, r1 = gk.partition(_dev(x), 30, 0.03)
+        assert len(blocks) >= 1  # the workspace came from the callback
+        assert np.array_equal(_np(b0), _np(b1)) and np.array_equal(_np(C0), _np(C1))
+        assert r0["balance_passes"] == r1["balance_passes"]
+    finally:
+        gk.set_allocator()
+    assert len(blocks) == 0  # and went back to it
+    b2, C2, I2, r2 = gk.partition(_dev(x), 30, 0.03)
+    assert np.array_equal(_np(b0), _np(b2))
