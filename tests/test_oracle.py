@@ -539,3 +539,38 @@ def test_sampled_rejects_an_order_that_is_not_a_permutation():
     assert oracle.partition_sampled(x, None, 4, 0.03, order)["result"]["status"] == oracle.OR_INVALID
     order[7] = 500
     assert oracle.partition_sampled(x, None, 4, 0.03, order)["result"]["status"] == oracle.OR_INVALID
+
+
+# ----------------------------------------------------------------------------------------
+# The paper's multi-process semantics (replicated centers, summed local block sizes and
+# coordinate sums; Section 4, Algorithm 1 globalSumVector): with exact reductions the
+# result does not depend on how the points are cut into process shards.
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shards", [2, 5, 16])
+def test_sharded_reductions_equal_the_global_ones(shards):
+    rng = np.random.default_rng(200 + shards)
+    n, d, k = 6000, 3, 11
+    x = rng.random((n, d)) ** 2
+    C = x[rng.choice(n, k, replace=False)]
+    I = rng.uniform(0.8, 1.2, k)
+    A, _, _ = oracle.assign(x, C, I)
+    S_glob, W = oracle.block_weights(A, None, k)
+    # each shard (a contiguous range of the curve order, as after the redistribution)
+    # assigns its own points against the replicated centers and sums locally
+    keys = oracle.hilbert_keys(x)
+    order = oracle.sort_keys(keys)
+    cuts = np.linspace(0, n, shards + 1).astype(int)
+    S = np.zeros(k)
+    sums = np.zeros((k, d))
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        idx = order[a:b]
+        As, _, _ = oracle.assign(x[idx], C, I)
+        assert np.array_equal(As, A[idx])
+        S += np.bincount(As, minlength=k)
+        for c in range(k):
+            sums[c] += x[idx][As == c].sum(0)
+    assert np.array_equal(S, S_glob) and S.sum() == W == n
+    C_new, _, _ = oracle.move_centers(x, None, A, C)
+    nonempty = S > 0
+    assert np.allclose(sums[nonempty] / S[nonempty, None], C_new[nonempty], rtol=1e-13, atol=0)
