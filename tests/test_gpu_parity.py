@@ -511,3 +511,19 @@ def test_workspace_from_torch_allocator(gk):
     assert len(blocks) == 0  # and went back to it
     b2, C2, I2, r2 = gk.partition(_dev(x), 30, 0.03)
     assert np.array_equal(_np(b0), _np(b2))
+
+
+def test_allocation_failure_is_reported(gk):
+    """A failing allocation, injected through the allocator hook on the host, gives
+    GK_ERR_OOM, and the library works again once cudaMalloc is back."""
+    x = _dev(_points("uniform", 5_000, 2, 69, "f64"))
+    gk.release()
+    gk.set_allocator(lambda nbytes: 0, lambda ptr, nbytes: None)
+    try:
+        with pytest.raises(gk.GKError) as e:
+            gk.partition(x, 8, 0.03)
+        assert e.value.status == gk.GK_ERR_OOM
+    finally:
+        gk.set_allocator()
+    block, C, I, res = gk.partition(x, 8, 0.03)
+    assert res["balanced"] == 1
