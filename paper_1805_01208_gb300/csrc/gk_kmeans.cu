@@ -1726,8 +1726,9 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
     __shared__ int s_newpp;
     if (last && threadIdx.x == 0) s_newpp = -1;
     if (last && threadIdx.x == 0) {
-        double maxS = okey_to_f64(atomicOr(&ctl->maxS_key, 0ull));
-        double maxg = okey_to_f64(atomicOr(&ctl->maxg_key, 0ull));
+        // the other CTAs' atomics precede the last-block fence: plain L2 loads, in parallel
+        double maxS = okey_to_f64(__ldcg(&ctl->maxS_key));
+        double maxg = okey_to_f64(__ldcg(&ctl->maxg_key));
         ctl->maxS_key = 0ull;
         ctl->maxg_key = 0ull;
         ctl->coop_cnt = 0u;  // the next filter rebuilds the cooperative list
@@ -1749,7 +1750,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         if (bnd) {
             // the next pass continues the phase: the running sum of the passes' (smallest -
             // largest) log2 g ratio, lowered by the margin for the rounding of the logs
-            const float m = okey_to_f32(ctl->min_lr_key), M = okey_to_f32(ctl->max_lr_key);
+            const float m = okey_to_f32(__ldcg(&ctl->min_lr_key)), M = okey_to_f32(__ldcg(&ctl->max_lr_key));
             ctl->min_lr_key = 0xffffffffu;
             ctl->max_lr_key = 0u;
             if (!bal) {
@@ -1965,8 +1966,8 @@ __global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
     if (last_block(ctl) && tid == 0) {
         double s = 0.0;
         for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&p.part[b]);
-        int n = atomicAdd(&ctl->nonempty, 0);
-        double m = okey_to_f64(atomicOr(&ctl->maxd_key, 0ull));
+        int n = __ldcg(&ctl->nonempty);
+        double m = okey_to_f64(__ldcg(&ctl->maxd_key));
         ctl->nonempty = 0;
         ctl->maxd_key = 0ull;
         ctl->beta = n > 0 ? s / (double)n : 0.0;

@@ -19,15 +19,20 @@ __global__ void quality_vertex_kernel(const long long *row_ptr, const int *col, 
                                       unsigned long long *ext, unsigned long long *comm,
                                       unsigned long long *boundary, int *bad) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    const int b = block[v];
-    const long long e0 = row_ptr[v], e1 = row_ptr[v + 1];
-    if ((unsigned)b >= (unsigned)k || e0 < 0 || e1 < e0 || e1 > nnz) {
-        atomicOr(bad, 1);
-        return;
+    bool ok = v < n;  // every lane stays to the warp vote at the end
+    int b = 0;
+    long long e0 = 0, e1 = 0;
+    if (ok) {
+        b = block[v];
+        e0 = row_ptr[v];
+        e1 = row_ptr[v + 1];
+        if ((unsigned)b >= (unsigned)k || e0 < 0 || e1 < e0 || e1 > nnz) {
+            atomicOr(bad, 1);
+            ok = false;
+        }
     }
     unsigned nf = 0, nd = 0;
-    for (long long e = e0; e < e1; ++e) {
+    for (long long e = e0; ok && e < e1; ++e) {
         const int u = col[e];
         if ((unsigned long long)(long long)u >= (unsigned long long)n) {
             atomicOr(bad, 1);
@@ -51,8 +56,9 @@ __global__ void quality_vertex_kernel(const long long *row_ptr, const int *col, 
     if (nf) {
         atomicAdd(&ext[b], (unsigned long long)nf);
         atomicAdd(&comm[b], (unsigned long long)nd);
-        atomicAdd(boundary, 1ull);
     }
+    const unsigned m = __ballot_sync(0xffffffffu, nf != 0);  // boundary vertices of the warp
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(boundary, (unsigned long long)__popc(m));
 }
 
 // One CTA: sums and maxima over the k blocks -> out[0..3] = edge cut, total comm,
