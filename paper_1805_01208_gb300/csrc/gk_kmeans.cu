@@ -665,7 +665,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             cl = __ldg(&cd[2 * c + 1]);
         };
         float tt = INFINITY;
-        for (int i = lane; i < L; i += 32) {
+#pragma unroll 4
+        for (int i = lane; i < L; i += 32) {  // several chunks' loads in flight together
             int c;
             float4 ch, cl;
             center(i, c, ch, cl);
@@ -678,6 +679,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
         int cnt = 0;
         float gkept = 0.0f;
         float4 *rec = p.trec + (size_t)t * kRecF4;
+#pragma unroll 2
         for (int base = 0; base < L; base += 32) {
             const int i = base + lane;
             bool keep = false;
