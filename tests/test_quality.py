@@ -1,6 +1,6 @@
-"""Partition quality measures of Section 5 (edge cut, communication volume): the numpy
-oracle pinned by hand-counted graphs, closed forms on lattice meshes and brute force
-(CPU), and gk_partition_quality against it (GPU)."""
+"""Partition quality measures of Section 5 (edge cut, communication volume, block
+diameter): the numpy oracle pinned by hand-counted graphs, closed forms on lattice meshes,
+trees and brute force (CPU), and the GPU entry points against it (GPU)."""
 import math
 
 import numpy as np
@@ -94,6 +94,89 @@ def test_random_graph_against_brute_force():
         comm[block[v]] += len({block[u] for u in nb} - {block[v]})
     assert list(q["ext"]) == ext and list(q["comm"]) == comm
     assert q["edge_cut"] == sum(1 for a, b in edges if block[a] != block[b])
+
+
+def _tree(n, rng):
+    """A random tree on n vertices (vertex i > 0 hangs below a random earlier vertex)."""
+    return [(int(rng.integers(0, i)), i) for i in range(1, n)]
+
+
+def test_diameter_hand_graphs():
+    # cycle of 8: block 0 is the path 0-1-2-3-4-5 (its own diameter 5 although 5 and 0
+    # are 3 apart through block 1), block 1 = {6, 7}, block 2 empty
+    rp, col = _csr(8, [(i, (i + 1) % 8) for i in range(8)])
+    block = np.array([0, 0, 0, 0, 0, 0, 1, 1])
+    for f in (oq.block_diameter_exact, oq.block_diameter_sweeps):
+        assert f(rp, col, block, 3).tolist() == [5, 1, 0]
+    # star: diameter 2; a block of two separate vertices: not connected
+    rp, col = _csr(6, [(0, 1), (0, 2), (0, 3), (4, 4)])
+    block = np.array([0, 0, 0, 0, 1, 1])
+    for f in (oq.block_diameter_exact, oq.block_diameter_sweeps):
+        assert f(rp, col, block, 2).tolist() == [2, -1]
+    s = oq.diameter_summary([2, -1], [4, 2])
+    assert s == {"max_diameter": 2, "disconnected_blocks": 1, "harmonic_mean": 2 / 0.5}
+    assert oq.diameter_summary([0, 3, 6], [1, 4, 7])["harmonic_mean"] == 2 / (1 / 3 + 1 / 6)
+    assert oq.diameter_summary([-1], [2])["harmonic_mean"] == math.inf
+    assert oq.diameter_summary([0, 0], [1, 0])["harmonic_mean"] == 0.0
+
+
+def test_diameter_sweeps_exact_on_trees():
+    """On a tree a sweep from any vertex ends at an end of a longest path, so the second
+    sweep already gives the exact diameter."""
+    rng = np.random.default_rng(12)
+    for n in (2, 7, 40, 300):
+        rp, col = _csr(n, _tree(n, rng))
+        block = np.zeros(n, dtype=np.int64)
+        exact = oq.block_diameter_exact(rp, col, block, 1)
+        assert oq.block_diameter_sweeps(rp, col, block, 1, sweeps=2).tolist() == exact.tolist()
+        assert oq.block_diameter_sweeps(rp, col, block, 1).tolist() == exact.tolist()
+    # a forest, one tree per block, vertices shuffled
+    sizes = [5, 30, 1, 12]
+    edges, off = [], 0
+    for m in sizes:
+        edges += [(a + off, b + off) for a, b in _tree(m, rng)]
+        off += m
+    perm = rng.permutation(off)
+    rp, col = _csr(off, [(int(perm[a]), int(perm[b])) for a, b in edges])
+    block = np.empty(off, dtype=np.int64)
+    block[perm] = np.repeat(np.arange(len(sizes)), sizes)
+    assert oq.block_diameter_sweeps(rp, col, block, 4).tolist() == \
+        oq.block_diameter_exact(rp, col, block, 4).tolist()
+
+
+def test_diameter_sweeps_within_factor_two():
+    rng = np.random.default_rng(13)
+    for trial in range(6):
+        n, k = 80, 4
+        e = {tuple(sorted(p)) for p in rng.integers(0, n, (140, 2)).tolist() if p[0] != p[1]}
+        rp, col = _csr(n, sorted(e))
+        block = rng.integers(0, k, n)
+        exact = oq.block_diameter_exact(rp, col, block, k)
+        lb1 = oq.block_diameter_sweeps(rp, col, block, k, sweeps=1)
+        lb = oq.block_diameter_sweeps(rp, col, block, k)
+        assert np.array_equal(exact < 0, lb < 0) and np.array_equal(lb1 < 0, lb < 0)
+        c = exact >= 0
+        assert np.all(lb[c] <= exact[c]) and np.all(2 * lb[c] >= exact[c])
+        assert np.all(lb1[c] <= lb[c])
+
+
+def test_diameter_lattice_closed_forms():
+    # 3-D, 6 neighbours: a box block of a x b x c vertices has diameter
+    # (a - 1) + (b - 1) + (c - 1); two sweeps reach it (the first ends at a corner)
+    nx, ny, nz, k = 12, 5, 4, 3
+    x, rp, col = synth.lattice_mesh((nx, ny, nz), 3)
+    block = _slabs(x, nx, k)
+    want = [3 + (ny - 1) + (nz - 1)] * k
+    assert oq.block_diameter_exact(rp, col, block, k).tolist() == want
+    assert oq.block_diameter_sweeps(rp, col, block, k).tolist() == want
+    # 2-D triangulated grid ((+1, +1) diagonals): a box of a x b vertices has diameter
+    # (a - 1) + (b - 1), between the corners that no diagonal shortens
+    nx, ny = 10, 7
+    x, rp, col = synth.lattice_mesh((nx, ny), 4)
+    block = _slabs(x, nx, 2)
+    assert oq.block_diameter_exact(rp, col, block, 2).tolist() == [4 + ny - 1] * 2
+    lb = oq.block_diameter_sweeps(rp, col, block, 2)
+    assert np.all(lb <= 4 + ny - 1) and np.all(2 * lb >= 4 + ny - 1)
 
 
 # ----------------------------------------------------------------------------------------
