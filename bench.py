@@ -576,8 +576,8 @@ def _bounds_leg(gk, xt, wt, spec, stream, flush, plain_ms, steps):
 
 
 def _quality(gk, synth, spec, stream):
-    """Edge cut and communication volume (gk_partition_quality) of balanced k-means and of
-    the plain curve split (the i-th n/k points on the Hilbert curve form block i) on a
+    """Edge cut and communication volume (gk_partition_quality) and block diameter bounds
+    (gk_block_diameter, three sweeps) of balanced k-means and of the plain curve split (the i-th n/k points on the Hilbert curve form block i) on a
     graded 3-D lattice mesh with as many vertices as the workload has points (at most
     200^3), the workload's k and eps."""
     import torch
@@ -598,12 +598,18 @@ def _quality(gk, synth, spec, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     qs, _, _ = gk.partition_quality(rpt, colt, sfc, k)
+    t0 = time.perf_counter()
+    dk, _ = gk.block_diameter(rpt, colt, block, k, 3)  # waits for its own work
+    diam_ms = (time.perf_counter() - t0) * 1e3
+    ds, _ = gk.block_diameter(rpt, colt, sfc, k, 3)
     return {"mesh": f"graded 3-D lattice {side}^3 (6-neighbour), random vertex order",
             "vertices": n, "edges": int(rp[-1]) // 2, "k": k, "kmeans": qk, "sfc_split": qs,
             "kmeans_balanced": res["balanced"], "kmeans_partition_ms": res["time_total_ms"],
             "quality_ms": e0.elapsed_time(e1),
             "cut_ratio_kmeans_over_sfc": qk["edge_cut"] / max(1, qs["edge_cut"]),
-            "max_comm_ratio_kmeans_over_sfc": qk["max_comm_volume"] / max(1, qs["max_comm_volume"])}
+            "max_comm_ratio_kmeans_over_sfc": qk["max_comm_volume"] / max(1, qs["max_comm_volume"]),
+            "diameter_sweeps": 3, "diameter_kmeans": dk, "diameter_sfc_split": ds,
+            "diameter_ms": diam_ms}
 
 
 def _attach_traffic(roof, workload):

@@ -293,6 +293,42 @@ gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64
                                const int32_t *block, int32_t k, int64_t *ext_out,
                                int64_t *comm_out, gk_quality *quality, void *stream);
 
+/* Block diameters of a partition (Section 5). */
+typedef struct gk_diameter {
+    int64_t max_diameter;         /* largest bound over the connected blocks (0 if none)       */
+    int64_t disconnected_blocks;  /* blocks whose induced subgraph is not connected            */
+    int64_t bfs_levels;           /* breadth-first levels run, over all sweeps                 */
+    double harmonic_mean;         /* over the blocks of >= 2 vertices, a disconnected block
+                                     adding 1/inf = 0 to the sum of reciprocals; +inf if the
+                                     sum is 0, 0 if there is no such block                    */
+} gk_diameter;
+
+/* Largest number of sweeps gk_block_diameter accepts. */
+#define GK_MAX_SWEEPS 64
+
+/*
+ * Lower bounds of the block diameters of a partition (Section 5): diam(V_i) is the largest
+ * distance between two vertices of V_i in the subgraph V_i induces (infinite when that
+ * subgraph is not connected).  The paper evaluates a lower bound from the first rounds of
+ * iFUB; this call runs `sweeps` breadth-first searches inside every block (all blocks in
+ * parallel), the first from the block's smallest vertex index, each later one from the
+ * smallest vertex index at the largest distance of the previous one, and returns the
+ * largest eccentricity seen.  Every sweep's eccentricity lies in [diam/2, diam]; on a tree
+ * two sweeps give diam exactly.
+ *   row_ptr, col, block, n, nnz, k: as for gk_partition_quality;
+ *   sweeps:   1 .. GK_MAX_SWEEPS (3 is the usual choice);
+ *   diam_out: k int32 (nullable): the bound of each block, -1 for a block that is not
+ *             connected, 0 for an empty block;
+ *   summary:  nullable.
+ * Every pointer may be host or device memory.  The host waits for the stream once per
+ * breadth-first level (to size the next launch), so the call returns with its work done.
+ * Malformed input gives GK_ERR_INVALID_ARG (found on the device, before any search).
+ * Requires 1 <= n < 2^31, nnz >= 0, k >= 1.
+ */
+gk_status gk_block_diameter(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
+                            const int32_t *block, int32_t k, int32_t sweeps, int32_t *diam_out,
+                            gk_diameter *summary, void *stream);
+
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);
 

@@ -116,6 +116,19 @@ class Quality(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Diameter(ctypes.Structure):
+    """gk_diameter (include/gk.h)."""
+    _fields_ = [
+        ("max_diameter", ctypes.c_int64),
+        ("disconnected_blocks", ctypes.c_int64),
+        ("bfs_levels", ctypes.c_int64),
+        ("harmonic_mean", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _alloc_refs: dict = {}  # the registered callbacks, kept alive while the library may call them
@@ -145,6 +158,8 @@ def lib():
                                            P, P]
         L.gk_partition_quality.argtypes = [P, P, i64, i64, P, i32, P, P, P, P]
         L.gk_partition_quality.restype = i32
+        L.gk_block_diameter.argtypes = [P, P, i64, i64, P, i32, i32, P, P, P]
+        L.gk_block_diameter.restype = i32
         for name in ("gk_hilbert_keys", "gk_sfc_init", "gk_assign", "gk_move_centers",
                      "gk_balanced_kmeans", "gk_partition", "gk_partition_sampled"):
             getattr(L, name).restype = i32
@@ -386,6 +401,20 @@ def partition_quality(row_ptr, col, block, k: int, stream=None):
                                     _ptr(comm), ctypes.byref(q), _stream(block, stream))
     _check(st, "gk_partition_quality")
     return q.as_dict(), ext, comm
+
+
+def block_diameter(row_ptr, col, block, k: int, sweeps: int = 3, stream=None):
+    """Lower bounds of the block diameters (Section 5) from `sweeps` breadth-first sweeps
+    inside every block.  Returns (dict, diam) with diam the per-block bounds as int32 on
+    the side of `block` (-1: block not connected, 0: empty block)."""
+    n = int(block.shape[0])
+    nnz = int(col.shape[0])
+    diam = _empty(block, (k,), "i32")
+    q = Diameter()
+    st = lib().gk_block_diameter(_ptr(row_ptr), _ptr(col), n, nnz, _ptr(block), k, sweeps,
+                                 _ptr(diam), ctypes.byref(q), _stream(block, stream))
+    _check(st, "gk_block_diameter")
+    return q.as_dict(), diam
 
 
 def set_allocator(alloc=None, free=None):

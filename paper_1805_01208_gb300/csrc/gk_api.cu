@@ -1154,6 +1154,70 @@ gk_status gk_partition_quality(const int64_t *row_ptr, const int32_t *col, int64
     return GK_OK;
 }
 
+gk_status gk_block_diameter(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
+                            const int32_t *block, int32_t k, int32_t sweeps, int32_t *diam_out,
+                            gk_diameter *summary, void *stream) {
+    if (!row_ptr || (!col && nnz > 0) || !block || n < 1 || n >= (1ll << 31) || nnz < 0 || k < 1 ||
+        sweeps < 1 || sweeps > GK_MAX_SWEEPS)
+        return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    const void *in[3] = {row_ptr, col, block};
+    const size_t in_bytes[3] = {(size_t)(n + 1) * 8, (size_t)nnz * 4, (size_t)n * 4};
+    const size_t align[3] = {8, 4, 4};
+    PtrKind kind[3];
+    size_t need = 0;
+    for (int i = 0; i < 3; ++i) {
+        kind[i] = in[i] ? ptr_kind(in[i], dev) : kDevice;
+        if (kind[i] == kForeign || (kind[i] == kDevice && ((uintptr_t)in[i] % align[i])))
+            return GK_ERR_INVALID_ARG;
+        if (kind[i] == kHost) need += align_up(in_bytes[i]);
+    }
+    if (diam_out && ptr_kind(diam_out, dev) == kForeign) return GK_ERR_INVALID_ARG;
+    need += align_up(diameter_work_bytes(n, k)) + align_up((size_t)k * 4) + align_up(16) +
+            align_up(8);
+    gk_status st = ensure_workspace(need);
+    if (st != GK_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = g_ws.dev;
+    const void *dptr[3];
+    for (int i = 0; i < 3; ++i) {
+        if (kind[i] == kHost) {
+            GK_CUDA(cudaMemcpyAsync(ws, in[i], in_bytes[i], cudaMemcpyHostToDevice, s));
+            dptr[i] = ws;
+            ws += align_up(in_bytes[i]);
+        } else {
+            dptr[i] = in[i];
+        }
+    }
+    void *work = ws;
+    ws += align_up(diameter_work_bytes(n, k));
+    int *diam = (int *)ws;
+    ws += align_up((size_t)k * 4);
+    long long *out_i = (long long *)ws;
+    ws += align_up(16);
+    double *out_d = (double *)ws;
+    int hbad = 0;
+    long long levels = 0;
+    GK_CUDA(run_diameter((const long long *)dptr[0], (const int *)dptr[1], n, nnz,
+                         (const int *)dptr[2], k, sweeps, work, diam, out_i, out_d, &hbad, &levels,
+                         s));
+    if (hbad) return GK_ERR_INVALID_ARG;
+    if (diam_out) GK_CUDA(cudaMemcpyAsync(diam_out, diam, (size_t)k * 4, cudaMemcpyDefault, s));
+    long long hi[2];
+    double hd = 0.0;
+    GK_CUDA(cudaMemcpyAsync(hi, out_i, sizeof(hi), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(&hd, out_d, sizeof(hd), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (summary) {
+        summary->max_diameter = hi[0];
+        summary->disconnected_blocks = hi[1];
+        summary->bfs_levels = levels;
+        summary->harmonic_mean = hd;
+    }
+    return GK_OK;
+}
+
 void gk_release(void) { release_all(); }
 
 gk_status gk_set_allocator(gk_alloc_fn alloc, gk_free_fn free_fn, void *ctx) {

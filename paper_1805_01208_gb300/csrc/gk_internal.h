@@ -40,6 +40,16 @@ cudaError_t launch_quality(const long long *row_ptr, const int *col, long long n
                            const int *block, int k, unsigned long long *ext,
                            unsigned long long *comm, unsigned long long *out, int *bad,
                            cudaStream_t s);
+// Block diameter lower bounds from `sweeps` breadth-first sweeps (gk_quality.cu).  work:
+// diameter_work_bytes(n, k) bytes of device memory, 4-byte aligned; diam: k int32 (device);
+// out_i[0..1] = largest bound, disconnected blocks; out_d[0] = harmonic mean (device).
+// Synchronises the stream once per level; on malformed input sets *hbad and returns
+// before any search.
+size_t diameter_work_bytes(long long n, int k);
+cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, long long nnz,
+                         const int *block, int k, int sweeps, void *work, int *diam,
+                         long long *out_i, double *out_d, int *hbad, long long *hlevels,
+                         cudaStream_t s);
 
 // iteration (gk_kmeans.cu)
 cudaError_t launch_init(const Prob &p, cudaStream_t s);

@@ -1,8 +1,12 @@
 // gk_quality.cu -- partition quality measures of Section 5 on a graph given as a
 // symmetric CSR adjacency: per block ext(V_i) (edges leaving the block) and comm(V_i)
 // (for every vertex of the block, the number of other blocks holding a neighbour),
-// then edge cut = sum ext / 2, total and maximum communication volume.
+// then edge cut = sum ext / 2, total and maximum communication volume; and per block a
+// lower bound of diam(V_i), the largest distance between two vertices of V_i inside the
+// subgraph V_i induces, from breadth-first sweeps.
 #include <cuda_runtime.h>
+
+#include <climits>
 
 #include "gk_common.cuh"
 #include "gk_internal.h"
@@ -116,6 +120,209 @@ cudaError_t launch_quality(const long long *row_ptr, const int *col, long long n
         quality_vertex_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, n, nnz, block, k,
                                                                           ext, comm, out + 4, bad);
     quality_final_kernel<<<1, 256, 0, s>>>(ext, comm, k, out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------------
+// Block diameters.  The paper evaluates a lower bound from the first rounds of iFUB; here
+// the bound of every block comes from `sweeps` breadth-first sweeps inside the block, the
+// first from its smallest vertex index, each later one from the vertex the previous sweep
+// reached last (smallest index among those at the largest distance).  Each sweep's
+// eccentricity lies in [diam / 2, diam].  A block the first sweep does not cover is not
+// connected (infinite diameter, reported as -1).
+//
+// The sweeps of all blocks run together: an edge between two blocks is never followed, so
+// one search seeded with one vertex per block is k separate searches.  Each level expands
+// a frontier list; a vertex joins the next list when its distance moves from -1 to the
+// next level (compare-and-swap, so once per sweep), and the host reads the length of the
+// next list to size the next launch and to stop when it is empty.
+// ----------------------------------------------------------------------------------------
+__global__ void diam_fill_kernel(int *a, long long m, int v) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] = v;
+}
+
+// Block sizes, smallest vertex of every block, and the checks of the input (row ranges,
+// neighbours, block ids): the searches run only on input that passed.
+__global__ void diam_init_kernel(const long long *row_ptr, const int *col, long long n,
+                                 long long nnz, const int *block, int k, int *size, int *start,
+                                 int *bad) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int b = block[v];
+    const long long e0 = row_ptr[v], e1 = row_ptr[v + 1];
+    if ((unsigned)b >= (unsigned)k || e0 < 0 || e1 < e0 || e1 > nnz) {
+        atomicOr(bad, 1);
+        return;
+    }
+    for (long long e = e0; e < e1; ++e)
+        if ((unsigned long long)(long long)col[e] >= (unsigned long long)n) atomicOr(bad, 1);
+    atomicAdd(&size[b], 1);
+    atomicMin(&start[b], (int)v);
+}
+
+// One thread per block: its start vertex (if any) opens the sweep at distance 0.
+__global__ void diam_seed_kernel(int k, const int *start, int *dist, int *front, unsigned *cnt,
+                                 int *ecc, int *reached) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= k) return;
+    const int s = start[b];
+    ecc[b] = 0;
+    reached[b] = s != INT_MAX;
+    if (s != INT_MAX) {
+        dist[s] = 0;
+        front[atomicAdd(cnt, 1u)] = s;
+    }
+}
+
+// One thread per frontier vertex of distance `level`.
+__global__ void diam_expand_kernel(const int *front, const unsigned *cnt_in, int level,
+                                   const long long *row_ptr, const int *col, const int *block,
+                                   int *dist, int *next, unsigned *cnt_out, int *ecc,
+                                   int *reached) {
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *cnt_in) return;
+    const int v = front[i];
+    const int b = block[v];
+    const long long e1 = row_ptr[v + 1];
+    for (long long e = row_ptr[v]; e < e1; ++e) {
+        const int u = col[e];
+        if (u == v || block[u] != b) continue;
+        if (atomicCAS(&dist[u], -1, level + 1) == -1) {
+            next[atomicAdd(cnt_out, 1u)] = u;
+            atomicAdd(&reached[b], 1);
+            atomicMax(&ecc[b], level + 1);
+        }
+    }
+}
+
+// The next start of every block: its smallest vertex at the largest distance.
+__global__ void diam_far_kernel(long long n, const int *block, const int *dist, const int *ecc,
+                                int *start) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int dv = dist[v];
+    const int b = block[v];
+    if (dv >= 0 && dv == ecc[b]) atomicMin(&start[b], (int)v);
+}
+
+// Bound and connectivity per block after a sweep.
+__global__ void diam_record_kernel(int k, int sweep, const int *size, const int *reached,
+                                   const int *ecc, int *bound, int *conn) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= k) return;
+    if (sweep == 0) {
+        conn[b] = reached[b] == size[b];
+        bound[b] = ecc[b];
+    } else {
+        bound[b] = max(bound[b], ecc[b]);
+    }
+}
+
+// One CTA: per-block results (bound, -1 when not connected, 0 when empty) and the summary
+// out_i[0..1] = largest bound over the connected blocks, disconnected blocks;
+// out_d[0] = harmonic mean over the blocks of at least two vertices (1/inf = 0 for a
+// disconnected block; +inf when the sum of reciprocals is 0, 0 when there is no such
+// block).  Every thread sums a fixed stride of blocks, then a fixed tree: the same sum
+// on every run.
+__global__ void __launch_bounds__(256) diam_final_kernel(int k, const int *size, const int *bound,
+                                                         const int *conn, int *diam,
+                                                         long long *out_i, double *out_d) {
+    __shared__ double sr[256];
+    __shared__ long long sm[256], sd[256], sb[256];
+    long long mx = 0, nd = 0, nb = 0;
+    double r = 0.0;
+    for (int b = threadIdx.x; b < k; b += blockDim.x) {
+        const int sz = size[b];
+        const int val = sz == 0 ? 0 : (conn[b] ? bound[b] : -1);
+        diam[b] = val;
+        if (val >= 0) mx = max(mx, (long long)val);
+        if (val < 0) ++nd;
+        if (sz >= 2) {
+            ++nb;
+            if (val > 0) r += 1.0 / (double)val;
+        }
+    }
+    sr[threadIdx.x] = r;
+    sm[threadIdx.x] = mx;
+    sd[threadIdx.x] = nd;
+    sb[threadIdx.x] = nb;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sr[threadIdx.x] += sr[threadIdx.x + o];
+            sm[threadIdx.x] = max(sm[threadIdx.x], sm[threadIdx.x + o]);
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+            sb[threadIdx.x] += sb[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out_i[0] = sm[0];
+        out_i[1] = sd[0];
+        const double sum = sr[0];
+        out_d[0] = sb[0] == 0 ? 0.0 : (sum == 0.0 ? __longlong_as_double(0x7ff0000000000000ll)
+                                                  : (double)sb[0] / sum);
+    }
+}
+
+size_t diameter_work_bytes(long long n, int k) {
+    return (size_t)n * 4 * 3 + (size_t)k * 4 * 6 + 64;
+}
+
+static unsigned blocks_of(long long m) { return (unsigned)((m + 255) / 256); }
+
+cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, long long nnz,
+                         const int *block, int k, int sweeps, void *work, int *diam,
+                         long long *out_i, double *out_d, int *hbad, long long *hlevels,
+                         cudaStream_t s) {
+    // work: dist, two frontier lists (n each), six k-vectors, two counters and the flag
+    int *dist = (int *)work;
+    int *front[2] = {dist + n, dist + 2 * n};
+    int *size = dist + 3 * n, *start = size + k, *ecc = start + k, *reached = ecc + k;
+    int *bound = reached + k, *conn = bound + k;
+    unsigned *cnt = (unsigned *)(conn + k);
+    int *bad = (int *)(cnt + 2);
+    *hbad = 0;
+    *hlevels = 0;
+    cudaError_t e = cudaMemsetAsync(size, 0, (size_t)k * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    diam_fill_kernel<<<blocks_of(k), 256, 0, s>>>(start, k, INT_MAX);
+    diam_init_kernel<<<blocks_of(n), 256, 0, s>>>(row_ptr, col, n, nnz, block, k, size, start, bad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (*hbad) return cudaSuccess;
+    for (int sweep = 0; sweep < sweeps; ++sweep) {
+        if ((e = cudaMemsetAsync(dist, 0xff, (size_t)n * 4, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(cnt, 0, 4, s)) != cudaSuccess) return e;
+        diam_seed_kernel<<<blocks_of(k), 256, 0, s>>>(k, start, dist, front[0], cnt, ecc, reached);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        int cur = 0;
+        for (int level = 0;; ++level) {  // at most n levels: every vertex joins one list
+            unsigned h = 0;
+            if ((e = cudaMemcpyAsync(&h, cnt + cur, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            if (h == 0) break;
+            if ((e = cudaMemsetAsync(cnt + (cur ^ 1), 0, 4, s)) != cudaSuccess) return e;
+            diam_expand_kernel<<<blocks_of(h), 256, 0, s>>>(front[cur], cnt + cur, level, row_ptr,
+                                                            col, block, dist, front[cur ^ 1],
+                                                            cnt + (cur ^ 1), ecc, reached);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            cur ^= 1;
+            ++*hlevels;
+        }
+        diam_record_kernel<<<blocks_of(k), 256, 0, s>>>(k, sweep, size, reached, ecc, bound, conn);
+        if (sweep + 1 < sweeps) {
+            diam_fill_kernel<<<blocks_of(k), 256, 0, s>>>(start, k, INT_MAX);
+            diam_far_kernel<<<blocks_of(n), 256, 0, s>>>(n, block, dist, ecc, start);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    diam_final_kernel<<<1, 256, 0, s>>>(k, size, bound, conn, diam, out_i, out_d);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ def test_header_declares_the_entry_points():
     for want in ("gk_hilbert_keys", "gk_sfc_init", "gk_balanced_kmeans", "gk_partition",
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
                  "gk_status_string", "gk_abi_version", "gk_partition_batched",
-                 "gk_partition_sampled", "gk_partition_quality", "gk_set_allocator"):
+                 "gk_partition_sampled", "gk_partition_quality", "gk_block_diameter",
+                 "gk_set_allocator"):
         assert want in names
 
 
@@ -91,6 +92,19 @@ def test_quality_rejects_bad_arguments_before_any_launch(libgk):
         gk.GK_ERR_INVALID_ARG
     assert L.gk_partition_quality(P(rp), None, 2, 4, P(blk), 1, None, None, None, None) == \
         gk.GK_ERR_INVALID_ARG
+
+
+def test_diameter_rejects_bad_arguments_before_any_launch(libgk):
+    import paper_1805_01208_gb300 as gk
+    L = gk.lib()
+    assert ctypes.sizeof(gk.Diameter) == 32
+    rp = np.zeros(3, dtype=np.int64)
+    blk = np.zeros(2, dtype=np.int32)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    for args in ((None, None, 2, 0, P(blk), 1, 3), (P(rp), None, 2, 0, P(blk), 0, 3),
+                 (P(rp), None, 2, 4, P(blk), 1, 3), (P(rp), None, 2, 0, P(blk), 1, 0),
+                 (P(rp), None, 2, 0, P(blk), 1, 65), (P(rp), None, 0, 0, P(blk), 1, 3)):
+        assert L.gk_block_diameter(*args, None, None, None) == gk.GK_ERR_INVALID_ARG
 
 
 def test_set_allocator_needs_both_callbacks(libgk):

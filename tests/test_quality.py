@@ -256,11 +256,106 @@ def test_gpu_quality_rejects_malformed_input(gk):
     assert q["edge_cut"] == 1
 
 
+def _check_diam(gk, rp, col, block, k, sweeps=3, on_device=True):
+    args = (_dev(rp), _dev(col), _dev(block)) if on_device else (rp, col, block)
+    q, diam = gk.block_diameter(*args, k, sweeps)
+    ref = oq.block_diameter_sweeps(rp, col, block, k, sweeps)
+    assert np.array_equal(_np(diam), ref)
+    s = oq.diameter_summary(ref, np.bincount(block, minlength=k))
+    assert q["max_diameter"] == s["max_diameter"]
+    assert q["disconnected_blocks"] == s["disconnected_blocks"]
+    hm = s["harmonic_mean"]
+    if hm in (0.0, math.inf):
+        assert q["harmonic_mean"] == hm
+    else:  # a sum of k reciprocals in another order
+        assert math.isclose(q["harmonic_mean"], hm, rel_tol=1e-12)
+    assert q["bfs_levels"] >= sweeps * max(s["max_diameter"], 0) // 2
+    return q, _np(diam)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("on_device", [True, False])
+def test_gpu_diameter_hand_graphs(gk, on_device):
+    rp, col = _csr(8, [(i, (i + 1) % 8) for i in range(8)])
+    q, d = _check_diam(gk, rp, col, np.array([0, 0, 0, 0, 0, 0, 1, 1], dtype=np.int32), 3,
+                       on_device=on_device)
+    assert d.tolist() == [5, 1, 0]
+    rp, col = _csr(6, [(0, 1), (0, 2), (0, 3), (4, 4)])
+    q, d = _check_diam(gk, rp, col, np.array([0, 0, 0, 0, 1, 1], dtype=np.int32), 2,
+                       on_device=on_device)
+    assert d.tolist() == [2, -1] and q["disconnected_blocks"] == 1
+    q, d = _check_diam(gk, rp, col, np.zeros(6, dtype=np.int32), 1, sweeps=1, on_device=on_device)
+    assert d.tolist() == [-1] and q["harmonic_mean"] == math.inf
+
+
+@pytest.mark.gpu
+def test_gpu_diameter_exact_on_a_forest(gk):
+    rng = np.random.default_rng(21)
+    sizes = [1, 2, 50, 700, 3000, 9]
+    edges, off = [], 0
+    for m in sizes:
+        edges += [(a + off, b + off) for a, b in _tree(m, rng)]
+        off += m
+    perm = rng.permutation(off)
+    rp, col = _csr(off, [(int(perm[a]), int(perm[b])) for a, b in edges])
+    block = np.empty(off, dtype=np.int32)
+    block[perm] = np.repeat(np.arange(len(sizes)), sizes)
+    q, d = _check_diam(gk, rp, col, block, len(sizes), sweeps=2)
+    assert d.tolist() == oq.block_diameter_exact(rp, col, block, len(sizes)).tolist()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dims,k", [((40, 30, 20), 64), ((300, 200), 37)])
+@pytest.mark.parametrize("sweeps", [1, 3])
+def test_gpu_diameter_of_a_partition_on_lattice_meshes(gk, dims, k, sweeps):
+    x, rp, col = synth.lattice_mesh(dims, 5)
+    block, C, I, res = gk.partition(_dev(x), k, 0.03)
+    _check_diam(gk, rp, col, _np(block).astype(np.int32), k, sweeps)
+
+
+@pytest.mark.gpu
+def test_gpu_diameter_lattice_slabs_closed_form(gk):
+    nx, ny, nz, k = 24, 9, 7, 6
+    x, rp, col = synth.lattice_mesh((nx, ny, nz), 8)
+    block = _slabs(x, nx, k)
+    q, d = _check_diam(gk, rp, col, block, k)
+    assert d.tolist() == [3 + (ny - 1) + (nz - 1)] * k
+
+
+@pytest.mark.gpu
+def test_gpu_diameter_random_graph_and_random_blocks(gk):
+    rng = np.random.default_rng(10)
+    n, k = 5000, 40
+    e = rng.integers(0, n, (12_000, 2))
+    rp, col = _csr(n, [tuple(r) for r in e.tolist()])  # parallel edges and self-loops too
+    block = rng.integers(0, k, n).astype(np.int32)
+    q, d = _check_diam(gk, rp, col, block, k + 3)  # three empty blocks
+    assert q["disconnected_blocks"] > 0 and d[-3:].tolist() == [0, 0, 0]
+
+
+@pytest.mark.gpu
+def test_gpu_diameter_rejects_malformed_input(gk):
+    rp, col = _csr(4, [(0, 1), (1, 2), (2, 3)])
+    with pytest.raises(gk.GKError):
+        gk.block_diameter(_dev(rp), _dev(col), _dev(np.array([0, 0, 2, 1], dtype=np.int32)), 2)
+    bad_col = col.copy()
+    bad_col[2] = -3
+    with pytest.raises(gk.GKError):
+        gk.block_diameter(_dev(rp), _dev(bad_col), _dev(np.zeros(4, dtype=np.int32)), 1)
+    bad_rp = rp.copy()
+    bad_rp[1] = -1
+    with pytest.raises(gk.GKError):
+        gk.block_diameter(_dev(bad_rp), _dev(col), _dev(np.zeros(4, dtype=np.int32)), 1)
+    q, d = _check_diam(gk, rp, col, np.zeros(4, dtype=np.int32), 1)  # still usable
+    assert d.tolist() == [3]
+
+
 @pytest.mark.gpu
 @pytest.mark.slow
 def test_gpu_quality_full_size_mesh(gk):
     """A 3-D graded mesh of 8e6 vertices partitioned into 1024 blocks: the GPU measures
-    equal the oracle's, and balanced k-means cuts fewer edges than the curve split."""
+    (edge cut, communication volume, diameter bounds) equal the oracle's, and balanced
+    k-means cuts fewer edges than the curve split."""
     x, rp, col = synth.lattice_mesh((200, 200, 200), 6)
     k = 1024
     block, C, I, res = gk.partition(_dev(x), k, 0.03)
@@ -271,3 +366,5 @@ def test_gpu_quality_full_size_mesh(gk):
     sfc[_np(perm)] = (np.arange(n, dtype=np.int64) * k // n).astype(np.int32)
     qs = _check(gk, rp, col, sfc, k)
     assert q["edge_cut"] < qs["edge_cut"]
+    _check_diam(gk, rp, col, _np(block).astype(np.int32), k)
+    _check_diam(gk, rp, col, sfc, k)
