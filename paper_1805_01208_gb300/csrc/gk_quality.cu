@@ -13,30 +13,15 @@
 
 namespace gk {
 
-// One thread per vertex.  The distinct foreign blocks among a vertex's neighbours are
-// counted by checking, for each foreign neighbour, the neighbours stored before it
-// (quadratic in the degree; mesh degrees are small).  Malformed input (a row range
-// outside [0, nnz], a neighbour outside [0, n), a block id outside [0, k)) sets *bad and
-// the offending entries are skipped.
-__global__ void quality_vertex_kernel(const long long *row_ptr, const int *col, long long n,
-                                      long long nnz, const int *block, int k,
-                                      unsigned long long *ext, unsigned long long *comm,
-                                      unsigned long long *boundary, int *bad) {
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool ok = v < n;  // every lane stays to the warp vote at the end
-    int b = 0;
-    long long e0 = 0, e1 = 0;
-    if (ok) {
-        b = block[v];
-        e0 = row_ptr[v];
-        e1 = row_ptr[v + 1];
-        if ((unsigned)b >= (unsigned)k || e0 < 0 || e1 < e0 || e1 > nnz) {
-            atomicOr(bad, 1);
-            ok = false;
-        }
-    }
-    unsigned nf = 0, nd = 0;
-    for (long long e = e0; ok && e < e1; ++e) {
+// Foreign neighbours (nf) and distinct foreign blocks (nd) of vertex v of block b, one
+// thread alone: each foreign neighbour is checked against the neighbours stored before it
+// (quadratic in the degree).  Entries that are out of range set *bad and are skipped.
+__device__ void vertex_counts(const long long *row_ptr, const int *col, long long n,
+                              const int *block, int k, long long v, int b, long long e0,
+                              long long e1, unsigned &nf, unsigned &nd, int *bad) {
+    nf = 0;
+    nd = 0;
+    for (long long e = e0; e < e1; ++e) {
         const int u = col[e];
         if ((unsigned long long)(long long)u >= (unsigned long long)n) {
             atomicOr(bad, 1);
@@ -57,12 +42,106 @@ __global__ void quality_vertex_kernel(const long long *row_ptr, const int *col, 
         }
         if (!seen) ++nd;
     }
-    if (nf) {
+}
+
+constexpr int kQWarps = 8;    // warps per CTA of the quality kernel
+constexpr int kQCap = 512;    // adjacency entries of a warp's 32 vertices staged in shared memory
+
+// One warp per 32 consecutive vertices.  Their rows are one contiguous range of col; the
+// lanes walk it together (coalesced neighbour loads, independent block-id gathers), store
+// each entry's foreign block (-1: own block or self-loop) in shared memory, then count per
+// row the foreign entries and the first occurrences of each foreign block (the check
+// against the earlier entries of the row reads shared memory).  A warp whose rows hold
+// more than kQCap entries counts each vertex in its own thread instead.  Malformed input
+// (a row range outside [0, nnz], a neighbour outside [0, n), a block id outside [0, k))
+// sets *bad; a warp with a malformed row skips its counts (the call then fails).
+__global__ void __launch_bounds__(kQWarps * 32) quality_vertex_kernel(
+    const long long *row_ptr, const int *col, long long n, long long nnz, const int *block, int k,
+    unsigned long long *ext, unsigned long long *comm, unsigned long long *boundary, int *bad) {
+    __shared__ long long s_rp[kQWarps][33];
+    __shared__ int s_fb[kQWarps][kQCap];
+    __shared__ int s_b[kQWarps][32];
+    __shared__ unsigned s_nf[kQWarps][32], s_nd[kQWarps][32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long v0 = ((long long)blockIdx.x * kQWarps + w) * 32;
+    if (v0 >= n) return;  // the whole warp
+    const long long v = v0 + lane;
+    const bool has = v < n;
+    const int cnt = (int)min(32ll, n - v0);
+    int b = 0;
+    long long e0 = 0, e1 = 0;
+    bool ok = true;
+    if (has) {
+        b = block[v];
+        e0 = row_ptr[v];
+        e1 = row_ptr[v + 1];
+        if ((unsigned)b >= (unsigned)k || e0 < 0 || e1 < e0 || e1 > nnz) {
+            atomicOr(bad, 1);
+            ok = false;
+        }
+    }
+    if (!__all_sync(full, ok)) return;  // the whole warp
+    const long long Eend = __shfl_sync(full, e1, cnt - 1);
+    s_rp[w][lane] = has ? e0 : Eend;
+    if (lane == 0) s_rp[w][32] = Eend;
+    s_b[w][lane] = b;
+    s_nf[w][lane] = 0;
+    s_nd[w][lane] = 0;
+    __syncwarp();
+    const long long E0 = s_rp[w][0];
+    const long long m = Eend - E0;
+    unsigned nf = 0, nd = 0;
+    if (m > kQCap) {
+        if (has) vertex_counts(row_ptr, col, n, block, k, v, b, e0, e1, nf, nd, bad);
+    } else {
+        int *fb = s_fb[w];
+        const long long *rp = s_rp[w];
+        for (int i = lane; i < (int)m; i += 32) {
+            const long long e = E0 + i;
+            int lo = 0, hi = 32;  // the row of entry e: rp[lo] <= e < rp[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (rp[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            const int u = col[e];
+            int f = -1;
+            if ((unsigned long long)(long long)u >= (unsigned long long)n) {
+                atomicOr(bad, 1);
+            } else if (u != v0 + lo) {
+                const int bu = block[u];
+                if ((unsigned)bu >= (unsigned)k) atomicOr(bad, 1);
+                else if (bu != s_b[w][lo]) f = bu;
+            }
+            fb[i] = f;
+        }
+        __syncwarp();
+        for (int i = lane; i < (int)m; i += 32) {
+            const int f = fb[i];
+            if (f < 0) continue;
+            const long long e = E0 + i;
+            int lo = 0, hi = 32;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (rp[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            bool seen = false;
+            for (int j = (int)(rp[lo] - E0); j < i && !seen; ++j) seen = fb[j] == f;
+            atomicAdd(&s_nf[w][lo], 1u);
+            if (!seen) atomicAdd(&s_nd[w][lo], 1u);
+        }
+        __syncwarp();
+        nf = s_nf[w][lane];
+        nd = s_nd[w][lane];
+    }
+    if (has && nf) {
         atomicAdd(&ext[b], (unsigned long long)nf);
         atomicAdd(&comm[b], (unsigned long long)nd);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, nf != 0);  // boundary vertices of the warp
-    if ((threadIdx.x & 31) == 0 && m) atomicAdd(boundary, (unsigned long long)__popc(m));
+    const unsigned bm = __ballot_sync(full, has && nf != 0);  // boundary vertices of the warp
+    if (lane == 0 && bm) atomicAdd(boundary, (unsigned long long)__popc(bm));
 }
 
 // One CTA: sums and maxima over the k blocks -> out[0..3] = edge cut, total comm,
@@ -117,8 +196,8 @@ cudaError_t launch_quality(const long long *row_ptr, const int *col, long long n
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (n > 0)
-        quality_vertex_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(row_ptr, col, n, nnz, block, k,
-                                                                          ext, comm, out + 4, bad);
+        quality_vertex_kernel<<<(unsigned)((n + kQWarps * 32 - 1) / (kQWarps * 32)), kQWarps * 32, 0,
+                                s>>>(row_ptr, col, n, nnz, block, k, ext, comm, out + 4, bad);
     quality_final_kernel<<<1, 256, 0, s>>>(ext, comm, k, out);
     return cudaGetLastError();
 }
