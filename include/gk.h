@@ -363,10 +363,13 @@ gk_status gk_set_allocator(gk_alloc_fn alloc, gk_free_fn free_fn, void *ctx);
  * 1 <= k <= GK_NOALLOC_MAX_K (larger k: GK_ERR_INVALID_ARG).  The first call on a
  * device looks up the array's device address (set-up); make that first call before
  * any stream capture.  Every call reuses the array and clears it first; calls whose
- * GPU work overlaps (other streams, other host threads) race on it.
+ * GPU work overlaps (other streams, other host threads) race on it.  The call waits
+ * for its stream before it returns (it reads the input check and beta back).
  *   coords, weights (nullable), block, centers, centers_out, delta_out (nullable):
- *   device memory of the current device; beta_out (nullable): host or device.
- *   Block ids outside [0, k) give GK_ERR_INVALID_ARG.
+ *   device memory of the current device; beta_out (nullable): host memory or device
+ *   memory of the current device (written by a copy on the stream).
+ *   Block ids outside [0, k), a coordinate that is not finite and a weight that is not
+ *   finite and > 0 give GK_ERR_INVALID_ARG (found on the device; outputs unspecified).
  */
 gk_status gk_move_centers_noalloc(const void *coords, int32_t dtype, const void *weights,
                                   int64_t n, int32_t d, int32_t k, const int32_t *block,

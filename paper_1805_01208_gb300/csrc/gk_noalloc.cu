@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "../../include/gk.h"
 #include "gk_common.cuh"
 
@@ -34,7 +36,8 @@ struct NAScratch {
     unsigned long long maxd_key;  // ordered key of the largest movement
     unsigned int done;            // last-block-done counter
     int nonempty;
-    int bad;
+    int bad;      // bit 0: a block id outside [0, k); bit 1: a non-finite coordinate or a
+                  // weight that is not finite and > 0
     int pad;
     double beta;
     double part[(kNoAllocMaxK + kNAKThreads - 1) / kNAKThreads];
@@ -88,14 +91,27 @@ __global__ void na_clear_kernel(NAScratch *s, int k, int d) {
     }
 }
 
+// Largest |x| and largest w, and a check of the input: every coordinate finite, every
+// weight finite and > 0 (as the allocating path requires).  A bad value sets bit 1 of
+// s->bad; the accumulation then does nothing and the call reports GK_ERR_INVALID_ARG.
 template <typename T>
 __global__ void na_range_kernel(const T *x, const T *w, long long n, int d, NAScratch *s) {
     double xm = 0.0, wm = 0.0;
+    bool badv = false;
     long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        for (int j = 0; j < d; ++j) xm = fmax(xm, fabs((double)x[i * d + j]));
-        if (w) wm = fmax(wm, (double)w[i]);
+        for (int j = 0; j < d; ++j) {
+            const double v = (double)x[i * d + j];
+            badv |= !isfinite(v);
+            xm = fmax(xm, fabs(v));
+        }
+        if (w) {
+            const double v = (double)w[i];
+            badv |= !(v > 0.0 && isfinite(v));
+            wm = fmax(wm, v);
+        }
     }
+    if (__any_sync(0xffffffffu, badv) && (threadIdx.x & 31) == 0) atomicOr(&s->bad, 2);
     for (int off = 16; off; off >>= 1) {
         xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, off));
         wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, off));
@@ -121,6 +137,7 @@ __global__ void __launch_bounds__(kNAThreads) na_accum_kernel(const T *x, const 
                                                               NAScratch *s) {
     const int lane = threadIdx.x & 31;
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s->bad & 2) return;  // rejected input (the range kernel ran before on this stream)
     int Fw, Fx;
     na_scales(s, w != nullptr, Fw, Fx);
     int b = i < n ? block[i] : -1;
@@ -264,9 +281,11 @@ __global__ void __launch_bounds__(kNAKThreads) na_finalize_kernel(NAScratch *s, 
     }
 }
 
-// Device address of the scratch, looked up once per device (set-up on first use).
+// Device address of the scratch, looked up once per device (set-up on first use).  The
+// entries are atomic: host threads may look them up concurrently (they all store the
+// same value).
 constexpr int kMaxDevices = 64;
-void *g_na_ptr[kMaxDevices] = {nullptr};
+std::atomic<void *> g_na_ptr[kMaxDevices];
 
 gk_status na_scratch_ptr(NAScratch **out) {
     int dev = 0;
@@ -275,16 +294,16 @@ gk_status na_scratch_ptr(NAScratch **out) {
         return GK_ERR_CUDA;
     }
     if (dev < 0 || dev >= kMaxDevices) return GK_ERR_CUDA;
-    if (!g_na_ptr[dev]) {
-        void *ptr = nullptr;
+    void *ptr = g_na_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
             cudaGetLastError();
             return GK_ERR_CUDA;
         }
-        g_na_ptr[dev] = ptr;
+        g_na_ptr[dev].store(ptr, std::memory_order_release);
     }
-    *out = (NAScratch *)g_na_ptr[dev];
+    *out = (NAScratch *)ptr;
     return GK_OK;
 }
 
@@ -357,6 +376,17 @@ extern "C" gk_status gk_move_centers_noalloc(const void *coords, int32_t dtype, 
         return GK_ERR_CUDA;
     }
     if (bad) return GK_ERR_INVALID_ARG;
-    if (beta_out) *beta_out = beta;
+    if (beta_out) {
+        if (on_device(beta_out, dev)) {  // device memory: a copy on the stream
+            if (cudaMemcpyAsync(beta_out, &s->beta, sizeof(double), cudaMemcpyDeviceToDevice, cs) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(cs) != cudaSuccess) {
+                cudaGetLastError();
+                return GK_ERR_CUDA;
+            }
+        } else {
+            *beta_out = beta;
+        }
+    }
     return GK_OK;
 }
