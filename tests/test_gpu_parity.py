@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 THREADS = max(1, min(16, os.cpu_count() or 1))
 TIE = 1e-12
+FP32_FORM_MAX_DISAGREEMENT = 1e-4  # FP32 form: fraction assigned differently from the FP64 argmin
 
 
 @pytest.fixture(scope="module")
@@ -414,9 +415,6 @@ def test_full_size_gmm3d_1e7_k1024(gk):
 # same box), the balance bound exactly on the host, the FP32-form disagreement with the
 # FP64 argmin under the returned state, and the centers of the returned assignment.
 # ----------------------------------------------------------------------------------------
-FP32_FORM_MAX_DISAGREEMENT = 1e-4
-
-
 def _full_size_fp32_form(gk, name, nsample):
     import torch
     x, w, spec = synth.workload(name, threads=THREADS)
@@ -463,6 +461,9 @@ def test_full_size_spots2d_1e9_k16384_fp32_form(gk):
     ("uniform", 2, "f64", 30_000, 2500, "f64", False),
 ])
 def test_bounds_give_identical_results(gk, shape, d, dtype, n, k, assign, weighted):
+    """With bounds the partition is the oracle's (FP64 argmin: the free-running oracle
+    trajectory exactly; FP32 form: the stated disagreement with the FP64 argmin under the
+    returned state and the balance bound), and bit for bit the partition without them."""
     x = _points(shape, n, d, 59, dtype)
     w = synth.uniform_weights(n, 59, dtype=x.dtype) if weighted else None
     out = []
@@ -472,6 +473,16 @@ def test_bounds_give_identical_results(gk, shape, d, dtype, n, k, assign, weight
                                         options=o)
         out.append((_np(block), _np(C), _np(I), res))
     (b1, C1, I1, r1), (b0, C0, I0, r0) = out
+    if assign == "f64":
+        ref = oracle.partition(x, None if w is None else w.astype(np.float64), k, 0.03,
+                               oracle.default_options(threads=THREADS))
+        _check_free_running(x, w, k, 0.03, b1, C1, I1, r1, ref)
+    else:
+        wd = None if w is None else w.astype(np.float64)
+        S, W = oracle.block_weights(b1, wd, k)
+        assert r1["balanced"] == 1 and S.max() <= 1.03 * math.ceil(W / k) * (1 + 1e-15)
+        A_ref, _, _ = oracle.assign(x.astype(np.float64), C1, I1, threads=THREADS)
+        assert (b1 != A_ref).mean() <= FP32_FORM_MAX_DISAGREEMENT
     assert np.array_equal(b1, b0)
     assert np.array_equal(C1, C0) and np.array_equal(I1, I0)
     assert r1["balance_passes"] == r0["balance_passes"] and r1["iterations"] == r0["iterations"]
@@ -491,6 +502,10 @@ def test_bounds_over_many_passes_wrap_to_fresh_passes(gk):
         out.append((_np(block), _np(C), _np(I), res))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
     assert out[0][3]["balance_passes"] == out[1][3]["balance_passes"] > 64
+    ref = oracle.partition(x, None, 37, 0.0, oracle.default_options(
+        threads=THREADS, max_iter=2, max_balance_iter=150, final_balance_iter=150))
+    b1, C1, I1, r1 = out[0]
+    _check_free_running(x, None, 37, 0.0, b1, C1, I1, r1, ref)
 
 
 # ----------------------------------------------------------------------------------------

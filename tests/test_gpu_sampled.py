@@ -211,6 +211,8 @@ def test_full_size_sampled_gmm3d_1e7_k1024(gk):
 
 
 def test_sampled_with_bounds_is_identical(gk):
+    """Random initialization with bounds: the oracle's trajectory exactly, and bit for
+    bit the run without bounds."""
     x = synth.make_points("gmm", 80_000, 3, 103, "f64")
     order = synth.random_order(len(x), 103)
     out = []
@@ -218,6 +220,16 @@ def test_sampled_with_bounds_is_identical(gk):
         block, C, I, res = gk.partition_sampled(_dev(x), 40, 0.03, _dev(order), 2000,
                                                 options=gk.default_options(bounds=bounds))
         out.append((_np(block), _np(C), _np(I), res))
+    ref = oracle.partition_sampled(x, None, 40, 0.03, order, 2000,
+                                   oracle.default_options(threads=THREADS))
+    b1, C1, I1, r1 = out[0]
+    rr = ref["result"]
+    assert r1["status"] == rr["status"] and r1["balanced"] == rr["balanced"]
+    assert np.array_equal(b1, ref["A"])
+    assert r1["iterations"] == rr["iterations"] and r1["balance_passes"] == rr["balance_passes"]
+    ext = float((x.max(0) - x.min(0)).max())
+    assert np.abs(C1 - ref["C"]).max() <= 1e-10 * ext
+    assert np.allclose(I1, ref["I"], rtol=1e-12, atol=0)
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][2], out[1][2])
     assert out[0][3]["balance_passes"] == out[1][3]["balance_passes"]
