@@ -4,16 +4,26 @@
 One step = one gk_partition call on the device-resident workload: Hilbert bootstrap
 (bounding box, keys, radix sort, gather, initial centers), the balanced k-means loop
 (assignment passes with influence updates, center movement, erosion) and the scatter of
-block ids to input order.  Default workload: 3D Gaussian mixture, n = 1e7, k = 1024,
-eps = 0.03, FP64 points and FP64 assignment.
+block ids to input order.  Default workload (the largest one-GPU configuration): 2D,
+n = 1e9, uniform background plus 256 Gaussian refinement spots, FP32 coordinates,
+unit weights, k = 16384, eps = 0.03, FP32 assignment with FP64 block weights, centroids
+and influence.
 
 Prints one JSON line (rank 0):
-  value      points processed per second by the balanced k-means iterations of the whole
-             job: sum over steps of n * (assignment passes) / sum of step times (bootstrap
-             and movement time included in the denominator)
-  e2e        the same through the C ABI with pinned host buffers (copies in the region)
-  roofline   the assignment kernel: algorithmic bytes per launch / mean launch time
-  cpu_baseline  the FP64 oracle's balance pass on a bounded sample, host cores
+  value        points processed per second by the balanced k-means iterations of the
+               whole job: sum over steps of n * (assignment passes) / sum of step times
+               (bootstrap and movement time included in the denominator)
+  e2e          the same through the C ABI with pinned host buffers (copies in the region)
+  roofline     the assignment kernel: algorithmic bytes per launch / mean launch time
+  fp32_form    the FP32 form's statistics: fraction of points assigned differently from
+               the FP64 argmin under the returned centers and influence (all points), the
+               largest error of the centroid step against FP64 means, the exact imbalance
+               (block sizes counted on the host)
+  fp64_form    the FP64 argmin (certified FP32 search + FP64 re-decision) on the same
+               points, and the FP32 form's speedup over it
+  legs         the other workloads (3D mixture n = 1e7 k = 1024 FP64; 2D radial n = 1e8
+               k = 4096 FP32; 64 batched instances), each with its own roofline
+  cpu_baseline the FP64 oracle's balance pass on a uniform sample, host cores
 
 --impl reference times the oracle (the slow FP64 CPU restatement) on the same metric.
 --gpus N > 1 runs N independent replicas (one per rank, weak scaling).
@@ -38,7 +48,10 @@ if ROOT not in sys.path:
 
 METRIC = "points/s per balanced k-means iter and partition time (s), FP32 vs FP64, 1 GB300"
 UNIT = "points/s"
-DEFAULT_WORKLOAD = "gmm3d_1e7_k1024_f64"
+DEFAULT_WORKLOAD = "spots2d_1e9_k16384_f32"
+BATCHED_WORKLOAD = "batched64_f32"
+EXTRA_LEGS = ("gmm3d_1e7_k1024_f64", "radial2d_1e8_k4096_f32", BATCHED_WORKLOAD)
+FLUSH_BYTES = 512 << 20  # written between timed steps: evicts the 129 MB L2
 
 
 def _args():
@@ -51,8 +64,11 @@ def _args():
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
     ap.add_argument("--assign", default=None, choices=["f32", "f64"],
                     help="override the workload's assignment precision")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="CPU time budget of one oracle pass of the cpu_baseline")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other workloads (3D mixture, 2D radial, batched)")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sampled", action="store_true",
                     help="skip the partition with random initialization (Section 4.5)")
@@ -128,7 +144,7 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------------------
-# CPU baseline: the oracle's balance pass (assign + block weights + influence update)
+# replicas (N > 1) and the CPU baseline
 # --------------------------------------------------------------------------------------
 def replica_points(spec, rank: int):
     """Points of rank's independent replica of a workload (rank 0: the workload itself)."""
@@ -147,66 +163,121 @@ def reduce_over_ranks(total_ms: float, work: float, dist, device):
     return float(t.item()), float(w.item())
 
 
-def cpu_baseline(x, w, spec, seconds: float):
+def _oracle_pass(xs, ws, C, I, spec, cores):
+    """One FP64 balance pass of the oracle (brute-force assignment over all k centers with
+    OpenMP on `cores` threads, block weights, influence update); returns its time in s."""
     import oracle
-    cores = len(os.sched_getaffinity(0))
-    k = spec["k"]
-    m = int(min(len(x), max(4 * k, 2_000_000_000 // (k * 150))))
-    rng = np.random.default_rng(12345)
-    idx = np.sort(rng.choice(len(x), m, replace=False))
+    t0 = time.perf_counter()
+    A, _, _ = oracle.assign(xs, C, I, threads=cores)
+    S, W = oracle.block_weights(A, ws, spec["k"])
+    oracle.balance_update(S, W, spec["k"], spec["d"], spec["eps"], I)
+    return time.perf_counter() - t0
+
+
+def _oracle_sample(x, w, m, seed=12345):
+    """A uniform sample of m of the points, curve-sorted, with its curve centers."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    n = len(x)
+    idx = np.sort(rng.choice(n, m, replace=False)) if m < n else np.arange(n)
     xs = np.ascontiguousarray(x[idx], dtype=np.float64)
     ws = None if w is None else np.ascontiguousarray(w[idx], dtype=np.float64)
-    xs = xs[oracle.sort_keys(oracle.hilbert_keys(xs))]
+    order = oracle.sort_keys(oracle.hilbert_keys(xs))
+    xs = xs[order]
+    ws = None if ws is None else ws[order]
+    return xs, ws
+
+
+def _sample_size(x, w, spec, seconds, cores):
+    """Points of the sample whose oracle pass takes about `seconds` (calibrated on a small
+    sample; the pass is O(points x k)), at most 1% of the workload above 1e8 points and
+    all of a smaller one."""
+    import oracle
+    n, k = len(x), spec["k"]
+    cap = n // 100 if n >= 100_000_000 else n
+    mc = int(min(cap, max(4 * k, 2_000_000_000 // (k * 400))))
+    xs, ws = _oracle_sample(x, w, mc, seed=777)
+    C = oracle.sfc_centers(xs, k)
+    t = _oracle_pass(xs, ws, C, np.ones(k), spec, cores)
+    per_point = t / mc
+    return int(max(min(cap, seconds / per_point), min(cap, 4 * k)))
+
+
+def cpu_baseline(x, w, spec, seconds: float, m: int | None = None, passes: int = 1):
+    """The oracle's FP64 balance pass on a uniform sample of the workload, sized to about
+    `seconds` per pass (1% of the points for the 1e9-point workload when that fits);
+    reported per point, with the full pass extrapolated from it."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    n, k = len(x), spec["k"]
+    if m is None:
+        m = _sample_size(x, w, spec, seconds, cores)
+    xs, ws = _oracle_sample(x, w, m)
     C = oracle.sfc_centers(xs, k)
     I = np.ones(k)
-    times = []
-    t_end = time.perf_counter() + seconds
-    while True:
-        t0 = time.perf_counter()
-        A, _, _ = oracle.assign(xs, C, I, threads=cores)
-        S, W = oracle.block_weights(A, ws, k)
-        bal, I, _ = oracle.balance_update(S, W, k, spec["d"], spec["eps"], I)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() > t_end and len(times) >= 2:
-            break
+    times = [_oracle_pass(xs, ws, C, I, spec, cores) for _ in range(passes)]
     t = float(np.mean(times))
+    frac = m / n
     return {"value": m / t, "unit": UNIT, "cores": cores, "kind": "oracle", "ms_per_pass": 1e3 * t,
-            "sample": (f"{m} of the workload's points (uniform sample, curve-sorted), k={k}: "
-                       f"one FP64 balance pass (brute-force assignment over all k with "
-                       f"{cores} OpenMP threads, block weights, influence update), "
-                       f"mean of {len(times)} passes")}
+            "sample_points": m, "sample_fraction": frac,
+            "full_pass_s_extrapolated": t * n / m,
+            "sample": (f"{m} of the workload's {n} points ({100 * frac:.3g}%, uniform sample, "
+                       f"curve-sorted), k={k}: one FP64 balance pass (brute-force assignment over "
+                       f"all k with {cores} OpenMP threads, block weights, influence update), "
+                       f"mean of {len(times)} pass(es); a full pass extrapolated x{n / m:.4g} "
+                       f"(extrapolated, not measured): {t * n / m:.1f} s")}
 
 
 def run_reference(args):
+    """The oracle on the headline workload's metric: every step one FP64 balance pass on
+    a bounded uniform sample of the workload's distribution (the generator's first points:
+    independent draws of the same distribution), sized so the whole run takes about two
+    minutes on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     from paper_1805_01208_gb300 import synth
-    x, w, spec = synth.workload(args.workload, n=args.n)
+    spec0 = dict(synth.WORKLOADS[args.workload]) if args.workload in synth.WORKLOADS else None
+    if spec0 is None:  # the batched workload: its largest instance stands in
+        return _reference_unavailable(args, "the batched workload has no single-config oracle arm")
+    n_full = args.n or spec0["n"]
     cores = len(os.sched_getaffinity(0))
+    probe_n = int(min(n_full, 4_000_000))
+    x, w, spec = synth.workload(args.workload, n=probe_n)
+    budget = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    m = min(probe_n, _sample_size(x, w, spec, budget, cores))
     for _ in range(args.warmup):
-        cpu_baseline(x, w, spec, 0.0)
-    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps)))
-    vals = [cpu_baseline(x, w, spec, per_step) for _ in range(args.steps)]
+        cpu_baseline(x, w, spec, 0.0, m=max(spec["k"], m // 10))
+    vals = [cpu_baseline(x, w, spec, 0.0, m=m) for _ in range(args.steps)]
     value = float(np.mean([v["value"] for v in vals]))
     ms = float(np.mean([v["ms_per_pass"] for v in vals]))
+    spec["n"] = n_full
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": _config(spec, args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+                             "sample": (f"{m} points drawn from the workload's distribution "
+                                        f"(the generator's first points) per step, k="
+                                        f"{spec['k']}: one FP64 balance pass (brute-force "
+                                        f"assignment with {cores} OpenMP threads, block "
+                                        f"weights, influence update)")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
+def _reference_unavailable(args, why):
+    print(json.dumps({"impl": "reference", "unavailable": why}), flush=True)
+    return 0
+
+
 def _config(spec, args):
     return {"workload": args.workload, "n": spec["n"], "d": spec["d"], "k": spec["k"],
             "eps": spec["eps"], "points": spec["dtype"], "assign": spec["assign"],
-            "weights": "uniform[1,10]" if spec["weighted"] else "unit",
+            "reductions": "f64", "weights": "uniform[1,10]" if spec["weighted"] else "unit",
             "l2": "inputs larger than L2 and a 512 MB write between timed steps",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single"}
 
@@ -214,7 +285,202 @@ def _config(spec, args):
 # --------------------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------------------
-BATCHED_WORKLOAD = "batched64_f32"
+def _timed(stream, flush, fn, steps):
+    """(times in ms, results) of `steps` calls of fn, each bracketed by CUDA events on the
+    library's stream, the L2 flushed before each (outside the events)."""
+    import torch
+    times, outs = [], []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        outs.append(out)
+    return times, outs
+
+
+def _roofline(gk, xt, wt, spec, workload):
+    """The assignment kernel's HBM roofline: algorithmic bytes of one balance pass (every
+    point's coordinates and weight read once) over the mean CUDA-event duration of its
+    launches in a host-driven run of the same partition (events on the library's stream)."""
+    n, d, k = int(xt.shape[0]), spec["d"], spec["k"]
+    timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1)
+    _, _, _, tres = gk.partition(xt, k, spec["eps"], weights=wt, options=timed)
+    ev_avg = tres["time_assign_ms"] / max(1, tres["assign_launches"])
+    es = 8 if spec["dtype"] == "f64" else 4
+    sw = es if spec["weighted"] else 0
+    bytes_per_launch = n * (d * es + sw)
+    # what the assignment kernel itself streams: FP32 frame coordinates, 16-bit block ids
+    # (k <= 65535), weights
+    kernel_bytes = n * (d * 4 + (2 if k <= 65535 else 4) + sw)
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "assign_kernel",
+            "bytes_per_launch": bytes_per_launch, "kernel_stream_bytes_per_launch": kernel_bytes,
+            "kernel_stream_frac": kernel_bytes / (ev_avg * 1e-3) / 1e9 / peak,
+            "launch_ms_events": ev_avg, "peak_source": peak_kind,
+            "other_kernels_ms_per_pass": {
+                "filter": tres["time_filter_ms"] / max(1, tres["filter_launches"]),
+                "balance": tres["time_balance_ms"] / max(1, tres["balance_launches"]),
+                "move_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])},
+            "pass_ms_events": (tres["time_assign_ms"] + tres["time_filter_ms"]
+                               + tres["time_balance_ms"]) / max(1, tres["assign_launches"])}
+    roof["pass_frac"] = bytes_per_launch / (roof["pass_ms_events"] * 1e-3) / 1e9 / peak
+    _attach_traffic(roof, workload)
+    return roof
+
+
+def _exact_imbalance(block_host, w_host, k, eps):
+    """Block sizes counted on the host from the returned block ids (exact integers for
+    unit weights), the largest over ceil(W/k) minus 1, and whether it meets eps."""
+    import torch
+    if w_host is None:
+        S = torch.bincount(torch.from_numpy(block_host), minlength=k).numpy()
+        W = float(len(block_host))
+    else:
+        S = np.bincount(block_host, weights=w_host.astype(np.float64), minlength=k)
+        W = float(w_host.astype(np.float64).sum())
+    ceil_avg = math.ceil(W / k)
+    return {"max_block": float(S.max()), "ceil_avg": ceil_avg,
+            "max_imbalance": float(S.max()) / ceil_avg - 1.0,
+            "meets_eps": bool(S.max() <= (1 + eps) * ceil_avg * (1 + 1e-15)),
+            "counted": "on the host from the returned block ids"}
+
+
+def _fp32_stats(gk, xt, wt, spec, block, C, I, block_host, w_host):
+    """The FP32 form's stated figures under the returned centers and influence.
+    disagreement: fraction of all points whose block differs from the FP64 argmin of the
+      effective distance (the library's certified FP64 assignment, parity-tested against
+      the oracle), on the curve-sorted points;
+    center_error: largest |centroid step - FP64 weighted mean| over the blocks of the
+      returned assignment (library: exact fixed-point sums; reference: plain FP64 sums with
+      torch), relative to the bounding-box extent;
+    imbalance: block sizes counted on the host."""
+    import torch
+    n, d, k = int(xt.shape[0]), spec["d"], spec["k"]
+    perm, _ = gk.sfc_init(xt, k)
+    As = block.index_select(0, perm)
+    xs = xt.index_select(0, perm)
+    A64, _ = gk.assign(xs, C, I, assign_dtype="f64")
+    differ = int((As != A64).sum().item())
+    del xs, As, A64, perm
+    ext = float((xt.amax(0).double() - xt.amin(0).double()).max().item())
+    Cm, _, _ = gk.move_centers(xt, block, C, weights=wt)
+    sums = torch.zeros((k, d), dtype=torch.float64, device=xt.device)
+    cnt = torch.zeros(k, dtype=torch.float64, device=xt.device)
+    chunk = 1 << 26
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        b = block[s:e].long()
+        wv = torch.ones(e - s, dtype=torch.float64, device=xt.device) if wt is None else wt[s:e].double()
+        sums.index_add_(0, b, xt[s:e].double() * wv[:, None])
+        cnt.index_add_(0, b, wv)
+    ne = cnt > 0
+    mean = sums[ne] / cnt[ne][:, None]
+    cerr = float((Cm[ne] - mean).abs().max().item()) / ext
+    out = {"disagreement": differ / n, "disagreeing_points": differ, "points_checked": n,
+           "disagreement_reference": "FP64 argmin under the returned centers and influence "
+                                     "(gk_assign in FP64 mode), every point",
+           "center_error": cerr,
+           "center_error_reference": "FP64 weighted means of the returned assignment (torch "
+                                     "FP64 sums), relative to the bounding-box extent"}
+    out.update(_exact_imbalance(block_host, w_host, k, spec["eps"]))
+    return out
+
+
+def _config_leg(gk, name, stream, flush, steps, x=None, w=None, spec=None):
+    """One workload as a leg of the line: partition time and points/s over `steps` timed
+    calls, its assignment kernel's roofline and, for the FP32 form, its statistics."""
+    import torch
+    from paper_1805_01208_gb300 import synth
+    if name == BATCHED_WORKLOAD:
+        return _batched_leg(gk, stream, flush, steps)
+    if x is None:
+        x, w, spec = synth.workload(name)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    xt = torch.from_numpy(x).to(dev)
+    wt = None if w is None else torch.from_numpy(w).to(dev)
+    n, k, eps = len(x), spec["k"], spec["eps"]
+    opts = gk.default_options(assign_dtype=spec["assign"])
+
+    def step():
+        return gk.partition(xt, k, eps, weights=wt, options=opts)
+
+    step()
+    torch.cuda.synchronize()
+    times, outs = _timed(stream, flush, step, steps)
+    res = outs[-1][3]
+    leg = {"workload": name, "n": n, "d": spec["d"], "k": k, "points": spec["dtype"],
+           "assign": spec["assign"], "weights": "uniform[1,10]" if spec["weighted"] else "unit",
+           "value": sum(n * o[3]["balance_passes"] for o in outs) / (sum(times) * 1e-3),
+           "unit": UNIT, "ms_per_step": float(np.mean(times)), "steps": steps,
+           "balance_passes": res["balance_passes"], "iterations": res["iterations"],
+           "balanced": res["balanced"], "max_imbalance": res["max_imbalance"],
+           "bootstrap_ms": res["time_bootstrap_ms"], "avg_candidates": res["avg_candidates"],
+           "assign_ms_per_pass_live": res["assign_live_ms"] / max(1, res["assign_live_launches"]),
+           "roofline": _roofline(gk, xt, wt, spec, name)}
+    if spec["assign"] == "f32":
+        block, C, I, _ = outs[-1]
+        leg["fp32_form"] = _fp32_stats(gk, xt, wt, spec, block, C, I, block.cpu().numpy(), w)
+    del xt, wt, outs
+    gk.release()
+    torch.cuda.empty_cache()
+    return leg
+
+
+def _batched_leg(gk, stream, flush, steps, rank=0):
+    """64 instances of mixed n, d, k with weights, FP32 form, one gk_partition_batched call
+    per step (one graph launch for all k-means loops); per instance the FP32-form
+    disagreement (all points) and the exact imbalance."""
+    import torch
+    from paper_1805_01208_gb300 import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = synth.batched_instances(64, seed=4 + 1000 * rank)
+    host = [synth.instance_data(sp) for sp in specs]
+    xs = [torch.from_numpy(x).to(dev) for x, _ in host]
+    ws = [torch.from_numpy(w).to(dev) if w is not None else None for _, w in host]
+    probs = [(xs[i], sp["k"], sp["eps"], ws[i]) for i, sp in enumerate(specs)]
+    opts = gk.default_options(assign_dtype="f32")
+    gk.partition_batched(probs, options=opts)
+    torch.cuda.synchronize()
+    times, outs = _timed(stream, flush, lambda: gk.partition_batched(probs, options=opts)[0], steps)
+    last = outs[-1]
+    res = [r for _, _, _, r in last]
+    pp = sum(sum(sp["n"] * r["balance_passes"] for sp, (_, _, _, r) in zip(specs, o)) for o in outs)
+    ntot = sum(sp["n"] for sp in specs)
+    dis, imb, meets = [], [], 0
+    for i, (sp, (b, C, I, r)) in enumerate(zip(specs, last)):
+        perm, _ = gk.sfc_init(xs[i], sp["k"])
+        A64, _ = gk.assign(xs[i].index_select(0, perm), C, I, assign_dtype="f64")
+        dis.append(int((b.index_select(0, perm) != A64).sum().item()) / sp["n"])
+        e = _exact_imbalance(b.cpu().numpy(), host[i][1], sp["k"], sp["eps"])
+        imb.append(e["max_imbalance"])
+        meets += int(e["meets_eps"])
+    leg = {"workload": BATCHED_WORKLOAD, "instances": len(specs), "points": ntot,
+           "n_range": [min(sp["n"] for sp in specs), max(sp["n"] for sp in specs)],
+           "k_range": [min(sp["k"] for sp in specs), max(sp["k"] for sp in specs)],
+           "weights": "uniform[1,10]", "assign": "f32",
+           "value": pp / (sum(times) * 1e-3), "unit": UNIT, "ms_per_step": float(np.mean(times)),
+           "steps": steps, "balance_passes_total": int(sum(r["balance_passes"] for r in res)),
+           "balance_passes_max": int(max(r["balance_passes"] for r in res)),
+           "balanced_instances": int(sum(r["balanced"] for r in res)),
+           "bootstrap_ms": res[0]["time_bootstrap_ms"],
+           "kernel_launches_per_step": int(sum(r["kernel_launches"] for r in res)),
+           "fp32_form": {"disagreement_max": max(dis), "disagreement_mean": float(np.mean(dis)),
+                         "disagreement_reference": "FP64 argmin under each instance's returned "
+                                                   "state (gk_assign FP64), every point",
+                         "max_imbalance_per_instance": imb,
+                         "instances_meeting_eps": meets,
+                         "counted": "block weights summed on the host from the returned ids"}}
+    del xs, ws, probs, outs, last
+    gk.release()
+    torch.cuda.empty_cache()
+    return leg, host, specs
 
 
 def main():
@@ -249,30 +515,21 @@ def main():
     wt = None if w is None else torch.from_numpy(w).to(dev)
     opts = gk.default_options(assign_dtype=spec["assign"])
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step(options):
+    def step(options=opts):
         return gk.partition(xt, k, eps, weights=wt, options=options)
 
     for _ in range(args.warmup):
-        step(opts)
+        step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    times, results = [], []
-    for _ in range(args.steps):
-        flush.fill_(1)  # evict L2 between timed steps (outside the events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, _, res = step(opts)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        results.append(res)
+    times, outs = _timed(stream, flush, step, args.steps)
     clk = clocks.stop()
+    results = [o[3] for o in outs]
     torch.cuda.synchronize()
     total_ms = float(sum(times))
     points_passes = float(sum(n * r["balance_passes"] for r in results))
@@ -281,74 +538,73 @@ def main():
     value = points_passes / (total_ms * 1e-3)
     ms_per_step = total_ms / args.steps
     launches = int(sum(r["kernel_launches"] for r in results))
+    block, C, I, last = outs[-1]
+    block_host = block.cpu().numpy()
+    del outs
 
     # ---- end to end through the C ABI with pinned host buffers -------------------------
     e2e = _e2e(gk, x, w, spec, opts, stream, max(1, min(3, args.steps)))
 
     # ---- roofline of the assignment kernel ---------------------------------------------
+    roof = _roofline(gk, xt, wt, spec, args.workload)
     live_ms = sum(r["assign_live_ms"] for r in results)
     live_n = sum(r["assign_live_launches"] for r in results)
-    timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1)
-    _, _, _, tres = step(timed)
-    ev_avg = tres["time_assign_ms"] / max(1, tres["assign_launches"])
-    es = 8 if spec["dtype"] == "f64" else 4
-    sw = es if spec["weighted"] else 0
-    # algorithmic bytes of one balance pass: every point's coordinates (and weight) read
-    # once; writing the block ids is not counted (only the last pass of a loop needs it)
-    bytes_per_launch = n * (d * es + sw)
-    # what this assignment kernel itself streams: FP32 frame coordinates, block ids (16
-    # bits when k <= 65535)
-    kernel_bytes = n * (d * 4 + (2 if k <= 65535 else 4) + sw)
-    peak, peak_kind = _peaks()
-    achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "assign_kernel",
-            "bytes_per_launch": bytes_per_launch, "kernel_stream_bytes_per_launch": kernel_bytes,
-            "kernel_stream_frac": kernel_bytes / (ev_avg * 1e-3) / 1e9 / peak,
-            "launch_ms_events": ev_avg,
-            "launch_ms_live_graph": live_ms / max(1, live_n), "peak_source": peak_kind,
-            "other_kernels_ms_per_pass": {
-                "filter": tres["time_filter_ms"] / max(1, tres["filter_launches"]),
-                "balance": tres["time_balance_ms"] / max(1, tres["balance_launches"]),
-                "move_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])}}
-    _attach_traffic(roof, args.workload)
+    roof["launch_ms_live_graph"] = live_ms / max(1, live_n)
 
-    # ---- FP32 form on the same data ------------------------------------------------------
+    # ---- FP32-form statistics under the returned state ----------------------------------
     fp32 = None
-    if not args.no_fp32_compare and spec["assign"] == "f64":
-        o32 = gk.default_options(assign_dtype="f32")
-        step(o32)
-        t32, r32 = [], []
-        for _ in range(max(1, min(2, args.steps))):
-            flush.fill_(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, _, _, res = step(o32)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t32.append(e0.elapsed_time(e1))
-            r32.append(res)
-        v32 = sum(n * r["balance_passes"] for r in r32) / (sum(t32) * 1e-3)
-        fp64_pass = live_ms / max(1, live_n)
-        fp32_pass = sum(r["assign_live_ms"] for r in r32) / max(1, sum(r["assign_live_launches"] for r in r32))
-        fp32 = {"value": v32, "ms_per_step": float(np.mean(t32)),
-                "balance_passes": r32[-1]["balance_passes"], "balanced": r32[-1]["balanced"],
-                "assign_ms_per_pass": fp32_pass, "speedup_per_pass_vs_fp64": fp64_pass / fp32_pass,
-                "speedup_partition_vs_fp64": ms_per_step / float(np.mean(t32))}
+    if spec["assign"] == "f32":
+        fp32 = _fp32_stats(gk, xt, wt, spec, block, C, I, block_host, w)
+
+    # ---- FP64 argmin on the same points --------------------------------------------------
+    fp64 = None
+    if not args.no_fp64_compare and spec["assign"] == "f32":
+        o64 = gk.default_options(assign_dtype="f64")
+        step(o64)
+        t64, o64s = _timed(stream, flush, lambda: step(o64), max(1, min(2, args.steps)))
+        r64 = o64s[-1][3]
+        b64, C64, I64 = o64s[-1][:3]
+        pass32 = live_ms / max(1, live_n)
+        pass64 = sum(o[3]["assign_live_ms"] for o in o64s) / max(1, sum(o[3]["assign_live_launches"] for o in o64s))
+        ext = float((xt.amax(0).double() - xt.amin(0).double()).max().item())
+        fp64 = {"value": sum(n * o[3]["balance_passes"] for o in o64s) / (sum(t64) * 1e-3),
+                "ms_per_step": float(np.mean(t64)), "balance_passes": r64["balance_passes"],
+                "iterations": r64["iterations"], "balanced": r64["balanced"],
+                "max_imbalance": r64["max_imbalance"],
+                "rechecked_points_per_step": r64["rechecked_points"],
+                "assign_ms_per_pass_live": pass64,
+                "fp32_speedup_per_pass": pass64 / pass32,
+                "fp32_speedup_per_partition": float(np.mean(t64)) / ms_per_step,
+                "partitions_differ_fraction": float((b64 != block).double().mean().item()),
+                "center_diff_vs_fp32_form": float((C64 - C).abs().max().item()) / ext}
+        del o64s, b64, C64, I64
 
     # ---- random initialization (Section 4.5) on the same data -----------------------------
     sampled = None
     if not args.no_sampled:
-        sampled = _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, ms_per_step,
-                                max(1, min(3, args.steps)))
+        sampled = _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, ms_per_step, 1)
 
     # ---- per-point bounds (Section 4.3 in spirit; gk_options.bounds) ---------------------
     bounds = None
     if not args.no_bounds:
-        bounds = _bounds_leg(gk, xt, wt, spec, stream, flush, ms_per_step, max(1, min(3, args.steps)))
+        bounds = _bounds_leg(gk, xt, wt, spec, stream, flush, ms_per_step, 1)
 
-    # ---- partition quality (Section 5 measures) on a mesh of the same scale ---------------
+    del xt, wt, block, C, I
+    gk.release()
+    torch.cuda.empty_cache()
+
+    # ---- the other workloads -------------------------------------------------------------
+    legs = {}
+    if not args.no_legs and rank == 0:
+        for name in EXTRA_LEGS:
+            if name == args.workload:
+                continue
+            if name == BATCHED_WORKLOAD:
+                legs[name] = _batched_leg(gk, stream, flush, 2)[0]
+            else:
+                legs[name] = _config_leg(gk, name, stream, flush, 3)
+
+    # ---- partition quality (Section 5 measures) on a mesh --------------------------------
     quality = None
     if not args.no_quality and rank == 0:
         quality = _quality(gk, synth, spec, stream)
@@ -357,7 +613,6 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x, w, spec, args.cpu_seconds)
 
-    last = results[-1]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -370,8 +625,8 @@ def main():
                 "rechecked_points_per_step": last["rechecked_points"],
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
-                "fp32_form": fp32, "sampled_init": sampled, "bounds": bounds, "quality": quality,
-                "cpu_baseline": cpu}
+                "fp32_form": fp32, "fp64_form": fp64, "legs": legs, "sampled_init": sampled,
+                "bounds": bounds, "quality": quality, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -380,11 +635,9 @@ def main():
 
 
 def run_batched(args):
-    """64 instances of mixed n, d, k with weights, FP32 form, one gk_partition_batched
-    call per step (one graph launch for all k-means loops)."""
+    """The batched workload as the line's own workload (--workload batched64_f32)."""
     import torch
     import paper_1805_01208_gb300 as gk
-    from paper_1805_01208_gb300 import synth
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -395,43 +648,32 @@ def run_batched(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     gk.build()
-    specs = synth.batched_instances(64, seed=4 + 1000 * rank)
-    host = [synth.instance_data(sp) for sp in specs]
-    xs = [torch.from_numpy(x).to(dev) for x, _ in host]
-    ws = [torch.from_numpy(w).to(dev) if w is not None else None for _, w in host]
-    probs = [(xs[i], sp["k"], sp["eps"], ws[i]) for i, sp in enumerate(specs)]
-    opts = gk.default_options(assign_dtype="f32")
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        gk.partition_batched(probs, options=opts)
-    torch.cuda.synchronize()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # warm-up calls inside the leg (one), then the timed steps
+    for _ in range(max(0, args.warmup - 1)):
+        _batched_leg(gk, stream, flush, 1, rank)
     if dist:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
-    times, pp = [], 0.0
-    for _ in range(args.steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        outs, st = gk.partition_batched(probs, options=opts)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        pp += sum(sp["n"] * r["balance_passes"] for sp, (_, _, _, r) in zip(specs, outs))
+    leg, host, specs = _batched_leg(gk, stream, flush, args.steps, rank)
     clk = clocks.stop()
-    total_ms = float(sum(times))
+    total_ms = leg["ms_per_step"] * args.steps
+    pp = leg["value"] * total_ms * 1e-3
     if dist:
         total_ms, pp = reduce_over_ranks(total_ms, pp, dist, dev)
-    res = [r for _, _, _, r in outs]
     # end to end: inputs from pinned host memory, block ids back, inside the timed region
+    xs = [torch.empty(x.shape, dtype=torch.from_numpy(x).dtype, device=dev) for x, _ in host]
+    ws = [None if w is None else torch.empty(w.shape, dtype=torch.from_numpy(w).dtype, device=dev)
+          for _, w in host]
+    probs = [(xs[i], sp["k"], sp["eps"], ws[i]) for i, sp in enumerate(specs)]
     hx = [torch.from_numpy(x).pin_memory() for x, _ in host]
     hw = [torch.from_numpy(w).pin_memory() if w is not None else None for _, w in host]
     hb = [torch.empty(sp["n"], dtype=torch.int32).pin_memory() for sp in specs]
-    e2e_ms, e2e_pp = 0.0, 0.0
-    for _ in range(max(1, min(3, args.steps))):
+    opts = gk.default_options(assign_dtype="f32")
+    e2e_ms, e2e_pp, reps = 0.0, 0.0, max(1, min(3, args.steps))
+    for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -448,25 +690,20 @@ def run_batched(args):
         e2e_pp += sum(sp["n"] * r["balance_passes"] for sp, (_, _, _, r) in zip(specs, outs))
     h2d = sum(x.nbytes + (0 if w is None else w.nbytes) for x, w in host)
     if rank == 0:
-        ntot = sum(sp["n"] for sp in specs)
         line = {"metric": METRIC, "value": pp / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": BATCHED_WORKLOAD, "instances": len(specs), "points": ntot,
-                           "n_range": [min(sp["n"] for sp in specs), max(sp["n"] for sp in specs)],
-                           "k_range": [min(sp["k"] for sp in specs), max(sp["k"] for sp in specs)],
-                           "weights": "uniform[1,10]", "assign": "f32",
-                           "l2": "a 512 MB write between timed steps", "parallelism": "single"},
+                "config": {"workload": BATCHED_WORKLOAD, "instances": leg["instances"],
+                           "points": leg["points"], "n_range": leg["n_range"],
+                           "k_range": leg["k_range"], "weights": "uniform[1,10]", "assign": "f32",
+                           "reductions": "f64", "l2": "a 512 MB write between timed steps",
+                           "parallelism": "single"},
                 "partition_time_s": total_ms / args.steps / 1e3,
-                "balance_passes_total": int(sum(r["balance_passes"] for r in res)),
-                "balance_passes_max": int(max(r["balance_passes"] for r in res)),
-                "balanced": int(sum(r["balanced"] for r in res)),
-                "bootstrap_ms": res[0]["time_bootstrap_ms"], "kmeans_loop_ms": res[0]["time_kmeans_ms"],
-                "gpu_launches": int(sum(r["kernel_launches"] for r in res)) * args.steps,
-                "clocks": clk, "roofline": None, "cpu_baseline": None,
+                "gpu_launches": leg["kernel_launches_per_step"] * args.steps,
+                "clocks": clk, "roofline": None, "cpu_baseline": None, "batched": leg,
                 "e2e": {"value": e2e_pp / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": 4 * ntot, "ms_per_step": e2e_ms / max(1, min(3, args.steps))}}
+                        "d2h_bytes_per_step": 4 * leg["points"], "ms_per_step": e2e_ms / reps}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -512,6 +749,7 @@ def _e2e(gk, x, w, spec, opts, stream, steps):
     es = 8 if spec["dtype"] == "f64" else 4
     h2d = n * d * es + (n * es if w is not None else 0)
     d2h = n * 4 + k * d * 8 + k * 8
+    del xh, wh, bh
     return {"value": pp / (tot * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": tot / steps}
 
@@ -532,16 +770,9 @@ def _sampled_init(gk, xt, wt, spec, opts, stream, flush, synth, plain_ms, steps)
 
     call()
     torch.cuda.synchronize()
-    times, res = [], None
-    for _ in range(steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, _, res = call()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times, outs = _timed(stream, flush, call, steps)
+    res = outs[-1][3]
+    del outs, order
     ms = float(np.mean(times))
     return {"ms_per_step": ms, "partition_time_s": ms / 1e3, "first_sample": m0,
             "sample_rounds": rounds, "iterations": res["iterations"],
@@ -558,16 +789,10 @@ def _bounds_leg(gk, xt, wt, spec, stream, flush, plain_ms, steps):
     o = gk.default_options(assign_dtype=spec["assign"], bounds=1)
     gk.partition(xt, k, eps, weights=wt, options=o)
     torch.cuda.synchronize()
-    times, res = [], None
-    for _ in range(steps):
-        flush.fill_(1)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, _, res = gk.partition(xt, k, eps, weights=wt, options=o)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times, outs = _timed(stream, flush, lambda: gk.partition(xt, k, eps, weights=wt, options=o),
+                         steps)
+    res = outs[-1][3]
+    del outs
     ms = float(np.mean(times))
     return {"ms_per_step": ms, "balance_passes": res["balance_passes"],
             "evaluated_fraction": res["evaluated_points"] / (n * res["balance_passes"]),
@@ -575,15 +800,17 @@ def _bounds_leg(gk, xt, wt, spec, stream, flush, plain_ms, steps):
             "speedup_vs_plain": plain_ms / ms}
 
 
-def _quality(gk, synth, spec, stream):
+def _quality(gk, synth, spec, stream, k=1024, seed=2):
     """Edge cut and communication volume (gk_partition_quality) and block diameter bounds
-    (gk_block_diameter, three sweeps) of balanced k-means and of the plain curve split (the i-th n/k points on the Hilbert curve form block i) on a
-    graded 3-D lattice mesh with as many vertices as the workload has points (at most
-    200^3), the workload's k and eps."""
+    (gk_block_diameter, three sweeps) of balanced k-means and of the plain curve split (the
+    i-th n/k points on the Hilbert curve form block i) on a graded 3-D lattice mesh of
+    200^3 vertices (at most as many as the workload has points), k = 1024, the workload's
+    eps."""
     import torch
     side = int(round(min(spec["n"], 200 ** 3) ** (1.0 / 3.0)))
-    x, rp, col = synth.lattice_mesh((side, side, side), spec["seed"])
-    n, k = len(x), spec["k"]
+    x, rp, col = synth.lattice_mesh((side, side, side), seed)
+    n = len(x)
+    k = min(k, n)
     xt = torch.from_numpy(x).cuda()
     rpt, colt = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
     block, _, _, res = gk.partition(xt, k, spec["eps"])
