@@ -383,7 +383,28 @@ def _fp32_stats(gk, xt, wt, spec, block, C, I, block_host, w_host):
     ne = cnt > 0
     mean = sums[ne] / cnt[ne][:, None]
     cerr = float((Cm[ne] - mean).abs().max().item()) / ext
+    # a second reference on the host: FP64 brute force over all k centers (numpy) for a
+    # uniform sample of the points
+    m = min(n, 10_000)
+    rng = np.random.default_rng(2024)
+    idx = np.sort(rng.choice(n, m, replace=False)) if m < n else np.arange(n)
+    it = torch.from_numpy(idx).to(xt.device)
+    xs_h = xt.index_select(0, it).double().cpu().numpy()
+    bs_h = block.index_select(0, it).cpu().numpy()
+    Ch, gh = C.double().cpu().numpy(), 1.0 / I.double().cpu().numpy() ** 2
+    ref = np.empty(m, dtype=np.int64)
+    for s0 in range(0, m, 512):  # the squared distance axis by axis, then times 1/I^2
+        xc = xs_h[s0:s0 + 512]
+        d2 = (xc[:, 0, None] - Ch[None, :, 0]) ** 2
+        for j in range(1, d):
+            d2 += (xc[:, j, None] - Ch[None, :, j]) ** 2
+        d2 *= gh[None, :]
+        ref[s0:s0 + 512] = np.argmin(d2, axis=1)
+    host_differ = int((ref != bs_h).sum())
     out = {"disagreement": differ / n, "disagreeing_points": differ, "points_checked": n,
+           "disagreement_host_sample": host_differ / m, "host_sample_points": m,
+           "host_sample_reference": "FP64 brute force over all k centers on the host (numpy), "
+                                    "uniform sample",
            "disagreement_reference": "FP64 argmin under the returned centers and influence "
                                      "(gk_assign in FP64 mode), every point",
            "center_error": cerr,
@@ -423,6 +444,8 @@ def _config_leg(gk, name, stream, flush, steps, x=None, w=None, spec=None):
            "balanced": res["balanced"], "max_imbalance": res["max_imbalance"],
            "bootstrap_ms": res["time_bootstrap_ms"], "avg_candidates": res["avg_candidates"],
            "assign_ms_per_pass_live": res["assign_live_ms"] / max(1, res["assign_live_launches"]),
+           "launch_shapes": {"supertile_tiles": res["supertile_tiles"],
+                             "assign_ctas_per_sm": res["assign_ctas_per_sm"]},
            "roofline": _roofline(gk, xt, wt, spec, name)}
     if spec["assign"] == "f32":
         block, C, I, _ = outs[-1]
@@ -520,8 +543,7 @@ def main():
     def step(options=opts):
         return gk.partition(xt, k, eps, weights=wt, options=options)
 
-    for _ in range(args.warmup):
-        step()
+    warm = [step()[3] for _ in range(args.warmup)]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -579,6 +601,17 @@ def main():
                 "center_diff_vs_fp32_form": float((C64 - C).abs().max().item()) / ext}
         del o64s, b64, C64, I64
 
+    # ---- launch shapes: the tuned ones against the fixed defaults of the kernels -----------
+    shapes = {"supertile_tiles": last["supertile_tiles"], "assign_ctas_per_sm": last["assign_ctas_per_sm"],
+              "tune_ms_first_call": warm[0]["tune_ms"] if warm else None}
+    ofix = gk.default_options(assign_dtype=spec["assign"], supertile_tiles=16, assign_ctas_per_sm=64)
+    step(ofix)
+    tfix, rfix = _timed(stream, flush, lambda: step(ofix), max(1, min(2, args.steps)))
+    shapes["fixed"] = {"supertile_tiles": 16, "assign_ctas_per_sm": rfix[-1][3]["assign_ctas_per_sm"],
+                       "ms_per_step": float(np.mean(tfix))}
+    shapes["tuned_speedup_vs_fixed"] = float(np.mean(tfix)) / ms_per_step
+    del rfix
+
     # ---- random initialization (Section 4.5) on the same data -----------------------------
     sampled = None
     if not args.no_sampled:
@@ -625,6 +658,7 @@ def main():
                 "rechecked_points_per_step": last["rechecked_points"],
                 "bootstrap_ms": last["time_bootstrap_ms"], "kmeans_loop_ms": last["time_kmeans_ms"],
                 "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roof,
+                "launch_shapes": shapes,
                 "fp32_form": fp32, "fp64_form": fp64, "legs": legs, "sampled_init": sampled,
                 "bounds": bounds, "quality": quality, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define GK_ABI_VERSION 2
+#define GK_ABI_VERSION 3
 
 typedef enum gk_status {
     GK_OK = 0,
@@ -78,7 +78,15 @@ typedef struct gk_options {
                                    benchmark workloads about a third of the point
                                    evaluations remain, but the bookkeeping makes a pass
                                    slower on this GPU, hence the default.                  */
-    int32_t reserved[4];        /* must be zero                                           */
+    int32_t supertile_tiles;    /* tiles of 256 curve-consecutive points per supertile, the
+                                   unit of the candidate filter's first level (Section 4.4's
+                                   bounding-box pruning) and one warp of it: 16 or 32; 0
+                                   (default): chosen by the launch-shape tuner            */
+    int32_t assign_ctas_per_sm; /* resident CTAs per SM of the persistent assignment kernel
+                                   (4 warps each, a tile of 256 points per warp and stage):
+                                   1 .. the kernel's maximum (larger values are clamped);
+                                   0 (default): chosen by the tuner                        */
+    int32_t reserved[2];        /* must be zero                                           */
 } gk_options;
 
 /* Outcome and counters of one call. */
@@ -111,7 +119,22 @@ typedef struct gk_result {
     int64_t assign_live_launches;
     int64_t evaluated_points;   /* point evaluations over all passes on all points (equal to
                                    n x passes without bounds)                               */
+    int32_t supertile_tiles;    /* the launch shapes used (given or tuned)                 */
+    int32_t assign_ctas_per_sm;
+    double tune_ms;             /* device time the tuner spent measuring (0: shapes given or
+                                   taken from its cache)                                   */
 } gk_result;
+
+/*
+ * Launch-shape tuner.  A field of gk_options left 0 is chosen by measurement: on the first
+ * call for a kind of problem (d, input and assignment precision, weights, bounds, and the
+ * powers of two of n and k), after the bootstrap, the filter and assignment of the
+ * problem's first pass run once per candidate shape (supertiles of 16 or 32 tiles; the
+ * assignment's largest CTA count per SM and the two below it), the state is restored,
+ * and the fastest shape is kept in a process-wide cache for later calls of that kind.
+ * gk_partition_batched tunes every instance by its own kind.  The shapes change the
+ * speed only: every shape gives the same results.
+ */
 
 /* Fills *opt with the defaults listed above. */
 void gk_default_options(gk_options *opt);
@@ -328,6 +351,79 @@ typedef struct gk_diameter {
 gk_status gk_block_diameter(const int64_t *row_ptr, const int32_t *col, int64_t n, int64_t nnz,
                             const int32_t *block, int32_t k, int32_t sweeps, int32_t *diam_out,
                             gk_diameter *summary, void *stream);
+
+/*
+ * Sharded runs: the points split over several processes (one GPU each), as in the
+ * paper's distributed design (Section 4.1; Algorithm 2: sortGlobal and the
+ * redistribution give each process a contiguous range of the curve-sorted points;
+ * centers and influence are replicated; Algorithm 1 globalSumVector and Algorithm 2
+ * globalWeightedMeanVector are the only exchanges of the loop).  The caller moves the
+ * points between the processes (a splitter-based sample sort on the Hilbert keys and a
+ * redistribution into equal ranges); the library computes every step on each shard and
+ * calls the caller's reduction wherever the method needs a sum over all shards.
+ */
+#define GK_REDUCE_SUM 0
+#define GK_REDUCE_MIN 1
+#define GK_REDUCE_MAX 2
+/*
+ * The caller's reduction over all shards: replaces buf[0 .. count) (host memory) by the
+ * element-wise sum (GK_REDUCE_SUM), minimum or maximum over every shard's buf, as
+ * int64; returns 0 on success.  Every shard's call passes the same count and op, in the
+ * same order (a collective such as MPI_Allreduce or torch.distributed.all_reduce).
+ * The library sends exact integers only: 128-bit fixed-point sums as four 32-bit limbs
+ * (no overflow below 2^31 shards) and ordered keys of floating-point values.
+ */
+typedef int32_t (*gk_reduce_fn)(int64_t *buf, int64_t count, int32_t op, void *ctx);
+
+/*
+ * Bounding box of the points (Algorithm 2 sfcIndex needs the box of all points; a shard
+ * reduces its box with the other shards' by minimum and maximum).
+ *   lo_out, hi_out: d FP64 each, host memory.  Coordinates that are not finite give
+ *   GK_ERR_INVALID_ARG.
+ */
+gk_status gk_bounding_box(const void *coords, int32_t dtype, int64_t n, int32_t d, double *lo_out,
+                          double *hi_out, void *stream);
+
+/*
+ * gk_hilbert_keys with the bounding box given (lo, hi: d FP64 each, host memory) instead
+ * of taken from the points: a shard's keys on the box of all shards' points are the keys
+ * the whole point set would get.  Every point must lie inside [lo, hi] (else
+ * GK_ERR_INVALID_ARG).  With the points' own box the keys equal gk_hilbert_keys'.
+ */
+gk_status gk_hilbert_keys_in_box(const void *coords, int32_t dtype, int64_t n, int32_t d,
+                                 const double *lo, const double *hi, uint64_t *keys_out,
+                                 void *stream);
+
+/*
+ * Stable sort of Hilbert keys (Algorithm 2 sortGlobal, the local part): perm_out[i] =
+ * index of the i-th smallest key; equal keys keep their order.  The same LSD radix sort
+ * as the bootstrap of gk_partition (64 key bits for d = 2, 63 for d = 3).
+ *   keys: n uint64 (host or device); perm_out: n int64 (host or device).
+ *   1 <= n < 2^32.
+ */
+gk_status gk_sort_keys(const uint64_t *keys, int64_t n, int32_t d, int64_t *perm_out, void *stream);
+
+/*
+ * gk_balanced_kmeans on one shard: this process's points are a contiguous range of the
+ * curve-sorted points of a problem of n_global points in all (every shard calls this
+ * with its own range, the same k, eps, options and initial centers and influence).
+ * Every step runs on the shard's points; the bounding box, the total weight, the block
+ * weights of every pass and the coordinate sums and block boxes of every movement go
+ * through `reduce` (see gk_reduce_fn), so that every shard takes the same decisions and
+ * ends with the same centers and influence.  All sums are exact integers, so the result
+ * does not depend on how the points are split: with the FP64 assignment the block ids
+ * are those of gk_balanced_kmeans on all points in curve order, bit for bit.  The loop
+ * is host-driven (use_graph is ignored).
+ *   n_local >= 1, n_global >= n_local, 1 <= k <= n_global; block_out: n_local int32;
+ *   other arguments as gk_balanced_kmeans.  A failed reduction gives GK_ERR_CUDA.
+ *   An argument error found on one shard before its first reduction leaves the other
+ *   shards waiting in theirs: the caller's collective decides how long.
+ */
+gk_status gk_balanced_kmeans_sharded(const void *coords, int32_t dtype, const void *weights,
+                                     int64_t n_local, int64_t n_global, int32_t d, int32_t k,
+                                     double eps, double *centers_inout, double *influence_inout,
+                                     int32_t *block_out, const gk_options *opt, gk_result *result,
+                                     gk_reduce_fn reduce, void *reduce_ctx, void *stream);
 
 /* Frees the device workspace and cached graphs of the current device. */
 void gk_release(void);

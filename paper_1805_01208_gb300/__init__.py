@@ -47,7 +47,9 @@ class Options(ctypes.Structure):
         ("use_graph", ctypes.c_int32),
         ("timing", ctypes.c_int32),
         ("bounds", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("supertile_tiles", ctypes.c_int32),
+        ("assign_ctas_per_sm", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -79,6 +81,9 @@ class Result(ctypes.Structure):
         ("assign_live_ms", ctypes.c_double),
         ("assign_live_launches", ctypes.c_int64),
         ("evaluated_points", ctypes.c_int64),
+        ("supertile_tiles", ctypes.c_int32),
+        ("assign_ctas_per_sm", ctypes.c_int32),
+        ("tune_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -130,6 +135,9 @@ class Diameter(ctypes.Structure):
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                              ctypes.c_int32, ctypes.c_void_p)
+GK_REDUCE_SUM, GK_REDUCE_MIN, GK_REDUCE_MAX = 0, 1, 2
 _FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _alloc_refs: dict = {}  # the registered callbacks, kept alive while the library may call them
 
@@ -167,6 +175,14 @@ def lib():
         L.gk_move_centers_noalloc.restype = i32
         L.gk_partition_batched.argtypes = [P, i32, P, P, P]
         L.gk_partition_batched.restype = i32
+        L.gk_bounding_box.argtypes = [P, i32, i64, i32, P, P, P]
+        L.gk_hilbert_keys_in_box.argtypes = [P, i32, i64, i32, P, P, P, P]
+        L.gk_sort_keys.argtypes = [P, i64, i32, P, P]
+        L.gk_balanced_kmeans_sharded.argtypes = [P, i32, P, i64, i64, i32, i32, dbl, P, P, P, P, P,
+                                                 ctypes.c_void_p, P, P]
+        for name in ("gk_bounding_box", "gk_hilbert_keys_in_box", "gk_sort_keys",
+                     "gk_balanced_kmeans_sharded"):
+            getattr(L, name).restype = i32
         L.gk_release.argtypes = []
         L.gk_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.gk_set_allocator.restype = i32
@@ -325,6 +341,70 @@ def move_centers_noalloc(coords, block, centers, weights=None, out=None, delta=N
                                        ctypes.byref(beta), _stream(coords, stream))
     _check(st, "gk_move_centers_noalloc")
     return out, delta, beta.value
+
+
+def bounding_box(coords, stream=None):
+    """(lo, hi): the points' bounding box, two numpy arrays of d FP64."""
+    n, d = _shape(coords)
+    lo, hi = np.empty(d), np.empty(d)
+    st = lib().gk_bounding_box(_ptr(coords), _dtype_code(coords), n, d, _ptr(lo), _ptr(hi),
+                               _stream(coords, stream))
+    _check(st, "gk_bounding_box")
+    return lo, hi
+
+
+def hilbert_keys_in_box(coords, lo, hi, stream=None):
+    """Hilbert keys of the points on the given bounding box (lo, hi: d values each)."""
+    n, d = _shape(coords)
+    keys = _empty(coords, (n,), "u64")
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    st = lib().gk_hilbert_keys_in_box(_ptr(coords), _dtype_code(coords), n, d, _ptr(lo), _ptr(hi),
+                                      _ptr(keys), _stream(coords, stream))
+    _check(st, "gk_hilbert_keys_in_box")
+    return keys
+
+
+def sort_keys(keys, d: int, stream=None):
+    """Stable sort of Hilbert keys: int64 permutation (position -> index of the key)."""
+    n = int(keys.shape[0])
+    perm = _empty(keys, (n,), "i64")
+    st = lib().gk_sort_keys(_ptr(keys), n, d, _ptr(perm), _stream(keys, stream))
+    _check(st, "gk_sort_keys")
+    return perm
+
+
+def balanced_kmeans_sharded(coords, n_global: int, k: int, eps: float, centers, influence, reduce,
+                            weights=None, options: Options | None = None, stream=None):
+    """gk_balanced_kmeans on one shard (this process's contiguous range of the curve-sorted
+    points of a problem of n_global points).  reduce(buf, op) replaces the int64 numpy
+    array buf in place by its sum (op 0), minimum (1) or maximum (2) over all shards.
+    centers / influence are updated in place.  Returns (block, result dict)."""
+    n, d = _shape(coords)
+    _same_dtype(coords, weights)
+    block = _empty(coords, (n,), "i32")
+    res = Result()
+    opt = options if options is not None else default_options()
+    failed = []
+
+    def cb(buf, count, op, ctx):
+        try:
+            reduce(np.ctypeslib.as_array(buf, shape=(int(count),)), int(op))
+            return 0
+        except Exception as e:  # reported as a failed call (the library stops)
+            failed.append(e)
+            return 1
+
+    fn = _REDUCE_FN(cb)
+    st = lib().gk_balanced_kmeans_sharded(_ptr(coords), _dtype_code(coords), _ptr(weights), n,
+                                          int(n_global), d, k, eps, _ptr(centers), _ptr(influence),
+                                          _ptr(block), ctypes.byref(opt), ctypes.byref(res),
+                                          ctypes.cast(fn, ctypes.c_void_p), None,
+                                          _stream(coords, stream))
+    if failed:
+        raise failed[0]
+    _check(st, "gk_balanced_kmeans_sharded", allow=(GK_ERR_NOT_BALANCED,))
+    return block, res.as_dict()
 
 
 def balanced_kmeans(coords, k: int, eps: float, centers, influence, weights=None,

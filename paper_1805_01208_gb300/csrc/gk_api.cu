@@ -4,6 +4,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -103,6 +106,54 @@ void release_all() {
     g_ws = Workspace();
 }
 
+// The exchange of a sharded call (gk_balanced_kmeans_sharded): the caller's reduction
+// over all shards of a host vector of int64.  The global sums of the method (block
+// weights, coordinate sums: 128-bit fixed point, so exact in any order) travel as four
+// 32-bit limbs per value, each in an int64, so that a plain int64 sum over fewer than 2^31
+// shards cannot overflow; ordered keys (bounding boxes: unsigned) travel with their top
+// bit flipped, so that a signed minimum or maximum orders them as unsigned.
+struct Exchange {
+    gk_reduce_fn fn = nullptr;
+    void *ctx = nullptr;
+    std::vector<int64_t> buf;
+    bool on() const { return fn != nullptr; }
+    // count 128-bit values as (lo, hi) word pairs, summed over the shards in place
+    gk_status sum128(unsigned long long *w, size_t count) {
+        buf.resize(4 * count);
+        for (size_t i = 0; i < count; ++i)
+            for (int j = 0; j < 4; ++j)
+                buf[4 * i + j] = (int64_t)((w[2 * i + (j >> 1)] >> (32 * (j & 1))) & 0xffffffffull);
+        if (fn(buf.data(), (int64_t)buf.size(), GK_REDUCE_SUM, ctx) != 0) return GK_ERR_CUDA;
+        for (size_t i = 0; i < count; ++i) {
+            unsigned long long limb[4], carry = 0;
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long v = (unsigned long long)buf[4 * i + j] + carry;
+                limb[j] = v & 0xffffffffull;
+                carry = v >> 32;
+            }
+            w[2 * i] = limb[0] | (limb[1] << 32);
+            w[2 * i + 1] = limb[2] | (limb[3] << 32);
+        }
+        return GK_OK;
+    }
+    // count ordered keys, their minimum (or maximum) over the shards in place
+    gk_status keys(unsigned long long *k, size_t count, bool max) {
+        buf.resize(count);
+        for (size_t i = 0; i < count; ++i) buf[i] = (int64_t)(k[i] ^ 0x8000000000000000ull);
+        if (fn(buf.data(), (int64_t)count, max ? GK_REDUCE_MAX : GK_REDUCE_MIN, ctx) != 0)
+            return GK_ERR_CUDA;
+        for (size_t i = 0; i < count; ++i) k[i] = (unsigned long long)buf[i] ^ 0x8000000000000000ull;
+        return GK_OK;
+    }
+    gk_status imax(int *v, size_t count) {
+        buf.resize(count);
+        for (size_t i = 0; i < count; ++i) buf[i] = v[i];
+        if (fn(buf.data(), (int64_t)count, GK_REDUCE_MAX, ctx) != 0) return GK_ERR_CUDA;
+        for (size_t i = 0; i < count; ++i) v[i] = (int)buf[i];
+        return GK_OK;
+    }
+};
+
 // Pointer kinds.
 enum PtrKind { kHost = 0, kDevice = 1, kForeign = 2 };
 PtrKind ptr_kind(const void *p, int device) {
@@ -156,6 +207,10 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.A = (int *)take((size_t)np * 4);
     p.A16 = (unsigned short *)take((size_t)np * 2);
     p.tiles = (float4 *)take((size_t)p.ntiles * 32);
+    p.tws = (unsigned long long *)take((size_t)p.ntiles * 8);
+    p.tsx = (long long *)take((size_t)p.ntiles * d * 8);
+    p.tlo = (unsigned long long *)take((size_t)p.ntiles * d * 8);
+    p.thi = (unsigned long long *)take((size_t)p.ntiles * d * 8);
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
     p.coop = (int *)take((size_t)p.ntiles * 4);
@@ -204,6 +259,9 @@ struct SampleBufs {
     int *A = nullptr;
     unsigned short *A16 = nullptr;
     float4 *tiles = nullptr, *supers = nullptr, *trec = nullptr;
+    unsigned long long *tws = nullptr;
+    long long *tsx = nullptr;
+    unsigned long long *tlo = nullptr, *thi = nullptr;
     int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
     float *prho = nullptr;            // per-point bounds of the sample
     unsigned char *pt1 = nullptr;
@@ -232,6 +290,10 @@ size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order
     sb.A = (int *)take((size_t)np * 4);
     sb.A16 = (unsigned short *)take((size_t)np * 2);
     sb.tiles = (float4 *)take((size_t)nt * 32);
+    sb.tws = (unsigned long long *)take((size_t)nt * 8);
+    sb.tsx = (long long *)take((size_t)nt * p.d * 8);
+    sb.tlo = (unsigned long long *)take((size_t)nt * p.d * 8);
+    sb.thi = (unsigned long long *)take((size_t)nt * p.d * 8);
     sb.supers = (float4 *)take((size_t)ns * 32);
     sb.trec = (float4 *)take((size_t)nt * kRecF4 * 16);
     sb.coop = (int *)take((size_t)nt * 4);
@@ -326,6 +388,23 @@ gk_status check_common(const void *coords, int32_t dtype, int64_t n, int32_t d) 
     return GK_OK;
 }
 
+// Launch-shape tuner cache: the shapes measured fastest per kind of problem.
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;  // d, dtype, f64, w, bounds, log2 n, log2 k
+struct TuneChoice {
+    int stiles, actas;
+};
+std::map<TuneKey, TuneChoice> g_tune;
+std::mutex g_tune_mu;
+
+int ilog2(long long v) {
+    int e = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++e;
+    }
+    return e;
+}
+
 // State shared by the entry points of one call.
 struct Call {
     cudaStream_t s;
@@ -335,12 +414,14 @@ struct Call {
     gk_status setup(const void *weights, int64_t n, int32_t d, int32_t k, int32_t dtype) {
         memset(&p, 0, sizeof(p));
         p.n = n;
+        p.n_global = n;
         p.n_pad = (n + kTile - 1) / kTile * kTile;
         p.d = d;
         p.k = k;
         p.dtype = dtype;
         p.weighted = weights != nullptr;
         p.ntiles = (int)(p.n_pad / kTile);
+        p.stiles = kSuperTiles;
         p.nsupers = (p.ntiles + kSuperTiles - 1) / kSuperTiles;
         p.qmul = tile_order_multiplier(p.ntiles);
         p.tile_magic = ~0ull / (unsigned long long)p.ntiles;
@@ -406,12 +487,139 @@ struct Call {
         GK_CUDA(cudaStreamSynchronize(s));
         return GK_OK;
     }
-    // Bounding box -> frame, grid and fixed-point parameters (one readback).
+    // Bounding box -> frame, grid and fixed-point parameters (one readback).  A shard
+    // takes the box, weight range and input flags of all shards.
     gk_status geometry(double delta_threshold) {
         GK_CUDA(launch_bbox(p, s));
         gk_status st = read_ctl();
         if (st != GK_OK) return st;
+        if (ex && ex->on()) {
+            Ctl &c = *g_ws.host_ctl;
+            int flags[2] = {c.nonfinite, c.nonpositive_w};
+            if ((st = ex->keys(c.bb_lo, 3, false)) != GK_OK || (st = ex->keys(c.bb_hi, 3, true)) != GK_OK ||
+                (st = ex->keys(&c.w_lo, 1, false)) != GK_OK || (st = ex->keys(&c.w_hi, 1, true)) != GK_OK ||
+                (st = ex->imax(flags, 2)) != GK_OK)
+                return st;
+            c.nonfinite = flags[0];
+            c.nonpositive_w = flags[1];
+        }
         return frame(*g_ws.host_ctl, delta_threshold);
+    }
+    // A shard: the total weight of all shards (after the gather formed the local one).
+    gk_status exchange_weight() {
+        if (!(ex && ex->on()) || !p.weighted) return GK_OK;
+        gk_status st = read_ctl();
+        if (st != GK_OK) return st;
+        unsigned long long w[2] = {g_ws.host_ctl->wsum_lo, g_ws.host_ctl->wsum_hi};
+        if ((st = ex->sum128(w, 1)) != GK_OK) return st;
+        GK_CUDA(cudaMemcpy(&p.ctl->wsum_lo, w, 16, cudaMemcpyHostToDevice));
+        return GK_OK;
+    }
+    // A shard: the block weights of the pass summed over all shards.
+    gk_status exchange_pass() {
+        if (!(ex && ex->on())) return GK_OK;
+        std::vector<unsigned long long> w(2 * (size_t)p.k);
+        GK_CUDA(cudaMemcpyAsync(w.data(), p.Sfix, w.size() * 8, cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        gk_status st = ex->sum128(w.data(), p.k);
+        if (st != GK_OK) return st;
+        GK_CUDA(cudaMemcpyAsync(p.Sfix, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        return GK_OK;
+    }
+    // A shard: the coordinate sums and block boxes of the movement over all shards.
+    gk_status exchange_move() {
+        if (!(ex && ex->on())) return GK_OK;
+        const size_t kd = (size_t)p.k * p.d;
+        std::vector<unsigned long long> sx(2 * kd), lo(kd), hi(kd);
+        GK_CUDA(cudaMemcpyAsync(sx.data(), p.SXfix, sx.size() * 8, cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaMemcpyAsync(lo.data(), p.BBlo, kd * 8, cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaMemcpyAsync(hi.data(), p.BBhi, kd * 8, cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        gk_status st;
+        if ((st = ex->sum128(sx.data(), kd)) != GK_OK || (st = ex->keys(lo.data(), kd, false)) != GK_OK ||
+            (st = ex->keys(hi.data(), kd, true)) != GK_OK)
+            return st;
+        GK_CUDA(cudaMemcpyAsync(p.SXfix, sx.data(), sx.size() * 8, cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaMemcpyAsync(p.BBlo, lo.data(), kd * 8, cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaMemcpyAsync(p.BBhi, hi.data(), kd * 8, cudaMemcpyHostToDevice, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        return GK_OK;
+    }
+    Exchange *ex = nullptr;
+    float tune_ms = 0.f;
+
+    void apply_shape(int stiles, int actas) {
+        p.stiles = stiles;
+        p.nsupers = (p.ntiles + stiles - 1) / stiles;
+        p.actas = actas;
+    }
+    // The launch shapes (gk_options supertile_tiles, assign_ctas_per_sm; 0: tuned).  Runs
+    // after the bootstrap: measures the first pass's filter and assignment for every
+    // candidate shape, keeps the fastest and restores the state (control block, block
+    // weights; the stored block ids and tile markers the trials wrote are those of the
+    // first pass, consistent with each other).
+    gk_status tune(const gk_options &o) {
+        std::vector<int> sts, cts;
+        if (o.supertile_tiles)
+            sts.push_back(o.supertile_tiles);
+        else
+            sts = {kSuperTiles, kMaxSuperTiles};
+        const int mc = assign_max_ctas(p);
+        if (o.assign_ctas_per_sm)
+            cts.push_back(o.assign_ctas_per_sm < mc ? o.assign_ctas_per_sm : mc);
+        else
+            for (int c = mc; c >= 1 && c >= mc - 2; --c) cts.push_back(c);
+        TuneChoice best{sts[0], cts[0]};
+        const TuneKey key{p.d, p.dtype, p.assign_f64, p.weighted, p.bounds, ilog2(p.n), ilog2(p.k)};
+        bool cached = false;
+        if (sts.size() * cts.size() > 1) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                best = it->second;
+                cached = true;
+            }
+        }
+        if (sts.size() * cts.size() > 1 && !cached) {
+            gk_status st = read_ctl();
+            if (st != GK_OK) return st;
+            const Ctl saved = *g_ws.host_ctl;
+            GK_CUDA(launch_init(p, s));
+            float best_ms = INFINITY;
+            cudaEvent_t e0 = g_ws.kev[0], e1 = g_ws.kev[1];
+            for (int stl : sts) {
+                apply_shape(stl, cts[0]);
+                GK_CUDA(launch_super_boxes(p, s));
+                for (int c : cts) {
+                    apply_shape(stl, c);
+                    float ms_min = INFINITY;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        GK_CUDA(cudaEventRecord(e0, s));
+                        GK_CUDA(launch_filter(p, s));
+                        GK_CUDA(launch_assign(p, s));
+                        GK_CUDA(cudaEventRecord(e1, s));
+                        GK_CUDA(cudaMemsetAsync(p.Sfix, 0, (size_t)p.k * 16, s));
+                        GK_CUDA(cudaMemsetAsync(&p.ctl->coop_cnt, 0, 2 * sizeof(unsigned), s));
+                        GK_CUDA(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                        tune_ms += ms;
+                        if (rep > 0 && ms < ms_min) ms_min = ms;  // the first run warms up
+                    }
+                    if (ms_min < best_ms) {
+                        best_ms = ms_min;
+                        best = {stl, c};
+                    }
+                }
+            }
+            GK_CUDA(cudaMemcpyAsync(p.ctl, &saved, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = best;
+        }
+        apply_shape(best.stiles, best.actas);
+        GK_CUDA(launch_super_boxes(p, s));
+        return GK_OK;
     }
     gk_status frame(const Ctl &c, double delta_threshold) {
         if (c.nonfinite || c.nonpositive_w) return GK_ERR_INVALID_ARG;
@@ -485,6 +693,9 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     r->assign_live_ms = (double)c.assign_ns * 1e-6;
     r->assign_live_launches = (int64_t)c.assign_cnt;
     r->evaluated_points = (int64_t)c.evaluated;
+    r->supertile_tiles = cl.p.stiles;
+    r->assign_ctas_per_sm = assign_ctas(cl.p);
+    r->tune_ms = cl.tune_ms;
 }
 
 gk_status copy_out(void *dst, const void *src, size_t bytes, cudaStream_t s) {
@@ -506,7 +717,8 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 gk_status run_loop(Call &cl, const gk_options &o) {
     Prob &p = cl.p;
     cudaStream_t s = cl.s;
-    if (o.use_graph) {
+    const bool sharded = cl.ex && cl.ex->on();  // host-driven: the exchanges sit between kernels
+    if (o.use_graph && !sharded) {
         Prob key = p;
         key.coords = nullptr;
         key.weights = nullptr;
@@ -533,6 +745,10 @@ gk_status run_loop(Call &cl, const gk_options &o) {
         if (o.timing) GK_CUDA(cudaEventRecord(ev[1], s));
         GK_CUDA(launch_assign(p, s));
         if (o.timing) GK_CUDA(cudaEventRecord(ev[2], s));
+        if (sharded) {
+            gk_status xs = cl.exchange_pass();
+            if (xs != GK_OK) return xs;
+        }
         GK_CUDA(launch_balance(p, mode, s));
         if (o.timing) GK_CUDA(cudaEventRecord(ev[3], s));
         gk_status st = cl.read_ctl();
@@ -552,7 +768,14 @@ gk_status run_loop(Call &cl, const gk_options &o) {
             if (!g_ws.host_ctl->cont_balance) break;
         }
         if (o.timing) GK_CUDA(cudaEventRecord(ev[0], s));
-        GK_CUDA(launch_move(p, 0, s));
+        if (sharded) {
+            GK_CUDA(launch_centroid(p, s));
+            gk_status xs = cl.exchange_move();
+            if (xs != GK_OK) return xs;
+            GK_CUDA(launch_move_finish(p, 0, s));
+        } else {
+            GK_CUDA(launch_move(p, 0, s));
+        }
         if (o.timing) GK_CUDA(cudaEventRecord(ev[1], s));
         gk_status st = cl.read_ctl();
         if (st != GK_OK) return st;
@@ -576,9 +799,10 @@ gk_status run_loop(Call &cl, const gk_options &o) {
 Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     Prob ps = p;
     ps.n = m;
+    ps.n_global = m;
     ps.n_pad = (m + kTile - 1) / kTile * kTile;
     ps.ntiles = (int)(ps.n_pad / kTile);
-    ps.nsupers = (ps.ntiles + kSuperTiles - 1) / kSuperTiles;
+    ps.nsupers = (ps.ntiles + ps.stiles - 1) / ps.stiles;
     ps.qmul = tile_order_multiplier(ps.ntiles);
     ps.tile_magic = ~0ull / (unsigned long long)ps.ntiles;
     ps.keys[0] = ps.keys[1] = nullptr;
@@ -589,6 +813,10 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.A = sb.A;
     ps.A16 = sb.A16;
     ps.tiles = sb.tiles;
+    ps.tws = sb.tws;
+    ps.tsx = sb.tsx;
+    ps.tlo = sb.tlo;
+    ps.thi = sb.thi;
     ps.supers = sb.supers;
     ps.trec = sb.trec;
     ps.coop = sb.coop;
@@ -666,7 +894,10 @@ gk_status check_options(const gk_options &o) {
         (o.assign_dtype != GK_F32 && o.assign_dtype != GK_F64) || !(o.delta_threshold == o.delta_threshold))
         return GK_ERR_INVALID_ARG;
     if (o.bounds != 0 && o.bounds != 1) return GK_ERR_INVALID_ARG;
-    for (int i = 0; i < 4; ++i)
+    if (o.supertile_tiles != 0 && o.supertile_tiles != kSuperTiles && o.supertile_tiles != kMaxSuperTiles)
+        return GK_ERR_INVALID_ARG;
+    if (o.assign_ctas_per_sm < 0 || o.assign_ctas_per_sm > 64) return GK_ERR_INVALID_ARG;
+    for (int i = 0; i < 2; ++i)
         if (o.reserved[i] != 0) return GK_ERR_INVALID_ARG;
     return GK_OK;
 }
@@ -678,10 +909,12 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
                         int32_t d, int32_t k, double eps, const gk_options *opt, bool sort,
                         double *centers_io, double *influence_io, int32_t *block_out,
                         double *centers_out, double *influence_out, gk_result *result,
-                        void *stream, const int64_t *order = nullptr, int64_t sample0 = 0) {
+                        void *stream, const int64_t *order = nullptr, int64_t sample0 = 0,
+                        Exchange *ex = nullptr, int64_t n_global = 0) {
     gk_status st = check_common(coords, dtype, n, d);
     if (st != GK_OK) return st;
-    if (k < 1 || k > n || !(eps >= 0.0) || !block_out) return GK_ERR_INVALID_ARG;
+    const int64_t n_all = ex ? n_global : n;  // a shard: k is bounded by all shards' points
+    if (k < 1 || k > n_all || !(eps >= 0.0) || !block_out) return GK_ERR_INVALID_ARG;
     if (!sort && (!centers_io || !influence_io)) return GK_ERR_INVALID_ARG;
     gk_options o;
     options_or_default(opt, &o);
@@ -707,10 +940,12 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
     }
     Call cl;
     cl.s = (cudaStream_t)stream;
+    cl.ex = ex;
     st = cl.init(coords, dtype, weights, n, d, k, sort, block_host, false, order ? &sb : nullptr,
                  order_host);
     if (st != GK_OK) return st;
     Prob &p = cl.p;
+    p.n_global = n_all;
     p.eps = eps;
     p.assign_f64 = o.assign_dtype == GK_F64;
     p.max_iter = o.max_iter - sb.rounds;
@@ -730,12 +965,14 @@ gk_status kmeans_common(const void *coords, int32_t dtype, const void *weights, 
         perm = p.perm[sel];
     }
     GK_CUDA(launch_gather(p, perm, cl.s));
+    if ((st = cl.exchange_weight()) != GK_OK) return st;
     if (sort) {
         GK_CUDA(launch_centers(p, cl.s));
     } else {
         GK_CUDA(cudaMemcpyAsync(p.C, centers_io, (size_t)k * d * 8, cudaMemcpyDefault, cl.s));
         GK_CUDA(cudaMemcpyAsync(p.Iin, influence_io, (size_t)k * 8, cudaMemcpyDefault, cl.s));
     }
+    if ((st = cl.tune(o)) != GK_OK) return st;
     if (order) {
         const long long *ord = (const long long *)order;
         if (order_host) {
@@ -849,6 +1086,7 @@ gk_status partition_batched(const gk_instance *inst, int32_t count, const gk_opt
         perm[i] = p.perm[sel];
         GK_CUDA(launch_gather(p, perm[i], s));
         GK_CUDA(launch_centers(p, s));
+        if ((st = cl[i].tune(o)) != GK_OK) return st;  // the instance's launch shapes
     }
     GK_CUDA(cudaEventRecord(g_ws.ev[1], s));
     std::vector<Prob> key(count);
@@ -964,6 +1202,103 @@ gk_status gk_hilbert_keys(const void *coords, int32_t dtype, int64_t n, int32_t 
     return GK_OK;
 }
 
+gk_status gk_bounding_box(const void *coords, int32_t dtype, int64_t n, int32_t d, double *lo_out,
+                          double *hi_out, void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (!lo_out || !hi_out) return GK_ERR_INVALID_ARG;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    if ((st = cl.init(coords, dtype, nullptr, n, d, 1, false, false, false)) != GK_OK) return st;
+    GK_CUDA(launch_bbox(cl.p, cl.s));
+    if ((st = cl.read_ctl()) != GK_OK) return st;
+    const Ctl &c = *g_ws.host_ctl;
+    if (c.nonfinite) return GK_ERR_INVALID_ARG;
+    for (int j = 0; j < d; ++j) {
+        lo_out[j] = okey_to_f64(c.bb_lo[j]);
+        hi_out[j] = okey_to_f64(c.bb_hi[j]);
+    }
+    return GK_OK;
+}
+
+gk_status gk_hilbert_keys_in_box(const void *coords, int32_t dtype, int64_t n, int32_t d,
+                                 const double *lo, const double *hi, uint64_t *keys_out,
+                                 void *stream) {
+    gk_status st = check_common(coords, dtype, n, d);
+    if (st != GK_OK) return st;
+    if (!keys_out || !lo || !hi) return GK_ERR_INVALID_ARG;
+    for (int j = 0; j < d; ++j)
+        if (!(lo[j] <= hi[j]) || !isfinite(lo[j]) || !isfinite(hi[j])) return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    PtrKind kk = ptr_kind(keys_out, dev);
+    if (kk == kForeign || (kk == kDevice && ((uintptr_t)keys_out % 8))) return GK_ERR_INVALID_ARG;
+    Call cl;
+    cl.s = (cudaStream_t)stream;
+    if ((st = cl.init(coords, dtype, nullptr, n, d, 1, true, false, false)) != GK_OK) return st;
+    GK_CUDA(launch_bbox(cl.p, cl.s));
+    if ((st = cl.read_ctl()) != GK_OK) return st;
+    Ctl c = *g_ws.host_ctl;
+    if (c.nonfinite) return GK_ERR_INVALID_ARG;
+    for (int j = 0; j < d; ++j) {  // the points must lie in the given box
+        if (okey_to_f64(c.bb_lo[j]) < lo[j] || okey_to_f64(c.bb_hi[j]) > hi[j]) return GK_ERR_INVALID_ARG;
+        c.bb_lo[j] = okey_f64(lo[j]);
+        c.bb_hi[j] = okey_f64(hi[j]);
+    }
+    if ((st = cl.frame(c, -1.0)) != GK_OK) return st;
+    Prob kp = cl.key_prob();
+    unsigned long long *dst = kk == kDevice ? (unsigned long long *)keys_out : cl.p.keys[0];
+    GK_CUDA(launch_keys(kp, dst, nullptr, cl.s));
+    if (kk != kDevice) st = copy_out(keys_out, dst, (size_t)n * 8, cl.s);
+    if (st != GK_OK) return st;
+    GK_CUDA(cudaStreamSynchronize(cl.s));
+    return GK_OK;
+}
+
+gk_status gk_sort_keys(const uint64_t *keys, int64_t n, int32_t d, int64_t *perm_out, void *stream) {
+    if (!keys || !perm_out || n < 1 || n >= 0xffffffffll || (d != 2 && d != 3)) return GK_ERR_INVALID_ARG;
+    int dev = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    const PtrKind kk = ptr_kind(keys, dev), kp = ptr_kind(perm_out, dev);
+    if (kk == kForeign || kp == kForeign || (kk == kDevice && ((uintptr_t)keys % 8)) ||
+        (kp == kDevice && ((uintptr_t)perm_out % 8)))
+        return GK_ERR_INVALID_ARG;
+    Prob p;
+    memset(&p, 0, sizeof(p));
+    p.n = n;
+    p.n_global = n;
+    p.n_pad = (n + kTile - 1) / kTile * kTile;
+    p.d = d;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align_up(bytes);
+        return o;
+    };
+    const size_t o_ctl = take(sizeof(Ctl)), o_k0 = take((size_t)n * 8), o_k1 = take((size_t)n * 8),
+                 o_p0 = take((size_t)n * 4), o_p1 = take((size_t)n * 4),
+                 o_h = take(radix_hist_entries(n) * 4), o_out = take((size_t)n * 8);
+    gk_status st = ensure_workspace(off);
+    if (st != GK_OK) return st;
+    char *base = g_ws.dev;
+    p.ctl = (Ctl *)(base + o_ctl);
+    p.keys[0] = (unsigned long long *)(base + o_k0);
+    p.keys[1] = (unsigned long long *)(base + o_k1);
+    p.perm[0] = (unsigned *)(base + o_p0);
+    p.perm[1] = (unsigned *)(base + o_p1);
+    long long *out = kp == kDevice ? (long long *)perm_out : (long long *)(base + o_out);
+    cudaStream_t s = (cudaStream_t)stream;
+    GK_CUDA(cudaMemsetAsync(p.ctl, 0, sizeof(Ctl), s));
+    GK_CUDA(cudaMemcpyAsync(p.keys[0], keys, (size_t)n * 8, cudaMemcpyDefault, s));
+    GK_CUDA(launch_iota(p.perm[0], n, s));
+    int sel = 0;
+    GK_CUDA(launch_radix_sort(p, d == 2 ? 64 : 63, (unsigned *)(base + o_h), &sel, s));
+    GK_CUDA(launch_perm_out(p, p.perm[sel], out, s));
+    if (kp != kDevice) GK_CUDA(cudaMemcpyAsync(perm_out, out, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    return GK_OK;
+}
+
 gk_status gk_sfc_init(const void *coords, int32_t dtype, int64_t n, int32_t d, int32_t k,
                       int64_t *perm_out, double *centers_out, void *stream) {
     gk_status st = check_common(coords, dtype, n, d);
@@ -1072,6 +1407,20 @@ gk_status gk_balanced_kmeans(const void *coords, int32_t dtype, const void *weig
                              gk_result *result, void *stream) {
     return kmeans_common(coords, dtype, weights, n, d, k, eps, opt, false, centers_inout,
                          influence_inout, block_out, nullptr, nullptr, result, stream);
+}
+
+gk_status gk_balanced_kmeans_sharded(const void *coords, int32_t dtype, const void *weights,
+                                     int64_t n_local, int64_t n_global, int32_t d, int32_t k,
+                                     double eps, double *centers_inout, double *influence_inout,
+                                     int32_t *block_out, const gk_options *opt, gk_result *result,
+                                     gk_reduce_fn reduce, void *reduce_ctx, void *stream) {
+    if (!reduce || n_global < n_local) return GK_ERR_INVALID_ARG;
+    Exchange ex;
+    ex.fn = reduce;
+    ex.ctx = reduce_ctx;
+    return kmeans_common(coords, dtype, weights, n_local, d, k, eps, opt, false, centers_inout,
+                         influence_inout, block_out, nullptr, nullptr, result, stream, nullptr, 0,
+                         &ex, n_global);
 }
 
 gk_status gk_partition(const void *coords, int32_t dtype, const void *weights, int64_t n,

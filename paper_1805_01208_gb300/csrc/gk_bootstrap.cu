@@ -258,17 +258,15 @@ __global__ void __launch_bounds__(kSortThreads)
 radix_upsweep(const unsigned long long *keys, long long n, int shift, int tiles_per_seg, int G,
               unsigned *hist, Ctl *ctl) {
     count_launch(ctl);
-    __shared__ unsigned cnt[kSortWarps][256];  // per-warp counts (one atomic per distinct digit)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ unsigned cnt[kSortWarps][256];  // per-warp counts (a shared atomic per key)
+    const int tid = threadIdx.x, warp = tid >> 5;
     for (int w = 0; w < kSortWarps; ++w) cnt[w][tid] = 0;
     __syncthreads();
     const long long beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;  // even
     long long end = beg + (long long)tiles_per_seg * kSortTile;
     if (end > n) end = n;
     auto count = [&](unsigned d) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (d < 256u && (peers & ((1u << lane) - 1u)) == 0u)
-            atomicAdd(&cnt[warp][d], (unsigned)__popc(peers));
+        if (d < 256u) atomicAdd(&cnt[warp][d], 1u);
     };
     // pairs of keys (16-byte loads), kLoads pairs in flight per thread
     constexpr int kLoads = 4;
@@ -554,6 +552,53 @@ __global__ void __launch_bounds__(kTileBoxWarps * 32) tile_box_kernel(Prob p) {
             hi[j] = fmaxf(hi[j], __shfl_xor_sync(0xffffffffu, hi[j], o));
         }
     }
+    // the tile's fixed-point coordinate sums (w x) and the ordered keys of its smallest and
+    // largest coordinates, as the movement converts them (its points never move)
+    for (int j = 0; j < p.d; ++j) {
+        long long sum = 0;
+        unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (i0 + q < p.n) {
+                long long v;
+                unsigned long long kk;
+                if (p.dtype == 1) {
+                    const double x = p.X64[(size_t)j * p.n_pad + i0 + q];
+                    v = p.weighted ? fix_f64(((const double *)p.Ws)[i0 + q] * x, p.Fx) : fix_f64(x, p.Fx);
+                    kk = okey_f64(x);
+                } else {
+                    const float x = p.X32[(size_t)j * p.n_pad + i0 + q];
+                    v = p.weighted ? fix_prod_f32(((const float *)p.Ws)[i0 + q], x, p.Fx) : fix_f32(x, p.Fx);
+                    kk = okey_f32(x);
+                }
+                sum += v;
+                kmin = kk < kmin ? kk : kmin;
+                kmax = kk > kmax ? kk : kmax;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, o);
+            kmin = a < kmin ? a : kmin;
+            kmax = b > kmax ? b : kmax;
+        }
+        if (lane == 0) {
+            p.tsx[t * p.d + j] = sum;
+            p.tlo[t * p.d + j] = kmin;
+            p.thi[t * p.d + j] = kmax;
+        }
+    }
+    if (p.weighted) {  // the tile's weight sum, as the assignment's histogram converts weights
+        unsigned long long ws = 0ull;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (i0 + q < p.n)
+                ws += (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i0 + q], p.Fw)
+                                                        : fix_f32(((const float *)p.Ws)[i0 + q], p.Fw));
+        for (int o = 16; o; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        if (lane == 0) p.tws[t] = ws;
+    }
     if (lane == 0) {
         float o[3] = {0.f, 0.f, 0.f}, h[3] = {0.f, 0.f, 0.f};
         float r2 = 0.0f;
@@ -563,7 +608,9 @@ __global__ void __launch_bounds__(kTileBoxWarps * 32) tile_box_kernel(Prob p) {
             r2 = __fadd_ru(r2, __fmul_ru(h[j], h[j]));
         }
         p.tiles[2 * t] = make_float4(o[0], o[1], o[2], __fsqrt_ru(r2));
-        p.tiles[2 * t + 1] = make_float4(h[0], h[1], h[2], 0.0f);
+        // w: the block id that every stored 16-bit id of the tile holds, -1 for none yet
+        // (kept up to date by the assignment, forwarded to it by the filter)
+        p.tiles[2 * t + 1] = make_float4(h[0], h[1], h[2], __int_as_float(-1));
     }
 }
 static int tile_box_grid(int ntiles) { return (ntiles + kTileBoxWarps - 1) / kTileBoxWarps; }
@@ -585,7 +632,7 @@ __global__ void super_box_kernel(Prob p) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= p.nsupers) return;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    int t0 = s * kSuperTiles, t1 = min(p.ntiles, t0 + kSuperTiles);
+    int t0 = s * p.stiles, t1 = min(p.ntiles, t0 + p.stiles);
     for (int t = t0; t < t1; ++t) {
         float4 a = p.tiles[2 * t], b = p.tiles[2 * t + 1];
         float o[3] = {a.x, a.y, a.z}, h[3] = {b.x, b.y, b.z};
@@ -841,6 +888,11 @@ cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_super_boxes(const Prob &p, cudaStream_t s) {
+    super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 long long sample_rho_entries(long long n) {
     return (n + kSampleChunk - 1) / kSampleChunk * kSampleChunk;
 }
@@ -880,6 +932,15 @@ cudaError_t launch_sample_select(const Prob &ps, const SampleSel &sel, cudaStrea
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+__global__ void iota_kernel(unsigned *perm, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = (unsigned)i;
+}
+cudaError_t launch_iota(unsigned *perm, long long n, cudaStream_t s) {
+    iota_kernel<<<blocks_for(n, 256), 256, 0, s>>>(perm, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_centers(const Prob &p, cudaStream_t s) {

@@ -9,7 +9,7 @@
 //   A      n_pad int32 block ids in sorted order (A16: the same as 16 bits, which the
 //          k-means loop uses instead when k <= 65535: 2 B per point written per pass).
 //   tiles  2 float4 per tile of kTile points: {origin xyz, radius}, {half extents xyz, -};
-//   supers the same per supertile of kSuperTiles tiles.
+//   supers the same per supertile of stiles tiles.
 //   per tile record (written by the filter every pass, kRecF4 float4): header
 //          {count (int32; -1 = overflow: scan all centers), largest g of the tile's
 //          candidates, lower bound of the E of every center left out of the list, 0},
@@ -33,12 +33,14 @@
 namespace gk {
 
 constexpr int kTile = 256;          // points per tile (one warp of the assign kernel)
-constexpr int kSuperTiles = 16;     // tiles per supertile (one CTA of the filter kernel)
+constexpr int kSuperTiles = 16;     // tiles per supertile (one warp of the filter), default and
+                                    // the smallest choice (it sizes the per-supertile arrays)
+constexpr int kMaxSuperTiles = 32;  // the largest choice (one lane per tile in the filter)
 constexpr int kCap = 128;           // candidate centers stored per tile
 constexpr int kFastCands = 32;      // candidates brought in with the tile's bulk copy
 constexpr int kCoopCands = kFastCands;  // tiles with more candidates are taken by a whole CTA
 constexpr int kRecF4 = 2 + 2 * kCap;  // float4 per tile record (header + candidates)
-constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // bytes of one bulk copy
+constexpr unsigned kRecFastBytes = (2 + 2 * kFastCands) * 16;  // largest record copy of a tile
 constexpr int kKThreads = 32;       // threads per CTA of the k-sized kernels
 constexpr int kSuperCap = 1024;     // candidate centers kept per supertile
 constexpr int kGroup = 32;          // centers per group record (one CTA of the k-sized kernels)
@@ -112,8 +114,11 @@ struct Ctl {
 struct Prob {
     long long n;
     long long n_pad;
+    long long n_global;         // points of the whole problem (n, unless the call is one shard)
     int d, k, dtype, weighted, assign_f64;
     int ntiles, nsupers;
+    int stiles;                 // tiles per supertile (kSuperTiles or kMaxSuperTiles)
+    int actas;                  // resident CTAs per SM of the assignment (0: the default)
     int qmul;                   // tile order of the assignment: t = pos * qmul mod ntiles
     unsigned long long tile_magic;  // floor((2^64 - 1) / ntiles), for that reduction
     int bits, grid_m;           // Hilbert bits per axis and the scaling exponent b - E
@@ -137,6 +142,9 @@ struct Prob {
     unsigned short *A16;        // the block ids as 16 bits (a16: k <= 65535, no bounds)
     int a16;
     float4 *tiles, *supers;
+    unsigned long long *tws;    // per tile: sum of its points' fixed-point weights (weighted)
+    long long *tsx;             // per tile and axis: sum of the points' fixed-point w x
+    unsigned long long *tlo, *thi;  // per tile and axis: ordered keys of the smallest / largest x
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;
     int *coop;                  // tiles of the cooperative path (ntiles entries)

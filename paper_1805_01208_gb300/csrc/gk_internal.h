@@ -15,6 +15,8 @@ cudaError_t launch_radix_sort(const Prob &p, int key_bits, unsigned *hist, int *
                               cudaStream_t s);
 cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s);
 cudaError_t launch_centers(const Prob &p, cudaStream_t s);
+// supertile boxes for p.stiles tiles per supertile (p.nsupers of them)
+cudaError_t launch_super_boxes(const Prob &p, cudaStream_t s);
 cudaError_t launch_scatter(const Prob &p, const unsigned *perm, int *out, cudaStream_t s);
 cudaError_t launch_perm_out(const Prob &p, const unsigned *perm, long long *out, cudaStream_t s);
 
@@ -57,9 +59,17 @@ cudaError_t launch_load_state(const Prob &p, cudaStream_t s);
 cudaError_t launch_pass(const Prob &p, int mode, cudaStream_t s);
 cudaError_t launch_filter(const Prob &p, cudaStream_t s);
 cudaError_t launch_assign(const Prob &p, cudaStream_t s);
+// resident CTAs per SM of the assignment: its largest count, and the count p launches with
+int assign_max_ctas(const Prob &p);
+int assign_ctas(const Prob &p);
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s);
 cudaError_t launch_block_weights(const Prob &p, cudaStream_t s);
 cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s);
+// launch_move in two parts (a sharded run exchanges the block sums in between)
+cudaError_t launch_centroid(const Prob &p, cudaStream_t s);
+cudaError_t launch_move_finish(const Prob &p, int mode, cudaStream_t s);
+// identity permutation 0..n-1 (the values of a standalone key sort)
+cudaError_t launch_iota(unsigned *perm, long long n, cudaStream_t s);
 cudaError_t launch_final_begin(const Prob &p, cudaStream_t s);
 cudaError_t launch_export(const Prob &p, cudaStream_t s);
 // The whole loop of each of count problems as one graph (independent chains).

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         if (p.weighted)
             ctl->W = i128_to_f64(ctl->wsum_lo, ctl->wsum_hi, p.Fw);
         else
-            ctl->W = (double)p.n;
+            ctl->W = (double)p.n_global;  // all points of the problem (every shard's)
         ctl->target = ctl->W / (double)p.k;
         ctl->ceil_avg = ceil(ctl->W / (double)p.k);
         ctl->bound = (1.0 + p.eps) * ctl->ceil_avg;
@@ -539,12 +539,14 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
 // lam: smallest lower bound of the centers left out of the tile's list, which the
 // record keeps lowered by 16 u (the rounding of the bound's own arithmetic), as a lower
 // bound of every left-out center's E on the tile (+inf when all centers are evaluated).
+// uid: the tile's stored-id marker (the w of its second box word), handed to the
+// assignment in the header's w.
 __device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float gkept, float gall,
-                                            const float4 &tb0, float lam) {
+                                            const float4 &tb0, float lam, float uid) {
     const bool over = cnt > kCap;
     float4 *rec = p.trec + (size_t)t * kRecF4;
     const float lamr = over ? INFINITY : __fmul_rd(lam, 1.0f - 16.0f * kU);
-    rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, lamr, 0.f);
+    rec[0] = make_float4(__int_as_float(over ? -1 : cnt), over ? gall : gkept, lamr, uid);
     rec[1] = tb0;
     const bool coop = over || cnt > kCoopCands;
     if (coop) p.coop[atomicAdd(&p.ctl->coop_cnt, 1u)] = t;
@@ -574,8 +576,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
     const float infl = 4.0f * kU * p.R;
     // this lane's tile box, loaded while level 1 runs
-    const int t = s * kSuperTiles + lane;
-    const bool has_tile = lane < kSuperTiles && t < p.ntiles;
+    const int t = s * p.stiles + lane;
+    const bool has_tile = lane < p.stiles && t < p.ntiles;
     float4 tb0 = make_float4(0.f, 0.f, 0.f, 0.f), tb1 = tb0;
     if (has_tile) {
         tb0 = p.tiles[2 * t];
@@ -628,11 +630,11 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
                 ++cnt;
             }
         }
-        finish_tile(p, t, cnt, gkept, gall, tb0, lamT);
+        finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
     }
 }
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
-static_assert(kSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
+static_assert(kMaxSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
 
 // Level 2 of the supertiles with long lists: one warp per tile, lanes over chunks
 // of 32 candidates (tau pass, then the ascending keep pass with ballots).
@@ -641,17 +643,17 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
     count_launch(p.ctl);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int total = (int)p.ctl->big_cnt * kSuperTiles;
+    const int total = (int)p.ctl->big_cnt * p.stiles;
     const int sel = p.ctl->isel;
     const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
     const float infl = 4.0f * kU * p.R;
     const int TW = gridDim.x * kFilterWarps;
     for (int item = blockIdx.x * kFilterWarps + (threadIdx.x >> 5); item < total; item += TW) {
-        const int slot = item / kSuperTiles;
+        const int slot = item / p.stiles;
         const int s = p.bigs[4 * slot], Lr = p.bigs[4 * slot + 1];
         const float gall = __int_as_float(p.bigs[4 * slot + 2]);
         float lamT = __int_as_float(p.bigs[4 * slot + 3]);
-        const int t = s * kSuperTiles + item % kSuperTiles;
+        const int t = s * p.stiles + item % p.stiles;
         if (t >= p.ntiles) continue;
         const bool all = Lr > kWarpList;
         const int L = all ? p.k : Lr;
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
             lamT = fminf(lamT, __shfl_xor_sync(0xffffffffu, lamT, off));
         }
-        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0, lamT);
+        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
     }
 }
 
@@ -808,6 +810,42 @@ __device__ __forceinline__ void store_blocks(const Prob &p, long long i0, int nv
 #pragma unroll
         for (int q = 0; q < 8; ++q)
             if (q < nval) p.A[i0 + q] = best[q];
+    }
+}
+
+// The block ids of a tile (called by the whole warp), skipping the stores when every
+// point of the tile keeps the block that all its stored ids already hold.  prev is the
+// tile's marker as the filter read it this pass: b when every stored 16-bit id of the
+// tile is b, -1 otherwise; the marker is updated when that changes.  On curve-sorted
+// points most tiles lie inside one block and keep it from pass to pass.
+// Returns whether every point of the tile got the same block.
+__device__ __forceinline__ bool store_blocks_tile(const Prob &p, int t, long long i0, int nval,
+                                                  const int best[8], int prev) {
+    const int b0 = __shfl_sync(0xffffffffu, best[0], 0);  // lane 0 holds a point of the tile
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) same &= q >= nval || best[q] == b0;
+    const bool uni = __all_sync(0xffffffffu, same);
+    if (!p.a16) {
+        store_blocks(p, i0, nval, best);
+        return uni;
+    }
+    if (uni && prev == b0) return true;  // the stored ids are b0 already
+    store_blocks(p, i0, nval, best);
+    const int now = uni ? b0 : -1;
+    if ((threadIdx.x & 31) == 0 && now != prev) reinterpret_cast<int *>(p.tiles)[8 * t + 7] = now;
+    return uni;
+}
+
+// Block weights of a tile all of whose points went to block b (called by lane 0): the
+// tile's point count, or its weight sum formed at the bootstrap with the same fixed-point
+// conversion of every weight as tile_histogram uses.
+__device__ __forceinline__ void tile_weight_to(const Prob &p, int t, int b) {
+    if (p.weighted) {
+        atomic_add_u128(&p.Sfix[2 * b], p.tws[t]);
+    } else {
+        const long long nv = p.n - (long long)t * kTile;
+        atomicAdd(&p.Sfix[2 * b], (unsigned long long)(nv < kTile ? nv : kTile));
     }
 }
 
@@ -1081,8 +1119,11 @@ __device__ __noinline__ void coop_tile(const Prob &p, int t, float *scratch, int
             }
         }
         if (lane == 0) *nevl += (unsigned long long)(p.n - (long long)t * kTile < kTile ? p.n - (long long)t * kTile : kTile);
-        store_blocks(p, i0, nval, best);
-        tile_histogram(p, i0, nval, best);
+        if (store_blocks_tile(p, t, i0, nval, best, __float_as_int(hdr.w))) {
+            if (lane == 0) tile_weight_to(p, t, best[0]);
+        } else {
+            tile_histogram(p, i0, nval, best);
+        }
     }
 }
 
@@ -1134,7 +1175,8 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     // per-point bounds: this pass's index in the phase; a fresh pass evaluates every point
     const int pp = BOUNDS ? p.ctl->phase_pass : 0;
     const bool fresh = !BOUNDS || pp == 0;
-    const unsigned bytes = kRecFastBytes + (unsigned)(D * kTile * 4) + (fresh ? 0u : (unsigned)(kTile * 9));
+    // bytes of one stage's copies besides the record head: coordinate planes (and state)
+    const unsigned bytes_pts = (unsigned)(D * kTile * 4) + (fresh ? 0u : (unsigned)(kTile * 9));
     __shared__ float dm_s[kSkipHist];
     __shared__ unsigned char s_act[kAWarps][kTile];  // the points the warp evaluates
     if (!fresh)
@@ -1150,11 +1192,14 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             __syncthreads();
         }
     }
-    auto issue = [&](int t, int b) {
+    // The record head is copied up to the tile's last candidate only: cnt (1 .. kFastCands,
+    // read from the record when the queue position was resolved) candidates of 2 float4.
+    auto issue = [&](int t, int cnt, int b) {
         if (lane == 0) {
+            const unsigned rec_bytes = (unsigned)(2 + 2 * cnt) * 16u;
             fence_proxy_async();
-            mbar_expect_tx(&bar[w][b], bytes);
-            bulk_g2s(st[w][b].rec, p.trec + (size_t)t * kRecF4, kRecFastBytes, &bar[w][b]);
+            mbar_expect_tx(&bar[w][b], rec_bytes + bytes_pts);
+            bulk_g2s(st[w][b].rec, p.trec + (size_t)t * kRecF4, rec_bytes, &bar[w][b]);
             for (int j = 0; j < D; ++j)
                 bulk_g2s(st[w][b].x[j], p.X32 + (size_t)j * p.n_pad + (size_t)t * kTile, kTile * 4,
                          &bar[w][b]);
@@ -1175,7 +1220,13 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     // warp passes over it without waiting.  A warp's positions increase, so once a
     // stage holds no tile the other one holds none either.  The queue state lives in
     // lane 0 and is broadcast when a stage is consumed.
+    // A tile with a single candidate needs neither its coordinates nor its record: the
+    // filter has proven that every point of the tile goes to that center (without
+    // per-point bounds to keep up), so lane 0 reads the center and the tile's stored-id
+    // marker when it resolves the position and marks the tile (kSingle): no copy, no wait.
     constexpr int kPass = 1 << 30;
+    constexpr int kSingle = 1 << 29;
+    constexpr int kTileMask = kSingle - 1;
     const int qi = (blockIdx.x * kAWarps + w) & (kQueues - 1);
     unsigned *qctr = &p.ctl->tile_q[qi * kQueueStride];
     // position -> tile (ntiles when the queue is empty) and its record count, whose load
@@ -1184,7 +1235,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     // coprime to ntiles, near 0.618 ntiles): the warps working at the same time then
     // hold tiles from all over the curve, whose blocks differ, instead of neighbouring
     // tiles that all add to the weights of the same few blocks.
-    auto resolve = [&](unsigned m, int &tile, int &cnt) {  // lane 0
+    auto resolve = [&](unsigned m, int &tile, int &cnt, int &c1, int &pv) {  // lane 0
         const long long pos = (long long)qi + (long long)kQueues * m;
         if (pos >= p.ntiles) {
             tile = p.ntiles;
@@ -1192,35 +1243,46 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             return;
         }
         tile = tile_of(p, pos);
-        cnt = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4].x));
+        const float4 h = __ldcg(&p.trec[(size_t)tile * kRecF4]);
+        cnt = __float_as_int(h.x);
+        pv = __float_as_int(h.w);
+        c1 = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4 + 3].x));
     };
-    auto mark = [&](int tile, int cnt) -> int {  // kPass for a cooperative tile
-        return (tile < p.ntiles && (cnt < 0 || cnt > kFastCands)) ? (tile | kPass) : tile;
+    auto mark = [&](int tile, int cnt) -> int {  // kPass: cooperative; kSingle: one candidate
+        if (tile >= p.ntiles) return tile;
+        if (cnt < 0 || cnt > kFastCands) return tile | kPass;
+        return (!BOUNDS && cnt == 1) ? (tile | kSingle) : tile;
     };
     int tq0 = p.ntiles, tq1 = p.ntiles, t_next = p.ntiles, c_next = 0;
+    int c1_0 = 0, c1_1 = 0, pv_0 = -1, pv_1 = -1, c1_next = 0, pv_next = -1;  // single tiles
     unsigned m_req = 0;
     if (lane == 0) {
         const unsigned m0 = atomicAdd(qctr, 1u), m1 = atomicAdd(qctr, 1u), m2 = atomicAdd(qctr, 1u);
         m_req = atomicAdd(qctr, 1u);
         int c0, c1;
-        resolve(m0, tq0, c0);
-        resolve(m1, tq1, c1);
-        resolve(m2, t_next, c_next);
+        resolve(m0, tq0, c0, c1_0, pv_0);
+        resolve(m1, tq1, c1, c1_1, pv_1);
+        resolve(m2, t_next, c_next, c1_next, pv_next);
         tq0 = mark(tq0, c0);
         tq1 = mark(tq1, c1);
-        if (tq0 < p.ntiles) issue(tq0, 0);
-        if (tq1 < p.ntiles) issue(tq1, 1);
+        if (tq0 < p.ntiles) issue(tq0, c0, 0);
+        if (tq1 < p.ntiles) issue(tq1, c1, 1);
     }
     // stage b is free again: load the next tile into it (lane 0)
     auto refill = [&](int b) {
         if (lane == 0) {
             const int tn = mark(t_next, c_next);
-            if (b)
+            if (b) {
                 tq1 = tn;
-            else
+                c1_1 = c1_next;
+                pv_1 = pv_next;
+            } else {
                 tq0 = tn;
-            if (tn < p.ntiles) issue(tn, b);
-            resolve(m_req, t_next, c_next);
+                c1_0 = c1_next;
+                pv_0 = pv_next;
+            }
+            if (tn < p.ntiles) issue(tn, c_next, b);
+            resolve(m_req, t_next, c_next, c1_next, pv_next);
             m_req = atomicAdd(qctr, 1u);
         }
     };
@@ -1228,9 +1290,25 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     for (int it = 0;; ++it) {
         const int b = it & 1;
         const int tqb = __shfl_sync(0xffffffffu, b ? tq1 : tq0, 0);
-        if ((tqb & (kPass - 1)) >= p.ntiles) break;  // the other stage holds no tile either
+        if ((tqb & kTileMask) >= p.ntiles) break;  // the other stage holds no tile either
         if (tqb & kPass) {  // a cooperative tile: nothing was copied into this stage
             refill(b);
+            continue;
+        }
+        if (!BOUNDS && (tqb & kSingle)) {  // every point of the tile goes to center c1
+            const int t = tqb & kTileMask;
+            const int c1 = __shfl_sync(0xffffffffu, b ? c1_1 : c1_0, 0);
+            const int pv = __shfl_sync(0xffffffffu, b ? pv_1 : pv_0, 0);
+            refill(b);
+            const long long t0 = (long long)t * kTile, i0 = t0 + lane * 8;
+            const long long nv = p.n - i0;
+            const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+            nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
+            int best[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) best[q] = c1;
+            store_blocks_tile(p, t, i0, nval, best, pv);
+            if (lane == 0) tile_weight_to(p, t, c1);
             continue;
         }
         const int t = tqb;
@@ -1250,6 +1328,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         const int ncand = __float_as_int(S.rec[0].x);  // 0 < ncand <= kFastCands
         const float gl = S.rec[0].y;    // largest g among the tile's candidates
         const float lamT = S.rec[0].z;  // lower bound of the E of every center left out
+        const int prev_id = __float_as_int(S.rec[0].w);  // the tile's stored-id marker
         const float sg = sqrtf(gl);
         const float4 ob = S.rec[1];
         const float o[3] = {ob.x, ob.y, ob.z};
@@ -1263,6 +1342,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         const float beta2 = ((float)D + 4.0f + 8.0f * sd) * kU;
         const float e0 = sd * kU * (p.R + 8.0f * __fmul_ru(ob.w, 1.0f + 9.5367431640625e-7f));
         int best[8];
+        bool uni = false;  // every point of the tile in one block
         if (fresh) {
             // every point is evaluated: lane l takes points 8l..8l+7
             nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
@@ -1441,7 +1521,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             }
             __syncwarp();  // every lane is done with stage b
             refill(b);
-            store_blocks(p, i0, nval, best);
+            uni = store_blocks_tile(p, t, i0, nval, best, prev_id);
         } else {
             if constexpr (BOUNDS) {
                 int *blk = S.a;  // old block ids (bounds), then this pass's
@@ -1613,7 +1693,11 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
                 refill(b);
                     }
         }
-        tile_histogram(p, i0, nval, best);
+        if (uni) {
+            if (lane == 0) tile_weight_to(p, t, best[0]);
+        } else {
+            tile_histogram(p, i0, nval, best);
+        }
     }
     if (F64MODE) {
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
@@ -1802,18 +1886,108 @@ struct KeyOf<double> {
     __device__ static unsigned long long key(double v) { return okey_f64(v); }
 };
 
+// The lane's 8 consecutive values of a plane starting at i0 (16-byte vector loads when
+// all 8 are points; the padding of the planes keeps the loads inside the buffers).
+template <typename T>
+__device__ __forceinline__ void load8(const T *src, long long i0, int nval, T v[8]) {
+    if (nval == 8) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 a = reinterpret_cast<const float4 *>(src + i0)[0];
+            const float4 b = reinterpret_cast<const float4 *>(src + i0)[1];
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const double2 a = reinterpret_cast<const double2 *>(src + i0)[h];
+                v[2 * h] = a.x;
+                v[2 * h + 1] = a.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = q < nval ? src[i0 + q] : (T)0;
+    }
+}
+
+// A tile all of whose points lie in one block (most tiles: a block of curve-sorted
+// points spans many tiles): lane sums of the 8 points' fixed-point values and ordered-key
+// extremes, one warp reduction, one set of atomics for the tile.  The values are the
+// ones the run-by-run path below forms (same conversions, integer sums, the same keys),
+// so the result does not depend on which path a tile takes.  Returns false (nothing
+// done) when the tile holds more than one block id or an id outside [0, k).
 template <typename T, int D>
-__global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
-    count_launch(p.ctl);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int pos = blockIdx.x * kAssignWarps + w;
-    if (pos >= p.ntiles) return;
-    // the tile order of the assignment: neighbouring warps take tiles of different blocks
-    const int t = tile_of(p, pos);
+__device__ __forceinline__ bool centroid_uniform_tile(const Prob &p, const T *X, long long i0, int nval) {
+    int ids[8];
+    if (nval == 8 && p.a16) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(p.A16 + i0);
+        const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            ids[2 * h] = (int)(u[h] & 0xffffu);
+            ids[2 * h + 1] = (int)(u[h] >> 16);
+        }
+    } else if (nval == 8) {
+        const int4 a = reinterpret_cast<const int4 *>(p.A + i0)[0];
+        const int4 b = reinterpret_cast<const int4 *>(p.A + i0)[1];
+        ids[0] = a.x; ids[1] = a.y; ids[2] = a.z; ids[3] = a.w;
+        ids[4] = b.x; ids[5] = b.y; ids[6] = b.z; ids[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ids[q] = q < nval ? (p.a16 ? (int)p.A16[i0 + q] : p.A[i0 + q]) : 0;
+    }
+    const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) same &= q >= nval || ids[q] == b0;
+    if (!__all_sync(0xffffffffu, same) || (unsigned)b0 >= (unsigned)p.k) return false;
+    T wv[8];
+    if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        T xv[8];
+        load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
+        long long sum = 0;
+        unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nval) {
+                long long v;
+                if (sizeof(T) == 8)
+                    v = p.weighted ? fix_f64((double)wv[q] * (double)xv[q], p.Fx) : fix_f64((double)xv[q], p.Fx);
+                else
+                    v = p.weighted ? fix_prod_f32((float)wv[q], (float)xv[q], p.Fx) : fix_f32((float)xv[q], p.Fx);
+                sum += v;
+                const unsigned long long kk = KeyOf<T>::key(xv[q]);
+                kmin = kk < kmin ? kk : kmin;
+                kmax = kk > kmax ? kk : kmax;
+            }
+        }
+        for (int off = 16; off; off >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, off);
+            const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+            kmin = a < kmin ? a : kmin;
+            kmax = b > kmax ? b : kmax;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomic_add_i128(&p.SXfix[2 * (b0 * D + j)], sum);
+            atomicMin(&p.BBlo[b0 * D + j], kmin);
+            atomicMax(&p.BBhi[b0 * D + j], kmax);
+        }
+    }
+    return true;
+}
+
+// One tile point by point (called by the whole warp): lane l takes points 8l..8l+7;
+// runs of equal block ids inside the lane, then a segmented reduction over the lanes.
+template <typename T, int D>
+__device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
+    const int lane = threadIdx.x & 31;
     const long long i0 = (long long)t * kTile + lane * 8;
     long long nv = p.n - i0;
     const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
+    if (centroid_uniform_tile<T, D>(p, X, i0, nval)) return;
     int cur = -1;
     long long sum[D];
     unsigned long long kmin[D], kmax[D];
@@ -1890,6 +2064,75 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
             atomicMax(&p.BBhi[cur * D + j], kmax[j]);
         }
     }
+}
+
+// Center movement, part 1 (Algorithm 2, the weighted means; the block boxes of the
+// erosion's beta): one warp per 32 consecutive tiles, lane = tile.  A tile whose stored
+// block ids are all b (its marker, kept by the assignment) adds its coordinate sums and
+// box, formed once at the bootstrap with the same conversions, to block b: a segmented
+// reduction over the lanes, then one set of atomics per run of equal blocks.  The other
+// tiles are then taken one at a time by the whole warp, point by point.
+template <typename T, int D>
+__global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
+    count_launch(p.ctl);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long t = ((long long)blockIdx.x * kAssignWarps + w) * 32 + lane;
+    const bool has = t < p.ntiles;
+    const int mk = has ? reinterpret_cast<const int *>(p.tiles)[8 * t + 7] : -2;
+    const int cur = mk >= 0 && mk < p.k ? mk : -1;
+    long long sum[D];
+    unsigned long long kmin[D], kmax[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        sum[j] = cur >= 0 ? p.tsx[t * D + j] : 0;
+        kmin[j] = cur >= 0 ? p.tlo[t * D + j] : ~0ull;
+        kmax[j] = cur >= 0 ? p.thi[t * D + j] : 0ull;
+    }
+    int prev = __shfl_up_sync(0xffffffffu, cur, 1);
+    bool head = lane == 0 || cur != prev;
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        bool take = lane - off >= start;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            long long s2 = __shfl_up_sync(0xffffffffu, sum[j], off);
+            unsigned long long a = __shfl_up_sync(0xffffffffu, kmin[j], off);
+            unsigned long long b = __shfl_up_sync(0xffffffffu, kmax[j], off);
+            if (take) {
+                sum[j] += s2;
+                kmin[j] = a < kmin[j] ? a : kmin[j];
+                kmax[j] = b > kmax[j] ? b : kmax[j];
+            }
+        }
+    }
+    bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (end && cur >= 0) {
+        for (int j = 0; j < D; ++j) {
+            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
+            atomicMin(&p.BBlo[cur * D + j], kmin[j]);
+            atomicMax(&p.BBhi[cur * D + j], kmax[j]);
+        }
+    }
+    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
+    unsigned rest = __ballot_sync(0xffffffffu, has && cur < 0);
+    while (rest) {
+        const int L = __ffs(rest) - 1;
+        rest &= rest - 1;
+        centroid_tile<T, D>(p, X, (int)(t - lane + L));
+    }
+}
+
+// The same without tile markers: one tile per warp, in the assignment's permuted tile
+// order (neighbouring warps take tiles of different blocks).
+template <typename T, int D>
+__global__ void __launch_bounds__(kAssignWarps * 32) centroid_points_kernel(Prob p) {
+    count_launch(p.ctl);
+    const int pos = blockIdx.x * kAssignWarps + (threadIdx.x >> 5);
+    if (pos >= p.ntiles) return;
+    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
+    centroid_tile<T, D>(p, X, tile_of(p, pos));
 }
 
 // ------------------------------------------------------------------------------
@@ -2066,7 +2309,7 @@ static void *filter_big_fn(int d) {
     return d == 2 ? (void *)filter_big_kernel<2> : (void *)filter_big_kernel<3>;
 }
 static dim3 filter_big_grid(const Prob &p) {
-    const long long need = ((long long)p.nsupers * kSuperTiles + kFilterWarps - 1) / kFilterWarps;
+    const long long need = ((long long)p.nsupers * p.stiles + kFilterWarps - 1) / kFilterWarps;
     const long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * 8;
     return dim3((unsigned)(need < cap ? need : cap));
 }
@@ -2078,11 +2321,22 @@ static void *assign_fn(const Prob &p) {
     if (p.d == 2) return p.assign_f64 ? (void *)assign_kernel<2, true, false> : (void *)assign_kernel<2, false, false>;
     return p.assign_f64 ? (void *)assign_kernel<3, true, false> : (void *)assign_kernel<3, false, false>;
 }
-static void *centroid_fn(int d, int dtype) {
-    if (dtype == 1) return d == 2 ? (void *)centroid_kernel<double, 2> : (void *)centroid_kernel<double, 3>;
-    return d == 2 ? (void *)centroid_kernel<float, 2> : (void *)centroid_kernel<float, 3>;
+// The movement's accumulation: by tile markers when the assignment keeps them (16-bit
+// block ids), else one tile per warp in the assignment's permuted tile order.
+static void *centroid_fn(const Prob &p) {
+    if (p.a16) {
+        if (p.dtype == 1) return p.d == 2 ? (void *)centroid_kernel<double, 2> : (void *)centroid_kernel<double, 3>;
+        return p.d == 2 ? (void *)centroid_kernel<float, 2> : (void *)centroid_kernel<float, 3>;
+    }
+    if (p.dtype == 1)
+        return p.d == 2 ? (void *)centroid_points_kernel<double, 2> : (void *)centroid_points_kernel<double, 3>;
+    return p.d == 2 ? (void *)centroid_points_kernel<float, 2> : (void *)centroid_points_kernel<float, 3>;
 }
-static int tile_warp_grid(const Prob &p) { return (p.ntiles + kAssignWarps - 1) / kAssignWarps; }
+// the movement's accumulation: one warp per 32 consecutive tiles, or per tile
+static int tile_warp_grid(const Prob &p) {
+    const int per = p.a16 ? kAssignWarps * 32 : kAssignWarps;
+    return (p.ntiles + per - 1) / per;
+}
 
 // Supergroup records of the current buffer, after every change of the group records.
 static void launch_supergroups(const Prob &p, cudaStream_t s) {
@@ -2114,11 +2368,17 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
 }
+// resident CTAs per SM: registers (FP64 mode) or the stages' shared memory (3-D)
+int assign_max_ctas(const Prob &p) {
+    return p.assign_f64 ? kAMinBlocks64 : ((p.bounds && p.d == 3) ? 4 : kAMinBlocks);
+}
+int assign_ctas(const Prob &p) {
+    const int m = assign_max_ctas(p);
+    return (p.actas > 0 && p.actas < m) ? p.actas : m;
+}
 static int assign_grid(const Prob &p) {
     int need = (p.ntiles + kAWarps - 1) / kAWarps;
-    // resident CTAs per SM: registers (FP64 mode) or the stages' shared memory (3-D)
-    const int per_sm = p.assign_f64 ? kAMinBlocks64 : ((p.bounds && p.d == 3) ? 4 : kAMinBlocks);
-    int cap = (p.nsm > 0 ? p.nsm : 152) * per_sm;
+    int cap = (p.nsm > 0 ? p.nsm : 152) * assign_ctas(p);
     return need < cap ? need : cap;
 }
 static size_t assign_smem_of(const Prob &p) {
@@ -2157,9 +2417,22 @@ cudaError_t launch_block_weights(const Prob &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_centroid(const Prob &p, cudaStream_t s) {
+    void *args1[] = {(void *)&p};
+    return cudaLaunchKernel(centroid_fn(p), dim3(tile_warp_grid(p)), dim3(kAssignWarps * 32),
+                            args1, 0, s);
+}
+cudaError_t launch_move_finish(const Prob &p, int mode, cudaStream_t s) {
+    finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
+    if (mode == 0 || mode == 3) {
+        finalize_b_kernel<<<kgrid(p), kKThreads, 0, s>>>(p);
+        launch_supergroups(p, s);
+    }
+    return cudaGetLastError();
+}
 cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    cudaError_t e = cudaLaunchKernel(centroid_fn(p.d, p.dtype), dim3(tile_warp_grid(p)),
+    cudaError_t e = cudaLaunchKernel(centroid_fn(p), dim3(tile_warp_grid(p)),
                                      dim3(kAssignWarps * 32), args1, 0, s);
     if (e != cudaSuccess) return e;
     finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
@@ -2269,7 +2542,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
             if (p.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
             if (bl.err != cudaSuccess) mv.err = bl.err;
         }
-        mv.kernel(centroid_fn(p.d, p.dtype), tg, tb, a_p);
+        mv.kernel(centroid_fn(p), tg, tb, a_p);
         mv.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
         mv.kernel((void *)finalize_b_kernel, kg, kb, a_p);
         if (p.nsgroups > 0) mv.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
@@ -2330,7 +2603,7 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
         if (ps.nsgroups > 0) bl.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
         if (bl.err != cudaSuccess) top.err = bl.err;
     }
-    top.kernel(centroid_fn(ps.d, ps.dtype), tg, tb, a_p);
+    top.kernel(centroid_fn(ps), tg, tb, a_p);
     top.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
     top.kernel((void *)finalize_b_kernel, kg, kb, a_p);
     if (ps.nsgroups > 0) top.kernel((void *)supergroup_kernel, sgg, sgb, a_p);

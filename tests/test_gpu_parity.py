@@ -542,3 +542,44 @@ def test_allocation_failure_is_reported(gk):
         gk.set_allocator()
     block, C, I, res = gk.partition(x, 8, 0.03)
     assert res["balanced"] == 1
+
+
+# ----------------------------------------------------------------------------------------
+# Launch shapes (gk_options.supertile_tiles, assign_ctas_per_sm): the speed changes, the
+# results do not; the tuner picks one of the candidates and reports it.
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,d,dtype,n,k,assign", [("gmm", 3, "f64", 60_000, 48, "f64"),
+                                                      ("spots", 2, "f32", 200_000, 300, "f32"),
+                                                      ("uniform", 2, "f64", 30_000, 2500, "f64")])
+def test_every_launch_shape_gives_the_same_partition(gk, shape, d, dtype, n, k, assign):
+    x = _points(shape, n, d, 71, dtype)
+    outs = []
+    for stl in (16, 32):
+        for ctas in (1, 2, 5):
+            o = gk.default_options(assign_dtype=assign, supertile_tiles=stl, assign_ctas_per_sm=ctas)
+            block, C, I, res = gk.partition(_dev(x), k, 0.03, options=o)
+            assert res["supertile_tiles"] == stl and res["tune_ms"] == 0.0
+            assert 1 <= res["assign_ctas_per_sm"] <= ctas
+            outs.append((_np(block), _np(C), _np(I), res["balance_passes"]))
+    o = gk.default_options(assign_dtype=assign)  # tuned
+    block, C, I, res = gk.partition(_dev(x), k, 0.03, options=o)
+    assert res["supertile_tiles"] in (16, 32) and res["assign_ctas_per_sm"] >= 1
+    outs.append((_np(block), _np(C), _np(I), res["balance_passes"]))
+    for b, C1, I1, passes in outs[1:]:
+        assert np.array_equal(b, outs[0][0]) and np.array_equal(C1, outs[0][1])
+        assert np.array_equal(I1, outs[0][2]) and passes == outs[0][3]
+    if assign == "f64":
+        ref = oracle.partition(x, None, k, 0.03, oracle.default_options(threads=THREADS))
+        assert np.array_equal(outs[0][0], ref["A"])
+    # a second tuned call of the same kind takes the cached shape (no measurement)
+    _, _, _, res2 = gk.partition(_dev(x), k, 0.03, options=o)
+    assert res2["tune_ms"] == 0.0 and res2["supertile_tiles"] == res["supertile_tiles"]
+    assert res2["assign_ctas_per_sm"] == res["assign_ctas_per_sm"]
+
+
+def test_launch_shape_options_are_checked(gk):
+    x = _dev(np.random.default_rng(0).random((1000, 2)))
+    for bad in (dict(supertile_tiles=8), dict(supertile_tiles=64), dict(assign_ctas_per_sm=-1)):
+        with pytest.raises(gk.GKError) as e:
+            gk.partition(x, 4, 0.03, options=gk.default_options(**bad))
+        assert e.value.status == gk.GK_ERR_INVALID_ARG
