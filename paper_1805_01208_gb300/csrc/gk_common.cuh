@@ -274,6 +274,13 @@ __device__ __forceinline__ void atomic_add_i128(unsigned long long *lohi, long l
     unsigned long long hinc = (v < 0 ? ~0ull : 0ull) + carry;
     if (hinc) atomicAdd(lohi + 1, hinc);
 }
+// A full 128-bit addend (two's complement, low word lo, high word hi).
+__device__ __forceinline__ void atomic_add_i128_full(unsigned long long *lohi, unsigned long long lo,
+                                                     unsigned long long hi) {
+    const unsigned long long old = atomicAdd(lohi, lo);
+    const unsigned long long hinc = hi + ((old + lo < old) ? 1ull : 0ull);
+    if (hinc) atomicAdd(lohi + 1, hinc);
+}
 __device__ __forceinline__ void atomic_add_u128(unsigned long long *lohi, unsigned long long v) {
     unsigned long long old = atomicAdd(lohi, v);
     if (old + v < old) atomicAdd(lohi + 1, 1ull);

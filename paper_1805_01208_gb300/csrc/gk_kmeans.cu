@@ -2070,8 +2070,10 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
 // erosion's beta): one warp per 32 consecutive tiles, lane = tile.  A tile whose stored
 // block ids are all b (its marker, kept by the assignment) adds its coordinate sums and
 // box, formed once at the bootstrap with the same conversions, to block b: a segmented
-// reduction over the lanes, then one set of atomics per run of equal blocks.  The other
-// tiles are then taken one at a time by the whole warp, point by point.
+// reduction over the lanes, then one set of atomics per run of equal blocks.  A tile sum
+// is below 2^62 in magnitude (256 values below 2^54), so the reduction over up to 32
+// tiles carries 128 bits.  The other tiles are then taken one at a time by the whole
+// warp, point by point.
 template <typename T, int D>
 __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     count_launch(p.ctl);
@@ -2080,11 +2082,13 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     const bool has = t < p.ntiles;
     const int mk = has ? reinterpret_cast<const int *>(p.tiles)[8 * t + 7] : -2;
     const int cur = mk >= 0 && mk < p.k ? mk : -1;
-    long long sum[D];
+    unsigned long long slo[D], shi[D];  // 128-bit sums (two's complement)
     unsigned long long kmin[D], kmax[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        sum[j] = cur >= 0 ? p.tsx[t * D + j] : 0;
+        const long long v = cur >= 0 ? p.tsx[t * D + j] : 0;
+        slo[j] = (unsigned long long)v;
+        shi[j] = v < 0 ? ~0ull : 0ull;
         kmin[j] = cur >= 0 ? p.tlo[t * D + j] : ~0ull;
         kmax[j] = cur >= 0 ? p.thi[t * D + j] : 0ull;
     }
@@ -2097,11 +2101,14 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
         bool take = lane - off >= start;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            long long s2 = __shfl_up_sync(0xffffffffu, sum[j], off);
+            const unsigned long long l2 = __shfl_up_sync(0xffffffffu, slo[j], off);
+            const unsigned long long h2 = __shfl_up_sync(0xffffffffu, shi[j], off);
             unsigned long long a = __shfl_up_sync(0xffffffffu, kmin[j], off);
             unsigned long long b = __shfl_up_sync(0xffffffffu, kmax[j], off);
             if (take) {
-                sum[j] += s2;
+                const unsigned long long lo = slo[j] + l2;
+                shi[j] += h2 + (lo < l2 ? 1ull : 0ull);
+                slo[j] = lo;
                 kmin[j] = a < kmin[j] ? a : kmin[j];
                 kmax[j] = b > kmax[j] ? b : kmax[j];
             }
@@ -2110,7 +2117,7 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
     if (end && cur >= 0) {
         for (int j = 0; j < D; ++j) {
-            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
+            atomic_add_i128_full(&p.SXfix[2 * (cur * D + j)], slo[j], shi[j]);
             atomicMin(&p.BBlo[cur * D + j], kmin[j]);
             atomicMax(&p.BBhi[cur * D + j], kmax[j]);
         }
