@@ -444,7 +444,7 @@ def _config_leg(gk, name, stream, flush, steps, x=None, w=None, spec=None):
            "balanced": res["balanced"], "max_imbalance": res["max_imbalance"],
            "bootstrap_ms": res["time_bootstrap_ms"], "avg_candidates": res["avg_candidates"],
            "assign_ms_per_pass_live": res["assign_live_ms"] / max(1, res["assign_live_launches"]),
-           "launch_shapes": {"supertile_tiles": res["supertile_tiles"],
+           "launch_shapes": {"supertile_tiles": res["supertile_tiles"], "hypertiles": res["hypertiles"],
                              "assign_ctas_per_sm": res["assign_ctas_per_sm"]},
            "roofline": _roofline(gk, xt, wt, spec, name)}
     if spec["assign"] == "f32":
@@ -603,11 +603,14 @@ def main():
 
     # ---- launch shapes: the tuned ones against the fixed defaults of the kernels -----------
     shapes = {"supertile_tiles": last["supertile_tiles"], "assign_ctas_per_sm": last["assign_ctas_per_sm"],
+              "hypertiles": last["hypertiles"],
               "tune_ms_first_call": warm[0]["tune_ms"] if warm else None}
-    ofix = gk.default_options(assign_dtype=spec["assign"], supertile_tiles=16, assign_ctas_per_sm=64)
+    ofix = gk.default_options(assign_dtype=spec["assign"], supertile_tiles=16, hypertiles=1,
+                              assign_ctas_per_sm=64)
     step(ofix)
     tfix, rfix = _timed(stream, flush, lambda: step(ofix), max(1, min(2, args.steps)))
-    shapes["fixed"] = {"supertile_tiles": 16, "assign_ctas_per_sm": rfix[-1][3]["assign_ctas_per_sm"],
+    shapes["fixed"] = {"supertile_tiles": 16, "hypertiles": 1,
+                       "assign_ctas_per_sm": rfix[-1][3]["assign_ctas_per_sm"],
                        "ms_per_step": float(np.mean(tfix))}
     shapes["tuned_speedup_vs_fixed"] = float(np.mean(tfix)) / ms_per_step
     del rfix

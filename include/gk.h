@@ -86,7 +86,11 @@ typedef struct gk_options {
                                    (4 warps each, a tile of 256 points per warp and stage):
                                    1 .. the kernel's maximum (larger values are clamped);
                                    0 (default): chosen by the tuner                        */
-    int32_t reserved[2];        /* must be zero                                           */
+    int32_t hypertiles;         /* the filter's first level per hypertile of 16 supertiles,
+                                   each supertile's list then taken from its hypertile's
+                                   (same lists, less work for large k): 1 off, 2 on;
+                                   0 (default): chosen by the tuner                        */
+    int32_t reserved[1];        /* must be zero                                           */
 } gk_options;
 
 /* Outcome and counters of one call. */
@@ -121,6 +125,8 @@ typedef struct gk_result {
                                    n x passes without bounds)                               */
     int32_t supertile_tiles;    /* the launch shapes used (given or tuned)                 */
     int32_t assign_ctas_per_sm;
+    int32_t hypertiles;         /* 1 off, 2 on                                             */
+    int32_t reserved1;
     double tune_ms;             /* device time the tuner spent measuring (0: shapes given or
                                    taken from its cache)                                   */
 } gk_result;
@@ -129,8 +135,9 @@ typedef struct gk_result {
  * Launch-shape tuner.  A field of gk_options left 0 is chosen by measurement: on the first
  * call for a kind of problem (d, input and assignment precision, weights, bounds, and the
  * powers of two of n and k), after the bootstrap, the filter and assignment of the
- * problem's first pass run once per candidate shape (supertiles of 16 or 32 tiles; the
- * assignment's largest CTA count per SM and the two below it), the state is restored,
+ * problem's first pass run once per candidate shape (supertiles of 16 or 32 tiles, with
+ * and without the hypertile level; the assignment's largest CTA count per SM and the one
+ * below it), the state is restored,
  * and the fastest shape is kept in a process-wide cache for later calls of that kind.
  * gk_partition_batched tunes every instance by its own kind.  The shapes change the
  * speed only: every shape gives the same results.
@@ -343,8 +350,9 @@ typedef struct gk_diameter {
  *   diam_out: k int32 (nullable): the bound of each block, -1 for a block that is not
  *             connected, 0 for an empty block;
  *   summary:  nullable.
- * Every pointer may be host or device memory.  The host waits for the stream once per
- * breadth-first level (to size the next launch), so the call returns with its work done.
+ * Every pointer may be host or device memory.  The host enqueues 16 breadth-first levels at
+ * a time (each reads its frontier's length on the device) and reads the length of the
+ * next frontier after them; the call returns with its work done.
  * Malformed input gives GK_ERR_INVALID_ARG (found on the device, before any search).
  * Requires 1 <= n < 2^31, nnz >= 0, k >= 1.
  */

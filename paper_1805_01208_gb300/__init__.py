@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
         ("bounds", ctypes.c_int32),
         ("supertile_tiles", ctypes.c_int32),
         ("assign_ctas_per_sm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("hypertiles", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -83,11 +84,14 @@ class Result(ctypes.Structure):
         ("evaluated_points", ctypes.c_int64),
         ("supertile_tiles", ctypes.c_int32),
         ("assign_ctas_per_sm", ctypes.c_int32),
+        ("hypertiles", ctypes.c_int32),
+        ("reserved1", ctypes.c_int32),
         ("tune_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved0"}
+        return {name: getattr(self, name) for name, _ in self._fields_
+                if name not in ("reserved0", "reserved1")}
 
 
 class Instance(ctypes.Structure):

@@ -216,6 +216,13 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.coop = (int *)take((size_t)p.ntiles * 4);
     p.bigs = (int *)take((size_t)p.nsupers * 16);
     p.blists = (int *)take((size_t)p.nsupers * kWarpList * 4);
+    {
+        const long long nh = (p.nsupers + kHyperSupers - 1) / kHyperSupers;
+        p.hypers = (float4 *)take((size_t)nh * 32);
+        p.hlists = (int *)take((size_t)nh * kWarpList * 4);
+        p.hlen = (int *)take((size_t)nh * 4);
+        p.hlam = (float *)take((size_t)nh * 4);
+    }
     p.C = (double *)take((size_t)k * d * 8);
     p.Cm = (double *)take((size_t)k * d * 8);
     p.delta = (double *)take((size_t)k * 8);
@@ -263,6 +270,9 @@ struct SampleBufs {
     long long *tsx = nullptr;
     unsigned long long *tlo = nullptr, *thi = nullptr;
     int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
+    float4 *hypers = nullptr;
+    int *hlists = nullptr, *hlen = nullptr;
+    float *hlam = nullptr;
     float *prho = nullptr;            // per-point bounds of the sample
     unsigned char *pt1 = nullptr;
 };
@@ -299,6 +309,13 @@ size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order
     sb.coop = (int *)take((size_t)nt * 4);
     sb.bigs = (int *)take((size_t)ns * 16);
     sb.blists = (int *)take((size_t)ns * kWarpList * 4);
+    {
+        const long long nh = (ns + kHyperSupers - 1) / kHyperSupers;
+        sb.hypers = (float4 *)take((size_t)nh * 32);
+        sb.hlists = (int *)take((size_t)nh * kWarpList * 4);
+        sb.hlen = (int *)take((size_t)nh * 4);
+        sb.hlam = (float *)take((size_t)nh * 4);
+    }
     sb.prho = (float *)take((size_t)np * 4);
     sb.pt1 = (unsigned char *)take((size_t)np);
     return off;
@@ -391,7 +408,7 @@ gk_status check_common(const void *coords, int32_t dtype, int64_t n, int32_t d) 
 // Launch-shape tuner cache: the shapes measured fastest per kind of problem.
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;  // d, dtype, f64, w, bounds, log2 n, log2 k
 struct TuneChoice {
-    int stiles, actas;
+    int stiles, hyper, actas;
 };
 std::map<TuneKey, TuneChoice> g_tune;
 std::mutex g_tune_mu;
@@ -423,6 +440,7 @@ struct Call {
         p.ntiles = (int)(p.n_pad / kTile);
         p.stiles = kSuperTiles;
         p.nsupers = (p.ntiles + kSuperTiles - 1) / kSuperTiles;
+        p.nhypers = (p.nsupers + kHyperSupers - 1) / kHyperSupers;
         p.qmul = tile_order_multiplier(p.ntiles);
         p.tile_magic = ~0ull / (unsigned long long)p.ntiles;
         p.bits = d == 2 ? 32 : 21;
@@ -549,9 +567,11 @@ struct Call {
     Exchange *ex = nullptr;
     float tune_ms = 0.f;
 
-    void apply_shape(int stiles, int actas) {
+    void apply_shape(int stiles, int hyper, int actas) {
         p.stiles = stiles;
+        p.hyper = hyper;
         p.nsupers = (p.ntiles + stiles - 1) / stiles;
+        p.nhypers = (p.nsupers + kHyperSupers - 1) / kHyperSupers;
         p.actas = actas;
     }
     // The launch shapes (gk_options supertile_tiles, assign_ctas_per_sm; 0: tuned).  Runs
@@ -560,20 +580,25 @@ struct Call {
     // weights; the stored block ids and tile markers the trials wrote are those of the
     // first pass, consistent with each other).
     gk_status tune(const gk_options &o) {
-        std::vector<int> sts, cts;
+        std::vector<int> sts, hys, cts;
         if (o.supertile_tiles)
             sts.push_back(o.supertile_tiles);
         else
             sts = {kSuperTiles, kMaxSuperTiles};
+        if (o.hypertiles)
+            hys.push_back(o.hypertiles == 2 ? 1 : 0);
+        else
+            hys = {0, 1};
         const int mc = assign_max_ctas(p);
         if (o.assign_ctas_per_sm)
             cts.push_back(o.assign_ctas_per_sm < mc ? o.assign_ctas_per_sm : mc);
         else
-            for (int c = mc; c >= 1 && c >= mc - 2; --c) cts.push_back(c);
-        TuneChoice best{sts[0], cts[0]};
+            for (int c = mc; c >= 1 && c >= mc - 1; --c) cts.push_back(c);
+        TuneChoice best{sts[0], hys[0], cts[0]};
+        const size_t ncand = sts.size() * hys.size() * cts.size();
         const TuneKey key{p.d, p.dtype, p.assign_f64, p.weighted, p.bounds, ilog2(p.n), ilog2(p.k)};
         bool cached = false;
-        if (sts.size() * cts.size() > 1) {
+        if (ncand > 1) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {
@@ -581,7 +606,7 @@ struct Call {
                 cached = true;
             }
         }
-        if (sts.size() * cts.size() > 1 && !cached) {
+        if (ncand > 1 && !cached) {
             gk_status st = read_ctl();
             if (st != GK_OK) return st;
             const Ctl saved = *g_ws.host_ctl;
@@ -589,10 +614,11 @@ struct Call {
             float best_ms = INFINITY;
             cudaEvent_t e0 = g_ws.kev[0], e1 = g_ws.kev[1];
             for (int stl : sts) {
-                apply_shape(stl, cts[0]);
+                apply_shape(stl, 0, cts[0]);
                 GK_CUDA(launch_super_boxes(p, s));
+                for (int hy : hys)
                 for (int c : cts) {
-                    apply_shape(stl, c);
+                    apply_shape(stl, hy, c);
                     float ms_min = INFINITY;
                     for (int rep = 0; rep < 3; ++rep) {
                         GK_CUDA(cudaEventRecord(e0, s));
@@ -609,7 +635,7 @@ struct Call {
                     }
                     if (ms_min < best_ms) {
                         best_ms = ms_min;
-                        best = {stl, c};
+                        best = {stl, hy, c};
                     }
                 }
             }
@@ -617,7 +643,7 @@ struct Call {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune[key] = best;
         }
-        apply_shape(best.stiles, best.actas);
+        apply_shape(best.stiles, best.hyper, best.actas);
         GK_CUDA(launch_super_boxes(p, s));
         return GK_OK;
     }
@@ -695,6 +721,7 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     r->evaluated_points = (int64_t)c.evaluated;
     r->supertile_tiles = cl.p.stiles;
     r->assign_ctas_per_sm = assign_ctas(cl.p);
+    r->hypertiles = cl.p.hyper ? 2 : 1;
     r->tune_ms = cl.tune_ms;
 }
 
@@ -822,6 +849,11 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.coop = sb.coop;
     ps.bigs = sb.bigs;
     ps.blists = sb.blists;
+    ps.hypers = sb.hypers;
+    ps.hlists = sb.hlists;
+    ps.hlen = sb.hlen;
+    ps.hlam = sb.hlam;
+    ps.nhypers = (ps.nsupers + kHyperSupers - 1) / kHyperSupers;
     ps.lq = sb.prho;
     ps.t1 = sb.pt1;
     ps.ctl = sb.ctl;
@@ -897,8 +929,8 @@ gk_status check_options(const gk_options &o) {
     if (o.supertile_tiles != 0 && o.supertile_tiles != kSuperTiles && o.supertile_tiles != kMaxSuperTiles)
         return GK_ERR_INVALID_ARG;
     if (o.assign_ctas_per_sm < 0 || o.assign_ctas_per_sm > 64) return GK_ERR_INVALID_ARG;
-    for (int i = 0; i < 2; ++i)
-        if (o.reserved[i] != 0) return GK_ERR_INVALID_ARG;
+    if (o.hypertiles < 0 || o.hypertiles > 2) return GK_ERR_INVALID_ARG;
+    if (o.reserved[0] != 0) return GK_ERR_INVALID_ARG;
     return GK_OK;
 }
 

@@ -652,6 +652,33 @@ __global__ void super_box_kernel(Prob p) {
     p.supers[2 * s + 1] = make_float4(h[0], h[1], h[2], 0.0f);
 }
 
+// Hypertile boxes from the boxes of their supertiles (rounded outwards).
+__global__ void hyper_box_kernel(Prob p) {
+    count_launch(p.ctl);
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= p.nhypers) return;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    int s0 = h * kHyperSupers, s1 = min(p.nsupers, s0 + kHyperSupers);
+    for (int s = s0; s < s1; ++s) {
+        float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
+        float o[3] = {a.x, a.y, a.z}, hh[3] = {b.x, b.y, b.z};
+        for (int j = 0; j < 3; ++j) {
+            lo[j] = fminf(lo[j], __fsub_rd(o[j], hh[j]));
+            hi[j] = fmaxf(hi[j], __fadd_ru(o[j], hh[j]));
+        }
+    }
+    float o[3] = {0.f, 0.f, 0.f}, hh[3] = {0.f, 0.f, 0.f};
+    float r2 = 0.0f;
+    for (int j = 0; j < p.d; ++j) {
+        o[j] = 0.5f * lo[j] + 0.5f * hi[j];
+        hh[j] = fmaxf(__fsub_ru(hi[j], o[j]), __fsub_ru(o[j], lo[j]));
+        r2 = __fadd_ru(r2, __fmul_ru(hh[j], hh[j]));
+    }
+    p.hypers[2 * h] = make_float4(o[0], o[1], o[2], __fsqrt_ru(r2));
+    p.hypers[2 * h + 1] = make_float4(hh[0], hh[1], hh[2], 0.0f);
+}
+
+
 __global__ void scatter_kernel(const int *A_sorted, const unsigned short *A16_sorted, const unsigned *perm,
                                long long n, int *out, Ctl *ctl) {
     count_launch(ctl);
@@ -885,11 +912,13 @@ cudaError_t launch_gather(const Prob &p, const unsigned *perm, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
+    hyper_box_kernel<<<blocks_for(p.nhypers, 128), 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_super_boxes(const Prob &p, cudaStream_t s) {
     super_box_kernel<<<blocks_for(p.nsupers, 128), 128, 0, s>>>(p);
+    hyper_box_kernel<<<blocks_for(p.nhypers, 128), 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -918,6 +947,7 @@ int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out) {
                 dim3((unsigned)blocks_for(ps.n_pad, 256)), dim3(256)};
     out[q++] = {(void *)tile_box_kernel, dim3((unsigned)tile_box_grid(ps.ntiles)), dim3(kTileBoxWarps * 32)};
     out[q++] = {(void *)super_box_kernel, dim3((unsigned)blocks_for(ps.nsupers, 128)), dim3(128)};
+    out[q++] = {(void *)hyper_box_kernel, dim3((unsigned)blocks_for(ps.nhypers, 128)), dim3(128)};
     return q;
 }
 

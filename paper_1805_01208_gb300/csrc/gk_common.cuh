@@ -36,6 +36,8 @@ constexpr int kTile = 256;          // points per tile (one warp of the assign k
 constexpr int kSuperTiles = 16;     // tiles per supertile (one warp of the filter), default and
                                     // the smallest choice (it sizes the per-supertile arrays)
 constexpr int kMaxSuperTiles = 32;  // the largest choice (one lane per tile in the filter)
+constexpr int kHyperSupers = 16;    // supertiles per hypertile (the filter's first level)
+constexpr int kHyperList = 128;     // longest hypertile list a supertile builds its own from
 constexpr int kCap = 128;           // candidate centers stored per tile
 constexpr int kFastCands = 32;      // candidates brought in with the tile's bulk copy
 constexpr int kCoopCands = kFastCands;  // tiles with more candidates are taken by a whole CTA
@@ -118,6 +120,12 @@ struct Prob {
     int d, k, dtype, weighted, assign_f64;
     int ntiles, nsupers;
     int stiles;                 // tiles per supertile (kSuperTiles or kMaxSuperTiles)
+    int hyper;                  // 1: supertile lists from hypertile lists (a level above them)
+    int nhypers;                // hypertiles of kHyperSupers supertiles
+    float4 *hypers;             // per hypertile: 2 float4 box, as the supertiles
+    int *hlists;                // per hypertile: its candidate list, kWarpList entries
+    int *hlen;                  // per hypertile: list length (-1: longer than kWarpList)
+    float *hlam;                // per hypertile: lower bound of the E of every center left out
     int actas;                  // resident CTAs per SM of the assignment (0: the default)
     int qmul;                   // tile order of the assignment: t = pos * qmul mod ntiles
     unsigned long long tile_magic;  // floor((2^64 - 1) / ntiles), for that reduction

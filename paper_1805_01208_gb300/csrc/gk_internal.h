@@ -32,7 +32,7 @@ long long sample_rho_entries(long long n);
 cudaError_t launch_sample_rho(const Prob &p, const long long *order, long long m0,
                               const unsigned *perm, unsigned char *rho_in, unsigned char *rho,
                               cudaStream_t s);
-constexpr int kSampleSelectNodes = 6;
+constexpr int kSampleSelectNodes = 7;
 int sample_select_nodes(const Prob &ps, const SampleSel &sel, KNode *out);
 cudaError_t launch_sample_select(const Prob &ps, const SampleSel &sel, cudaStream_t s);
 

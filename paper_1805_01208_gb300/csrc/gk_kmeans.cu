@@ -321,17 +321,18 @@ constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in regis
 
 // lamS gets the smallest lower bound of the supergroups, groups and centers the level
 // drops (+inf when none): every center outside the list has E >= lamS on the supertile.
+// box: the 2 float4 of the box (a supertile's, or a hypertile's for the level above).
 template <int D>
-__device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4 *cd, const float4 *gd,
-                                              int *list, float4 *lcd, int *glist, int *sglist,
-                                              int *glist_out, float &gall, float &lamS) {
+__device__ __forceinline__ int supertile_list(const Prob &p, const float4 *box, const float4 *cd,
+                                              const float4 *gd, int *list, float4 *lcd, int *glist,
+                                              int *sglist, int *glist_out, float &gall, float &lamS) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ng = p.ngroups;
     const float infl = 4.0f * kU * p.R;
     float so[3], sh[3];
     {
-        const float4 a = p.supers[2 * s], b = p.supers[2 * s + 1];
+        const float4 a = box[0], b = box[1];
         so[0] = a.x;
         so[1] = a.y;
         so[2] = a.z;
@@ -533,6 +534,99 @@ __device__ __forceinline__ int supertile_list(const Prob &p, int s, const float4
     return L;
 }
 
+// A supertile's level-1 list from its hypertile's list (one warp; lanes over the list's
+// centers, ascending): the supertile box lies inside the hypertile box, so a center the
+// hypertile level left out has a lower bound on the supertile at least as large, above
+// the hypertile's tau and so above the supertile's; the center that attains the
+// supertile's tau passes the hypertile's test.  tau over the hypertile list is therefore
+// the supertile's tau, and the centers of the list that pass its test are the list a
+// level 1 over all centers builds.  lamS: the smallest lower bound of what is left out
+// (the hypertile's bound, and the list's centers that fail).  Returns the list length.
+template <int D>
+__device__ __forceinline__ int list_from_hyper(const Prob &p, const float4 *box, const float4 *cd,
+                                               const int *hl, int Lh, float lamH, int *list, float4 *lcd,
+                                               int *glist_out, float &lamS) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const float infl = 4.0f * kU * p.R;
+    float so[3], sh[3];
+    {
+        const float4 a = box[0], b = box[1];
+        so[0] = a.x;
+        so[1] = a.y;
+        so[2] = a.z;
+        sh[0] = __fadd_ru(b.x, infl);
+        sh[1] = __fadd_ru(b.y, infl);
+        sh[2] = __fadd_ru(b.z, infl);
+    }
+    float tc = INFINITY;
+    for (int i = lane; i < Lh; i += 32) {
+        const int c = hl[i];
+        float lb, ub;
+        box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+        tc = fminf(tc, ub);
+    }
+    for (int off = 16; off; off >>= 1) tc = fminf(tc, __shfl_xor_sync(0xffffffffu, tc, off));
+    const float tauS = __fmul_ru(tc, 1.0f + 64.0f * kU);
+    float lam = lamH;
+    int L = 0;
+    for (int base = 0; base < Lh; base += 32) {
+        const int i = base + lane;
+        bool keep = false;
+        int c = 0;
+        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
+        if (i < Lh) {
+            c = hl[i];
+            ch = __ldg(&cd[2 * c]);
+            cl = __ldg(&cd[2 * c + 1]);
+            float lb, ub;
+            box_bounds<D>(ch, cl, so, sh, lb, ub);
+            keep = !(lb > tauS);
+            if (!keep) lam = fminf(lam, lb);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int pos = L + __popc(bal & lt);
+        if (keep) {
+            glist_out[pos] = c;  // L <= Lh <= kHyperList <= kWarpList
+            if (pos < kLaneMax) {
+                list[pos] = c;
+                lcd[2 * pos] = ch;
+                lcd[2 * pos + 1] = cl;
+            }
+        }
+        L += __popc(bal);
+    }
+    __syncwarp();
+    for (int off = 16; off; off >>= 1) lam = fminf(lam, __shfl_xor_sync(0xffffffffu, lam, off));
+    lamS = lam;
+    return L;
+}
+static_assert(kHyperList <= kWarpList, "a list built from a hypertile list fits the supertile's");
+
+// Level 1 for every hypertile (one warp each, the same as for a supertile): its list of
+// candidate centers, for the supertiles inside it.
+template <int D>
+__global__ void __launch_bounds__(kFilterThreads) hyper_kernel(Prob p) {
+    count_launch(p.ctl);
+    __shared__ int s_list[kFilterWarps][kLaneMax];
+    __shared__ float4 s_lcd[kFilterWarps][2 * kLaneMax];
+    __shared__ int s_grp[kFilterWarps][kWarpGroups];
+    __shared__ int s_sg[kFilterWarps][kWarpSG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int h = blockIdx.x * kFilterWarps + warp;
+    if (h >= p.nhypers) return;
+    const int sel = p.ctl->isel;
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
+    float gall, lam;
+    const int L = supertile_list<D>(p, p.hypers + 2 * h, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
+                                    s_sg[warp], p.hlists + (size_t)h * kWarpList, gall, lam);
+    if (lane == 0) {
+        p.hlen[h] = L <= kWarpList ? L : -1;
+        p.hlam[h] = lam;
+    }
+}
+
 // Header of tile t's record (count, -1: scan all centers; the largest g the tile can
 // meet) and, for a tile with more than kCoopCands candidates, its entry in the
 // cooperative list (one thread per tile).
@@ -583,10 +677,19 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         tb0 = p.tiles[2 * t];
         tb1 = p.tiles[2 * t + 1];
     }
-    float gall, lamS;
+    float gall = 0.0f, lamS = INFINITY;
     int *gl_out = p.blists + (size_t)s * kWarpList;
-    const int L = supertile_list<D>(p, s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp], s_sg[warp],
-                                    gl_out, gall, lamS);
+    int L = -1;
+    if (p.hyper) {  // from the hypertile's list, when it is short enough
+        const int h = s / kHyperSupers;
+        const int Lh = p.hlen[h];
+        if (Lh >= 0 && Lh <= kHyperList)
+            L = list_from_hyper<D>(p, p.supers + 2 * s, cd, p.hlists + (size_t)h * kWarpList, Lh,
+                                   p.hlam[h], s_list[warp], s_lcd[warp], gl_out, lamS);
+    }
+    if (L < 0)
+        L = supertile_list<D>(p, p.supers + 2 * s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
+                              s_sg[warp], gl_out, gall, lamS);
     if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
             const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
@@ -2312,6 +2415,10 @@ static int kgrid(const Prob &p) { return (p.k + kKThreads - 1) / kKThreads; }
 static void *filter_fn(int d) {
     return d == 2 ? (void *)filter_kernel<2> : (void *)filter_kernel<3>;
 }
+static void *hyper_fn(int d) {
+    return d == 2 ? (void *)hyper_kernel<2> : (void *)hyper_kernel<3>;
+}
+static dim3 hyper_grid(const Prob &p) { return dim3((unsigned)((p.nhypers + kFilterWarps - 1) / kFilterWarps)); }
 static void *filter_big_fn(int d) {
     return d == 2 ? (void *)filter_big_kernel<2> : (void *)filter_big_kernel<3>;
 }
@@ -2371,6 +2478,10 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     size_t smem;
     cudaError_t e = filter_config(p, grid, smem);
     if (e != cudaSuccess) return e;
+    if (p.hyper) {
+        e = cudaLaunchKernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), args1, 0, s);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
@@ -2541,6 +2652,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
         cudaGraph_t body_bal = mv.loop(h_bal);
         if (body_bal) {
             NodeAdder bl{body_bal};
+            if (p.hyper) bl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
             bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
@@ -2559,6 +2671,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
     cudaGraph_t body_fin = top.loop(h_fin);
     if (body_fin) {
         NodeAdder fl{body_fin};
+        if (p.hyper) fl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
@@ -2602,6 +2715,7 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
     cudaGraph_t body_bal = top.loop(h_bal);
     if (body_bal) {
         NodeAdder bl{body_bal};
+        if (ps.hyper) bl.kernel(hyper_fn(ps.d), hyper_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(filter_fn(ps.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         bl.kernel(filter_big_fn(ps.d), filter_big_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(assign_fn(ps), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p,

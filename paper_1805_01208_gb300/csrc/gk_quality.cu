@@ -255,22 +255,27 @@ __global__ void diam_seed_kernel(int k, const int *start, int *dist, int *front,
 }
 
 // One thread per frontier vertex of distance `level`.
+// One breadth-first level over the frontier list (its length read on the device, so that
+// the host can enqueue several levels without waiting; an empty frontier does nothing).
+// Grid-stride over the frontier; levels counts the non-empty levels.
 __global__ void diam_expand_kernel(const int *front, const unsigned *cnt_in, int level,
                                    const long long *row_ptr, const int *col, const int *block,
                                    int *dist, int *next, unsigned *cnt_out, int *ecc,
-                                   int *reached) {
-    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *cnt_in) return;
-    const int v = front[i];
-    const int b = block[v];
-    const long long e1 = row_ptr[v + 1];
-    for (long long e = row_ptr[v]; e < e1; ++e) {
-        const int u = col[e];
-        if (u == v || block[u] != b) continue;
-        if (atomicCAS(&dist[u], -1, level + 1) == -1) {
-            next[atomicAdd(cnt_out, 1u)] = u;
-            atomicAdd(&reached[b], 1);
-            atomicMax(&ecc[b], level + 1);
+                                   int *reached, unsigned long long *levels) {
+    const unsigned m = *cnt_in;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && m > 0) atomicAdd(levels, 1ull);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = front[i];
+        const int b = block[v];
+        const long long e1 = row_ptr[v + 1];
+        for (long long e = row_ptr[v]; e < e1; ++e) {
+            const int u = col[e];
+            if (u == v || block[u] != b) continue;
+            if (atomicCAS(&dist[u], -1, level + 1) == -1) {
+                next[atomicAdd(cnt_out, 1u)] = u;
+                atomicAdd(&reached[b], 1);
+                atomicMax(&ecc[b], level + 1);
+            }
         }
     }
 }
@@ -362,10 +367,12 @@ cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, 
     int *bound = reached + k, *conn = bound + k;
     unsigned *cnt = (unsigned *)(conn + k);
     int *bad = (int *)(cnt + 2);
+    unsigned long long *levels = (unsigned long long *)(((uintptr_t)(bad + 1) + 7) & ~(uintptr_t)7);
     *hbad = 0;
     *hlevels = 0;
     cudaError_t e = cudaMemsetAsync(size, 0, (size_t)k * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(levels, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     diam_fill_kernel<<<blocks_of(k), 256, 0, s>>>(start, k, INT_MAX);
     diam_init_kernel<<<blocks_of(n), 256, 0, s>>>(row_ptr, col, n, nnz, block, k, size, start, bad);
@@ -379,20 +386,26 @@ cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, 
         if ((e = cudaMemsetAsync(cnt, 0, 4, s)) != cudaSuccess) return e;
         diam_seed_kernel<<<blocks_of(k), 256, 0, s>>>(k, start, dist, front[0], cnt, ecc, reached);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        int cur = 0;
-        for (int level = 0;; ++level) {  // at most n levels: every vertex joins one list
+        // kLevelsPerWait levels are enqueued between two reads of the frontier length;
+        // the search ends with an empty frontier (at most n levels: every vertex joins one
+        // list once)
+        constexpr int kLevelsPerWait = 16;
+        const int grid = (int)(blocks_of(n) < 1216 ? blocks_of(n) : 1216);
+        int cur = 0, level = 0;
+        for (;;) {
+            for (int g = 0; g < kLevelsPerWait; ++g, ++level) {
+                if ((e = cudaMemsetAsync(cnt + (cur ^ 1), 0, 4, s)) != cudaSuccess) return e;
+                diam_expand_kernel<<<grid, 256, 0, s>>>(front[cur], cnt + cur, level, row_ptr, col, block,
+                                                        dist, front[cur ^ 1], cnt + (cur ^ 1), ecc,
+                                                        reached, levels);
+                if ((e = cudaGetLastError()) != cudaSuccess) return e;
+                cur ^= 1;
+            }
             unsigned h = 0;
             if ((e = cudaMemcpyAsync(&h, cnt + cur, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
                 return e;
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
             if (h == 0) break;
-            if ((e = cudaMemsetAsync(cnt + (cur ^ 1), 0, 4, s)) != cudaSuccess) return e;
-            diam_expand_kernel<<<blocks_of(h), 256, 0, s>>>(front[cur], cnt + cur, level, row_ptr,
-                                                            col, block, dist, front[cur ^ 1],
-                                                            cnt + (cur ^ 1), ecc, reached);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-            cur ^= 1;
-            ++*hlevels;
         }
         diam_record_kernel<<<blocks_of(k), 256, 0, s>>>(k, sweep, size, reached, ecc, bound, conn);
         if (sweep + 1 < sweeps) {
@@ -402,7 +415,12 @@ cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     diam_final_kernel<<<1, 256, 0, s>>>(k, size, bound, conn, diam, out_i, out_d);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long lv = 0;
+    if ((e = cudaMemcpyAsync(&lv, levels, sizeof(lv), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *hlevels = (long long)lv;
+    return cudaSuccess;
 }
 
 }  // namespace gk

@@ -46,16 +46,17 @@ def test_host_only_helpers(libgk):
     assert (o.max_iter, o.max_balance_iter, o.final_balance_iter, o.erosion) == (50, 50, 500, 1)
     assert o.delta_threshold < 0 and o.assign_dtype == gk.GK_F64 and o.use_graph == 1
     assert o.bounds == 0 and o.supertile_tiles == 0 and o.assign_ctas_per_sm == 0
+    assert o.hypertiles == 0
     assert gk.status_string(gk.GK_ERR_NOT_BALANCED) == "GK_ERR_NOT_BALANCED"
     assert gk.status_string(99) == "GK_UNKNOWN_STATUS"
 
 
 def test_struct_layouts_match_header():
     import paper_1805_01208_gb300 as gk
-    # gk_options: 4 int32, double, 4 int32, 2 int32 shapes, 2 int32 reserved
-    assert ctypes.sizeof(gk.Options) == 4 * 4 + 8 + 4 * 4 + 2 * 4 + 2 * 4
+    # gk_options: 4 int32, double, 4 int32, 3 int32 shapes, 1 int32 reserved
+    assert ctypes.sizeof(gk.Options) == 4 * 4 + 8 + 4 * 4 + 3 * 4 + 1 * 4
     assert ctypes.sizeof(gk.Result) == (6 * 4 + 4 * 8 + 2 * 8 + 3 * 8 + 4 * 8 + 4 * 8 + 8 + 8 + 8
-                                        + 2 * 4 + 8)
+                                        + 4 * 4 + 8)
     # gk_instance: 2 pointers, int64, 4 int32, double, 3 pointers
     assert ctypes.sizeof(gk.Instance) == 2 * 8 + 8 + 4 * 4 + 8 + 3 * 8
 

@@ -555,12 +555,14 @@ def test_every_launch_shape_gives_the_same_partition(gk, shape, d, dtype, n, k, 
     x = _points(shape, n, d, 71, dtype)
     outs = []
     for stl in (16, 32):
-        for ctas in (1, 2, 5):
-            o = gk.default_options(assign_dtype=assign, supertile_tiles=stl, assign_ctas_per_sm=ctas)
-            block, C, I, res = gk.partition(_dev(x), k, 0.03, options=o)
-            assert res["supertile_tiles"] == stl and res["tune_ms"] == 0.0
-            assert 1 <= res["assign_ctas_per_sm"] <= ctas
-            outs.append((_np(block), _np(C), _np(I), res["balance_passes"]))
+        for hy in (1, 2):
+            for ctas in (1, 5):
+                o = gk.default_options(assign_dtype=assign, supertile_tiles=stl, hypertiles=hy,
+                                       assign_ctas_per_sm=ctas)
+                block, C, I, res = gk.partition(_dev(x), k, 0.03, options=o)
+                assert res["supertile_tiles"] == stl and res["hypertiles"] == hy
+                assert res["tune_ms"] == 0.0 and 1 <= res["assign_ctas_per_sm"] <= ctas
+                outs.append((_np(block), _np(C), _np(I), res["balance_passes"]))
     o = gk.default_options(assign_dtype=assign)  # tuned
     block, C, I, res = gk.partition(_dev(x), k, 0.03, options=o)
     assert res["supertile_tiles"] in (16, 32) and res["assign_ctas_per_sm"] >= 1
@@ -579,7 +581,8 @@ def test_every_launch_shape_gives_the_same_partition(gk, shape, d, dtype, n, k, 
 
 def test_launch_shape_options_are_checked(gk):
     x = _dev(np.random.default_rng(0).random((1000, 2)))
-    for bad in (dict(supertile_tiles=8), dict(supertile_tiles=64), dict(assign_ctas_per_sm=-1)):
+    for bad in (dict(supertile_tiles=8), dict(supertile_tiles=64), dict(assign_ctas_per_sm=-1),
+                dict(hypertiles=3)):
         with pytest.raises(gk.GKError) as e:
             gk.partition(x, 4, 0.03, options=gk.default_options(**bad))
         assert e.value.status == gk.GK_ERR_INVALID_ARG
