@@ -62,6 +62,9 @@ def _args():
     ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--k", type=int, default=None,
+                    help="override the number of blocks (profiling a smaller n at the "
+                         "workload's points per block)")
     ap.add_argument("--assign", default=None, choices=["f32", "f64"],
                     help="override the workload's assignment precision")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
@@ -244,6 +247,8 @@ def run_reference(args):
     cores = len(os.sched_getaffinity(0))
     probe_n = int(min(n_full, 4_000_000))
     x, w, spec = synth.workload(args.workload, n=probe_n)
+    if args.k:
+        spec["k"] = args.k
     budget = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     m = min(probe_n, _sample_size(x, w, spec, budget, cores))
     for _ in range(args.warmup):
@@ -531,6 +536,8 @@ def main():
     x, w, spec = synth.workload(args.workload, n=args.n)
     if args.assign:
         spec["assign"] = args.assign
+    if args.k:
+        spec["k"] = args.k
     if world > 1 and rank > 0:  # replicas: an independent instance per rank
         x = replica_points(spec, rank)
     n, d, k, eps = len(x), spec["d"], spec["k"], spec["eps"]

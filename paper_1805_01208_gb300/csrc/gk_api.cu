@@ -406,7 +406,9 @@ gk_status check_common(const void *coords, int32_t dtype, int64_t n, int32_t d) 
 }
 
 // Launch-shape tuner cache: the shapes measured fastest per kind of problem.
-using TuneKey = std::tuple<int, int, int, int, int, int, int>;  // d, dtype, f64, w, bounds, log2 n, log2 k
+// d, dtype, f64, w, bounds, log2 n, log2 k, and the shapes the caller fixed (0: free):
+// supertile tiles, hypertiles, CTAs per SM
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int>;
 struct TuneChoice {
     int stiles, hyper, actas;
 };
@@ -596,7 +598,8 @@ struct Call {
             for (int c = mc; c >= 1 && c >= mc - 1; --c) cts.push_back(c);
         TuneChoice best{sts[0], hys[0], cts[0]};
         const size_t ncand = sts.size() * hys.size() * cts.size();
-        const TuneKey key{p.d, p.dtype, p.assign_f64, p.weighted, p.bounds, ilog2(p.n), ilog2(p.k)};
+        const TuneKey key{p.d, p.dtype, p.assign_f64, p.weighted, p.bounds, ilog2(p.n), ilog2(p.k),
+                          o.supertile_tiles, o.hypertiles, o.assign_ctas_per_sm};
         bool cached = false;
         if (ncand > 1) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -701,7 +704,7 @@ void fill_result(gk_result *r, const Ctl &c, gk_status st, double t_boot, double
     r->max_delta = c.max_delta;
     r->delta_threshold = c.thr;
     unsigned long long cand = 0;
-    for (int i = 0; i < kStripes; ++i) cand += c.cand_stripes[i];
+    for (int i = 0; i < kStripes; ++i) cand += c.cand_stripes[i * kStripeStride];
     r->avg_candidates = c.passes > 0 ? (double)cand / ((double)c.passes * (double)n) : 0.0;
     r->rechecked_points = (int64_t)c.rechecks;
     r->kernel_launches = (int64_t)c.launches;

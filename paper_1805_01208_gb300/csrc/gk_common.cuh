@@ -56,6 +56,7 @@ constexpr int kQueueStride = 32;    // one 128-byte line per queue counter
 static_assert(kGroup == kKThreads, "a group record is written by one CTA of the k-sized kernels");
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
 constexpr int kStripes = 64;        // striped counters for per-pass statistics
+constexpr int kStripeStride = 16;   // 64-bit words per stripe: each in its own 128-byte line
 constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers
 constexpr int kSkipHist = 64;       // passes of a phase with per-point bounds (then a fresh pass)
 
@@ -94,6 +95,8 @@ struct Ctl {
     unsigned int done_count;                // last-block-done counter (reset by the last block)
     unsigned int coop_cnt;                  // tiles in the cooperative list (reset before each filter)
     unsigned int big_cnt;                   // supertiles with long candidate lists (same)
+    unsigned int mixed_cnt;                 // tiles the movement takes point by point (reset
+                                            //   by the movement's finalize kernel)
     int nonempty;                           // non-empty blocks of the last movement
     double max_imbalance;
     double max_delta;
@@ -108,7 +111,8 @@ struct Ctl {
     unsigned long long t_assign0;           // globaltimer at the start of the last assign launch
     unsigned long long assign_ns;           // sum of assign launch durations (globaltimer)
     unsigned long long assign_cnt;          // assign launches measured
-    unsigned long long cand_stripes[kStripes];  // sum over tiles and passes of candidates x points
+    // sum over tiles and passes of candidates x points (stripe i at i * kStripeStride)
+    unsigned long long cand_stripes[kStripes * kStripeStride];
     alignas(128) unsigned int tile_q[kQueues * kQueueStride];  // assignment queues (reset by the filter)
 };
 

@@ -322,10 +322,20 @@ constexpr int kCenterRegs = 8;  // kept groups whose center bounds stay in regis
 // lamS gets the smallest lower bound of the supergroups, groups and centers the level
 // drops (+inf when none): every center outside the list has E >= lamS on the supertile.
 // box: the 2 float4 of the box (a supertile's, or a hypertile's for the level above).
+// split > 0: when the level keeps more than split groups (or more than kWarpSG
+// supergroups), it stops before the center sweeps and returns kSplit: the box is too large
+// for one warp's list to be cheap (a curve jump across sparse space), and the caller
+// builds each tile's list from its own box instead.  gcap: entries of glist_out.  Only the
+// boxes whose level 1 would sweep every center are split: at 1e9 points a few dozen
+// supertiles, each of which had taken 300-600 us alone; splitting the 3.5 % of supertiles
+// with more than 16 kept groups instead cost more work than it saved.
+constexpr int kSplitGroups = kWarpGroups;
+constexpr int kSplit = -2;
 template <int D>
 __device__ __forceinline__ int supertile_list(const Prob &p, const float4 *box, const float4 *cd,
                                               const float4 *gd, int *list, float4 *lcd, int *glist,
-                                              int *sglist, int *glist_out, float &gall, float &lamS) {
+                                              int *sglist, int *glist_out, float &gall, float &lamS,
+                                              int split = 0, int gcap = kWarpList) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int ng = p.ngroups;
@@ -446,6 +456,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, const float4 *box, 
             by_sg = true;
             nchunk = nks;
         } else {
+            if (split > 0) return kSplit;
             lamg = INFINITY;  // every group is tested below
         }
     }
@@ -472,6 +483,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, const float4 *box, 
         ngk += __popc(bal);
     }
     __syncwarp();
+    if (split > 0 && ngk > split) return kSplit;
     const bool gover = ngk > kWarpGroups;  // too many groups: sweep every center
     if (!gover) lam = lamg;                // (a sweep of every center tests them one by one)
     // tau of the supertile over the centers of the kept groups (lane = center of the group)
@@ -513,7 +525,7 @@ __device__ __forceinline__ int supertile_list(const Prob &p, const float4 *box, 
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = L + __popc(bal & lt);
-        if (keep && pos < kWarpList) glist_out[pos] = c;
+        if (keep && pos < gcap) glist_out[pos] = c;
         if (keep && pos < kLaneMax) list[pos] = c;
         L += __popc(bal);
     }
@@ -620,9 +632,9 @@ __global__ void __launch_bounds__(kFilterThreads) hyper_kernel(Prob p) {
     const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
     float gall, lam;
     const int L = supertile_list<D>(p, p.hypers + 2 * h, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
-                                    s_sg[warp], p.hlists + (size_t)h * kWarpList, gall, lam);
-    if (lane == 0) {
-        p.hlen[h] = L <= kWarpList ? L : -1;
+                                    s_sg[warp], p.hlists + (size_t)h * kWarpList, gall, lam, kSplitGroups);
+    if (lane == 0) {  // a split or overlong list: the supertiles build their own
+        p.hlen[h] = L >= 0 && L <= kWarpList ? L : -1;
         p.hlam[h] = lam;
     }
 }
@@ -634,9 +646,11 @@ __global__ void __launch_bounds__(kFilterThreads) hyper_kernel(Prob p) {
 // record keeps lowered by 16 u (the rounding of the bound's own arithmetic), as a lower
 // bound of every left-out center's E on the tile (+inf when all centers are evaluated).
 // uid: the tile's stored-id marker (the w of its second box word), handed to the
-// assignment in the header's w.
-__device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float gkept, float gall,
-                                            const float4 &tb0, float lam, float uid) {
+// assignment in the header's w.  Returns the tile's candidates x points (the caller adds
+// it to the statistics).
+__device__ __forceinline__ unsigned long long finish_tile(const Prob &p, int t, int cnt, float gkept,
+                                                          float gall, const float4 &tb0, float lam,
+                                                          float uid) {
     const bool over = cnt > kCap;
     float4 *rec = p.trec + (size_t)t * kRecF4;
     const float lamr = over ? INFINITY : __fmul_rd(lam, 1.0f - 16.0f * kU);
@@ -648,7 +662,10 @@ __device__ __forceinline__ void finish_tile(const Prob &p, int t, int cnt, float
     long long nv = p.n - (long long)t * kTile;
     nv = nv > kTile ? kTile : nv;
     const unsigned long long used = over ? (unsigned long long)p.k : (unsigned long long)cnt;
-    atomicAdd(&p.ctl->cand_stripes[t % kStripes], used * (unsigned long long)nv);
+    return used * (unsigned long long)nv;
+}
+__device__ __forceinline__ void add_candidates(const Prob &p, int stripe, unsigned long long v) {
+    if (v) atomicAdd(&p.ctl->cand_stripes[(stripe % kStripes) * kStripeStride], v);
 }
 
 // One warp per supertile, with no block-wide synchronisation: level 1; then, for a
@@ -689,8 +706,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     }
     if (L < 0)
         L = supertile_list<D>(p, p.supers + 2 * s, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
-                              s_sg[warp], gl_out, gall, lamS);
-    if (L > kLaneMax) {  // hand the supertile to the warp-per-tile kernel
+                              s_sg[warp], gl_out, gall, lamS, kSplitGroups);
+    if (L > kLaneMax || L == kSplit) {  // hand the supertile to the warp-per-tile kernel
         if (lane == 0) {
             const int slot = (int)atomicAdd(&p.ctl->big_cnt, 1u);
             p.bigs[4 * slot] = s;
@@ -701,6 +718,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         return;
     }
     // level 2, short list: lane = tile
+    unsigned long long cs = 0;  // candidates x points of the lane's tile
     const int *list = s_list[warp];
     const float4 *lcd = s_lcd[warp];
     if (has_tile) {
@@ -733,31 +751,70 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
                 ++cnt;
             }
         }
-        finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
+        cs = finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
     }
+    // the statistics: one atomic per supertile (one per tile contended at 1e9 points)
+    for (int off = 16; off; off >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, off);
+    if (lane == 0) add_candidates(p, s, cs);
 }
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
 static_assert(kMaxSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
 
 // Level 2 of the supertiles with long lists: one warp per tile, lanes over chunks
-// of 32 candidates (tau pass, then the ascending keep pass with ballots).
+// of 32 candidates (tau pass, then the ascending keep pass with ballots).  A split
+// supertile (kSplit: level 1 on its box would keep too many groups) gets level 1 on each
+// tile's own box instead, whose list is the tile's candidates: the tile's tau is the
+// smallest upper bound over all centers either way, and the kept centers are those whose
+// lower bound on the tile passes it.
 template <int D>
 __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
     count_launch(p.ctl);
-    const int lane = threadIdx.x & 31;
+    __shared__ int s_list[kFilterWarps][kLaneMax];
+    __shared__ float4 s_lcd[kFilterWarps][2 * kLaneMax];
+    __shared__ int s_grp[kFilterWarps][kWarpGroups];
+    __shared__ int s_sg[kFilterWarps][kWarpSG];
+    __shared__ int s_tl[kFilterWarps][kCap];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int total = (int)p.ctl->big_cnt * p.stiles;
     const int sel = p.ctl->isel;
     const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
     const float infl = 4.0f * kU * p.R;
     const int TW = gridDim.x * kFilterWarps;
-    for (int item = blockIdx.x * kFilterWarps + (threadIdx.x >> 5); item < total; item += TW) {
+    for (int item = blockIdx.x * kFilterWarps + warp; item < total; item += TW) {
         const int slot = item / p.stiles;
         const int s = p.bigs[4 * slot], Lr = p.bigs[4 * slot + 1];
-        const float gall = __int_as_float(p.bigs[4 * slot + 2]);
-        float lamT = __int_as_float(p.bigs[4 * slot + 3]);
         const int t = s * p.stiles + item % p.stiles;
         if (t >= p.ntiles) continue;
+        if (Lr == kSplit) {
+            float gall, lamT;
+            int L = supertile_list<D>(p, p.tiles + 2 * t, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
+                                      s_sg[warp], s_tl[warp], gall, lamT, 0, kCap);
+            const float4 tb0 = p.tiles[2 * t], tb1 = p.tiles[2 * t + 1];
+            float gkept = 0.0f;
+            if (L <= kCap) {
+                float4 *rec = p.trec + (size_t)t * kRecF4;
+                const bool inl = L <= kLaneMax;  // the level copied the list's center data
+                for (int i = lane; i < L; i += 32) {
+                    const int c = s_tl[warp][i];
+                    const float4 ch = inl ? s_lcd[warp][2 * i] : __ldg(&cd[2 * c]);
+                    const float4 cl = inl ? s_lcd[warp][2 * i + 1] : __ldg(&cd[2 * c + 1]);
+                    const float q0 = (ch.x - tb0.x) + cl.x;
+                    const float q1 = (ch.y - tb0.y) + cl.y;
+                    const float q2 = D == 3 ? (ch.z - tb0.z) + cl.z : 0.0f;
+                    rec[2 + 2 * i] = make_float4(q0, q1, q2, ch.w);
+                    rec[3 + 2 * i] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                    gkept = fmaxf(gkept, ch.w);
+                }
+                for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
+            }
+            __syncwarp();
+            if (lane == 0) add_candidates(p, t, finish_tile(p, t, L, gkept, gall, tb0, lamT, tb1.w));
+            continue;
+        }
+        const float gall = __int_as_float(p.bigs[4 * slot + 2]);
+        float lamT = __int_as_float(p.bigs[4 * slot + 3]);
         const bool all = Lr > kWarpList;
         const int L = all ? p.k : Lr;
         const int *list = p.blists + (size_t)s * kWarpList;
@@ -813,7 +870,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
             lamT = fminf(lamT, __shfl_xor_sync(0xffffffffu, lamT, off));
         }
-        if (lane == 0) finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
+        if (lane == 0) add_candidates(p, t, finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w));
     }
 }
 
@@ -1316,29 +1373,28 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         }
     };
     // Tiles come from kQueues interleaved queues: queue q serves positions q, q + kQueues,
-    // ... (one atomic per tile, requested two tiles ahead so that its latency is
-    // hidden).  A tile with more than kFastCands candidates was taken by a cooperative
-    // CTA above: lane 0 reads the count of the tile's record when it resolves the
-    // position and marks the tile (kPass), so that no copy is issued for it and the
-    // warp passes over it without waiting.  A warp's positions increase, so once a
-    // stage holds no tile the other one holds none either.  The queue state lives in
-    // lane 0 and is broadcast when a stage is consumed.
-    // A tile with a single candidate needs neither its coordinates nor its record: the
-    // filter has proven that every point of the tile goes to that center (without
-    // per-point bounds to keep up), so lane 0 reads the center and the tile's stored-id
-    // marker when it resolves the position and marks the tile (kSingle): no copy, no wait.
-    constexpr int kPass = 1 << 30;
-    constexpr int kSingle = 1 << 29;
-    constexpr int kTileMask = kSingle - 1;
+    // ... A warp claims qch positions at a time (one atomic per chunk) and resolves them
+    // in parallel: lane j of a half of the ring below reads the record header (candidate
+    // count, stored-id marker) and first candidate of one position's tile.  The ring has
+    // two halves of qch entries; a half is claimed and resolved again as soon as its last
+    // entry is taken, so its loads have the other half's tiles of work to arrive.  A
+    // warp's positions increase, so the first position past the end means that the warp
+    // is done.
+    // A tile with more than kFastCands candidates was taken by a cooperative CTA above
+    // and is passed over.  A tile with a single candidate needs neither its coordinates
+    // nor its record: the filter has proven that every point of the tile goes to that
+    // center (without per-point bounds to keep up), so it is finished from the ring's
+    // registers.  The other tiles go through the warp's two shared-memory stages in
+    // order of arrival: a tile's copy is issued when it is taken from the ring, and it is
+    // evaluated when a later tile needs its stage (or at the end), so the one-candidate
+    // tiles in between cover the copy's latency.
     const int qi = (blockIdx.x * kAWarps + w) & (kQueues - 1);
     unsigned *qctr = &p.ctl->tile_q[qi * kQueueStride];
-    // position -> tile (ntiles when the queue is empty) and its record count, whose load
-    // is only used one refill later
     // Positions map to tiles through the permutation t = pos * qmul mod ntiles (qmul
     // coprime to ntiles, near 0.618 ntiles): the warps working at the same time then
     // hold tiles from all over the curve, whose blocks differ, instead of neighbouring
     // tiles that all add to the weights of the same few blocks.
-    auto resolve = [&](unsigned m, int &tile, int &cnt, int &c1, int &pv) {  // lane 0
+    auto resolve = [&](unsigned m, int &tile, int &cnt, int &c1, int &pv) {
         const long long pos = (long long)qi + (long long)kQueues * m;
         if (pos >= p.ntiles) {
             tile = p.ntiles;
@@ -1351,70 +1407,39 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         pv = __float_as_int(h.w);
         c1 = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4 + 3].x));
     };
-    auto mark = [&](int tile, int cnt) -> int {  // kPass: cooperative; kSingle: one candidate
-        if (tile >= p.ntiles) return tile;
-        if (cnt < 0 || cnt > kFastCands) return tile | kPass;
-        return (!BOUNDS && cnt == 1) ? (tile | kSingle) : tile;
+    // A chunk is at most 8 positions and at most 1/16 of a warp's share of the tiles, so
+    // that a warp with few tiles (n of a few million) does not hold work the others could
+    // take.
+    const int qch = (int)min(8LL, max(1LL, (long long)p.ntiles / ((long long)gridDim.x * kAWarps * 16)));
+    int r_tile = p.ntiles, r_cnt = 0, r_c1 = 0, r_pv = -1;  // this lane's ring entry
+    // chunk bases are claimed one chunk ahead of their use (lane 0), so that the atomic's
+    // latency is not waited for
+    unsigned nb = lane == 0 ? atomicAdd(qctr, (unsigned)qch) : 0u;
+    auto resolve_half = [&](int h) {
+        const unsigned base = __shfl_sync(0xffffffffu, nb, 0);
+        if (lane == 0) nb = atomicAdd(qctr, (unsigned)qch);
+        const int j = lane - h * qch;
+        if (j >= 0 && j < qch) resolve(base + (unsigned)j, r_tile, r_cnt, r_c1, r_pv);
     };
-    int tq0 = p.ntiles, tq1 = p.ntiles, t_next = p.ntiles, c_next = 0;
-    int c1_0 = 0, c1_1 = 0, pv_0 = -1, pv_1 = -1, c1_next = 0, pv_next = -1;  // single tiles
-    unsigned m_req = 0;
-    if (lane == 0) {
-        const unsigned m0 = atomicAdd(qctr, 1u), m1 = atomicAdd(qctr, 1u), m2 = atomicAdd(qctr, 1u);
-        m_req = atomicAdd(qctr, 1u);
-        int c0, c1;
-        resolve(m0, tq0, c0, c1_0, pv_0);
-        resolve(m1, tq1, c1, c1_1, pv_1);
-        resolve(m2, t_next, c_next, c1_next, pv_next);
-        tq0 = mark(tq0, c0);
-        tq1 = mark(tq1, c1);
-        if (tq0 < p.ntiles) issue(tq0, c0, 0);
-        if (tq1 < p.ntiles) issue(tq1, c1, 1);
-    }
-    // stage b is free again: load the next tile into it (lane 0)
-    auto refill = [&](int b) {
-        if (lane == 0) {
-            const int tn = mark(t_next, c_next);
-            if (b) {
-                tq1 = tn;
-                c1_1 = c1_next;
-                pv_1 = pv_next;
-            } else {
-                tq0 = tn;
-                c1_0 = c1_next;
-                pv_0 = pv_next;
-            }
-            if (tn < p.ntiles) issue(tn, c_next, b);
-            resolve(m_req, t_next, c_next, c1_next, pv_next);
-            m_req = atomicAdd(qctr, 1u);
-        }
+    resolve_half(0);
+    resolve_half(1);
+    int cc = 0;  // ring entry taken next
+    int s_t0 = -1, s_t1 = -1;  // tile in each stage (-1: free)
+    auto stile = [&](int b) -> int { return b ? s_t1 : s_t0; };
+    auto set_stile = [&](int b, int v) {
+        if (b) s_t1 = v;
+        else s_t0 = v;
     };
+    int s_old = 0;             // of two busy stages, the one issued first
+    int pend = -1, pend_cnt = 0;  // the tile to copy into the stage being evaluated
     unsigned ph0 = 0, ph1 = 0;
-    for (int it = 0;; ++it) {
-        const int b = it & 1;
-        const int tqb = __shfl_sync(0xffffffffu, b ? tq1 : tq0, 0);
-        if ((tqb & kTileMask) >= p.ntiles) break;  // the other stage holds no tile either
-        if (tqb & kPass) {  // a cooperative tile: nothing was copied into this stage
-            refill(b);
-            continue;
-        }
-        if (!BOUNDS && (tqb & kSingle)) {  // every point of the tile goes to center c1
-            const int t = tqb & kTileMask;
-            const int c1 = __shfl_sync(0xffffffffu, b ? c1_1 : c1_0, 0);
-            const int pv = __shfl_sync(0xffffffffu, b ? pv_1 : pv_0, 0);
-            refill(b);
-            const long long t0 = (long long)t * kTile, i0 = t0 + lane * 8;
-            const long long nv = p.n - i0;
-            const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-            nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
-            int best[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) best[q] = c1;
-            store_blocks_tile(p, t, i0, nval, best, pv);
-            if (lane == 0) tile_weight_to(p, t, c1);
-            continue;
-        }
-        const int t = tqb;
+    // once stage b has been read: its next tile's copy (lane 0)
+    auto refill = [&](int b) {
+        if (pend >= 0) issue(pend, pend_cnt, b);
+    };
+    // Evaluates the tile of stage b (waits for its copy); false when the copy timed out.
+    auto process = [&](int b) -> bool {
+        const int t = stile(b);
         const unsigned phb = b ? ph1 : ph0;
         bool ok = mbar_wait_bounded(&bar[w][b], phb);
         if (!__all_sync(0xffffffffu, ok)) {
@@ -1422,9 +1447,8 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             // bounded wait for the copies still in flight (this stage and the other).
             if (lane == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
             mbar_wait_bounded(&bar[w][b], phb);
-            if (__shfl_sync(0xffffffffu, b ? tq0 : tq1, 0) < p.ntiles)
-                mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
-            return;
+            if (stile(b ^ 1) >= 0) mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
+            return false;
         }
         if (b) ph1 ^= 1u; else ph0 ^= 1u;
         AStage<D, BOUNDS> &S = st[w][b];
@@ -1801,6 +1825,58 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         } else {
             tile_histogram(p, i0, nval, best);
         }
+        return true;
+    };
+    for (;;) {
+        // the next ring entry (every lane holds the same warp-wide state)
+        const int tile = __shfl_sync(0xffffffffu, r_tile, cc);
+        const int cnt = __shfl_sync(0xffffffffu, r_cnt, cc);
+        const int c1 = __shfl_sync(0xffffffffu, r_c1, cc);
+        const int pv = __shfl_sync(0xffffffffu, r_pv, cc);
+        ++cc;
+        if (cc == qch) {
+            resolve_half(0);
+        } else if (cc == 2 * qch) {
+            resolve_half(1);
+            cc = 0;
+        }
+        if (tile >= p.ntiles) break;
+        if (cnt < 0 || cnt > kFastCands) continue;  // taken by a cooperative CTA
+        if (!BOUNDS && cnt == 1) {  // every point of the tile goes to center c1
+            const long long t0 = (long long)tile * kTile, i0 = t0 + lane * 8;
+            const long long nv = p.n - i0;
+            const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
+            nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
+            int best[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) best[q] = c1;
+            store_blocks_tile(p, tile, i0, nval, best, pv);
+            if (lane == 0) tile_weight_to(p, tile, c1);
+            continue;
+        }
+        if (s_t0 >= 0 && s_t1 >= 0) {
+            // both stages busy: evaluate the older one and copy this tile into it
+            const int b = s_old;
+            pend = tile;
+            pend_cnt = cnt;
+            if (!process(b)) return;
+            pend = -1;
+            set_stile(b, tile);
+            s_old = b ^ 1;
+            continue;
+        }
+        const int b = s_t0 < 0 ? 0 : 1;
+        if (stile(b ^ 1) < 0) s_old = b;  // the only busy stage is the older one
+        issue(tile, cnt, b);
+        set_stile(b, tile);
+    }
+    // the tiles still in the stages, in order of their copies
+    if (stile(s_old) >= 0) {
+        if (!process(s_old)) return;
+        set_stile(s_old, -1);
+    }
+    if (stile(s_old ^ 1) >= 0) {
+        if (!process(s_old ^ 1)) return;
     }
     if (F64MODE) {
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
@@ -2013,15 +2089,8 @@ __device__ __forceinline__ void load8(const T *src, long long i0, int nval, T v[
     }
 }
 
-// A tile all of whose points lie in one block (most tiles: a block of curve-sorted
-// points spans many tiles): lane sums of the 8 points' fixed-point values and ordered-key
-// extremes, one warp reduction, one set of atomics for the tile.  The values are the
-// ones the run-by-run path below forms (same conversions, integer sums, the same keys),
-// so the result does not depend on which path a tile takes.  Returns false (nothing
-// done) when the tile holds more than one block id or an id outside [0, k).
-template <typename T, int D>
-__device__ __forceinline__ bool centroid_uniform_tile(const Prob &p, const T *X, long long i0, int nval) {
-    int ids[8];
+// The lane's 8 block ids starting at i0 (one 16-byte load when all 8 are points).
+__device__ __forceinline__ void load_ids8(const Prob &p, long long i0, int nval, int ids[8]) {
     if (nval == 8 && p.a16) {
         const uint4 v = *reinterpret_cast<const uint4 *>(p.A16 + i0);
         const unsigned u[4] = {v.x, v.y, v.z, v.w};
@@ -2037,152 +2106,160 @@ __device__ __forceinline__ bool centroid_uniform_tile(const Prob &p, const T *X,
         ids[4] = b.x; ids[5] = b.y; ids[6] = b.z; ids[7] = b.w;
     } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) ids[q] = q < nval ? (p.a16 ? (int)p.A16[i0 + q] : p.A[i0 + q]) : 0;
+        for (int q = 0; q < 8; ++q) ids[q] = q < nval ? (p.a16 ? (int)p.A16[i0 + q] : p.A[i0 + q]) : -1;
     }
-    const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
-    bool same = true;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) same &= q >= nval || ids[q] == b0;
-    if (!__all_sync(0xffffffffu, same) || (unsigned)b0 >= (unsigned)p.k) return false;
-    T wv[8];
-    if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        T xv[8];
-        load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
-        long long sum = 0;
-        unsigned long long kmin = ~0ull, kmax = 0ull;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q < nval) {
-                long long v;
-                if (sizeof(T) == 8)
-                    v = p.weighted ? fix_f64((double)wv[q] * (double)xv[q], p.Fx) : fix_f64((double)xv[q], p.Fx);
-                else
-                    v = p.weighted ? fix_prod_f32((float)wv[q], (float)xv[q], p.Fx) : fix_f32((float)xv[q], p.Fx);
-                sum += v;
-                const unsigned long long kk = KeyOf<T>::key(xv[q]);
-                kmin = kk < kmin ? kk : kmin;
-                kmax = kk > kmax ? kk : kmax;
-            }
-        }
-        for (int off = 16; off; off >>= 1) {
-            sum += __shfl_xor_sync(0xffffffffu, sum, off);
-            const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
-            const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
-            kmin = a < kmin ? a : kmin;
-            kmax = b > kmax ? b : kmax;
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomic_add_i128(&p.SXfix[2 * (b0 * D + j)], sum);
-            atomicMin(&p.BBlo[b0 * D + j], kmin);
-            atomicMax(&p.BBhi[b0 * D + j], kmax);
-        }
-    }
-    return true;
 }
 
-// One tile point by point (called by the whole warp): lane l takes points 8l..8l+7;
-// runs of equal block ids inside the lane, then a segmented reduction over the lanes.
+// The fixed-point value of one point's (weighted) coordinate, as every movement path
+// forms it (the sums are exact integers, so the path a tile takes does not matter).
+template <typename T>
+__device__ __forceinline__ long long cent_fix(const Prob &p, T w, T x) {
+    if (sizeof(T) == 8)
+        return p.weighted ? fix_f64((double)w * (double)x, p.Fx) : fix_f64((double)x, p.Fx);
+    return p.weighted ? fix_prod_f32((float)w, (float)x, p.Fx) : fix_f32((float)x, p.Fx);
+}
+
+// One tile (called by the whole warp): lane l takes points 8l..8l+7, loaded with vector
+// loads (ids, weights, one coordinate plane at a time) so that each group of loads is in
+// flight together.  A tile all of whose points lie in one block (most tiles: a block of
+// curve-sorted points spans many tiles) takes one warp reduction and one set of atomics.
+// Otherwise the runs of equal block ids inside each lane are added directly, except the
+// lane's last run, which goes through a segmented reduction over the lanes (runs continue
+// across lanes).  Sums are 128-bit fixed point, extremes ordered keys.
 template <typename T, int D>
 __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     const int lane = threadIdx.x & 31;
     const long long i0 = (long long)t * kTile + lane * 8;
     long long nv = p.n - i0;
     const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-    if (centroid_uniform_tile<T, D>(p, X, i0, nval)) return;
-    int cur = -1;
-    long long sum[D];
-    unsigned long long kmin[D], kmax[D];
+    int ids[8];
+    load_ids8(p, i0, nval, ids);
+    T wv[8];
+    if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
+    const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
+    bool same = true, bad = false;
+    int last = -1;  // block of the lane's last run
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-        sum[j] = 0;
-        kmin[j] = ~0ull;
-        kmax[j] = 0ull;
-    }
-    int bad = 0;
-    for (int q = 0; q < nval; ++q) {
-        int b = p.a16 ? (int)p.A16[i0 + q] : p.A[i0 + q];
-        if ((unsigned)b >= (unsigned)p.k) {
-            bad = 1;
-            continue;
-        }
-        if (b != cur) {
-            if (cur >= 0) {
-                for (int j = 0; j < D; ++j) {
-                    atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
-                    atomicMin(&p.BBlo[cur * D + j], kmin[j]);
-                    atomicMax(&p.BBhi[cur * D + j], kmax[j]);
-                }
-            }
-            cur = b;
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                sum[j] = 0;
-                kmin[j] = ~0ull;
-                kmax[j] = 0ull;
-            }
-        }
-        T wv = p.weighted ? ((const T *)p.Ws)[i0 + q] : (T)1;
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            T x = X[(size_t)j * p.n_pad + i0 + q];
-            long long v;
-            if (sizeof(T) == 8)
-                v = p.weighted ? fix_f64((double)wv * (double)x, p.Fx) : fix_f64((double)x, p.Fx);
-            else
-                v = p.weighted ? fix_prod_f32((float)wv, (float)x, p.Fx) : fix_f32((float)x, p.Fx);
-            sum[j] += v;
-            unsigned long long kk = KeyOf<T>::key(x);
-            kmin[j] = kk < kmin[j] ? kk : kmin[j];
-            kmax[j] = kk > kmax[j] ? kk : kmax[j];
+    for (int q = 0; q < 8; ++q) {
+        if (q < nval) {
+            same &= ids[q] == b0;
+            if ((unsigned)ids[q] >= (unsigned)p.k) bad = true;
+            else last = ids[q];
         }
     }
     if (bad) atomicOr(&p.ctl->bad_block, 1);
-    // segmented reduction of the lanes' last runs
-    int prev = __shfl_up_sync(0xffffffffu, cur, 1);
-    bool head = lane == 0 || cur != prev;
-    unsigned heads = __ballot_sync(0xffffffffu, head);
-    int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        bool take = lane - off >= start;
+    if (__all_sync(0xffffffffu, same) && (unsigned)b0 < (unsigned)p.k) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            long long s2 = __shfl_up_sync(0xffffffffu, sum[j], off);
-            unsigned long long a = __shfl_up_sync(0xffffffffu, kmin[j], off);
-            unsigned long long b = __shfl_up_sync(0xffffffffu, kmax[j], off);
-            if (take) {
-                sum[j] += s2;
-                kmin[j] = a < kmin[j] ? a : kmin[j];
-                kmax[j] = b > kmax[j] ? b : kmax[j];
+            T xv[8];
+            load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
+            long long sum = 0;
+            unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q < nval) {
+                    sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[q]);
+                    const unsigned long long kk = KeyOf<T>::key(xv[q]);
+                    kmin = kk < kmin ? kk : kmin;
+                    kmax = kk > kmax ? kk : kmax;
+                }
+            }
+            for (int off = 16; off; off >>= 1) {
+                sum += __shfl_xor_sync(0xffffffffu, sum, off);
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+                kmin = a < kmin ? a : kmin;
+                kmax = b > kmax ? b : kmax;
+            }
+            if (lane == 0) {
+                atomic_add_i128(&p.SXfix[2 * (b0 * D + j)], sum);
+                atomicMin(&p.BBlo[b0 * D + j], kmin);
+                atomicMax(&p.BBhi[b0 * D + j], kmax);
             }
         }
+        return;
     }
-    bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
-    if (end && cur >= 0) {
-        for (int j = 0; j < D; ++j) {
-            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum[j]);
-            atomicMin(&p.BBlo[cur * D + j], kmin[j]);
-            atomicMax(&p.BBhi[cur * D + j], kmax[j]);
+    // segments of the lanes' last runs (the same for every plane)
+    const int prev = __shfl_up_sync(0xffffffffu, last, 1);
+    const bool head = lane == 0 || last != prev;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        T xv[8];
+        load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
+        int cur = -1;
+        long long sum = 0;
+        unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nval && (unsigned)ids[q] < (unsigned)p.k) {
+                if (ids[q] != cur) {
+                    if (cur >= 0) {  // a run that ends inside the lane
+                        atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum);
+                        atomicMin(&p.BBlo[cur * D + j], kmin);
+                        atomicMax(&p.BBhi[cur * D + j], kmax);
+                    }
+                    cur = ids[q];
+                    sum = 0;
+                    kmin = ~0ull;
+                    kmax = 0ull;
+                }
+                sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[q]);
+                const unsigned long long kk = KeyOf<T>::key(xv[q]);
+                kmin = kk < kmin ? kk : kmin;
+                kmax = kk > kmax ? kk : kmax;
+            }
+        }
+        // the lanes' last runs: a run covers at most 256 values below 2^54, so 64 bits
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const bool take = lane - off >= start;
+            const long long s2 = __shfl_up_sync(0xffffffffu, sum, off);
+            const unsigned long long a = __shfl_up_sync(0xffffffffu, kmin, off);
+            const unsigned long long b = __shfl_up_sync(0xffffffffu, kmax, off);
+            if (take) {
+                sum += s2;
+                kmin = a < kmin ? a : kmin;
+                kmax = b > kmax ? b : kmax;
+            }
+        }
+        if (end && cur >= 0) {
+            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum);
+            atomicMin(&p.BBlo[cur * D + j], kmin);
+            atomicMax(&p.BBhi[cur * D + j], kmax);
         }
     }
 }
 
+// Tiles per warp of the marker path of the movement: a power of two up to 32, the
+// largest that still gives about two waves of warps over the SMs (a warp takes the tiles
+// without a marker one at a time, so with few tiles per SM fewer per warp keep every SM
+// busy).
+__host__ __device__ __forceinline__ int centroid_tiles_per_warp(int ntiles, int nsm) {
+    const long long want = (long long)(nsm > 0 ? nsm : 1) * 128;  // warps
+    int tpw = 32;
+    while (tpw > 1 && (long long)ntiles < want * tpw) tpw >>= 1;
+    return tpw;
+}
+
 // Center movement, part 1 (Algorithm 2, the weighted means; the block boxes of the
-// erosion's beta): one warp per 32 consecutive tiles, lane = tile.  A tile whose stored
+// erosion's beta): one warp per tpw consecutive tiles, lane = tile.  A tile whose stored
 // block ids are all b (its marker, kept by the assignment) adds its coordinate sums and
 // box, formed once at the bootstrap with the same conversions, to block b: a segmented
 // reduction over the lanes, then one set of atomics per run of equal blocks.  A tile sum
 // is below 2^62 in magnitude (256 values below 2^54), so the reduction over up to 32
-// tiles carries 128 bits.  The other tiles are then taken one at a time by the whole
-// warp, point by point.
+// tiles carries 128 bits.  The other tiles go to a list (the cooperative-tile list of the
+// assignment, free during the movement) that centroid_list_kernel takes point by point,
+// one warp per tile.
 template <typename T, int D>
 __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     count_launch(p.ctl);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long t = ((long long)blockIdx.x * kAssignWarps + w) * 32 + lane;
-    const bool has = t < p.ntiles;
+    const int tpw = centroid_tiles_per_warp(p.ntiles, p.nsm);
+    const long long t = ((long long)blockIdx.x * kAssignWarps + w) * tpw + lane;
+    const bool has = lane < tpw && t < p.ntiles;
     const int mk = has ? reinterpret_cast<const int *>(p.tiles)[8 * t + 7] : -2;
     const int cur = mk >= 0 && mk < p.k ? mk : -1;
     unsigned long long slo[D], shi[D];  // 128-bit sums (two's complement)
@@ -2225,13 +2302,25 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
             atomicMax(&p.BBhi[cur * D + j], kmax[j]);
         }
     }
-    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
-    unsigned rest = __ballot_sync(0xffffffffu, has && cur < 0);
-    while (rest) {
-        const int L = __ffs(rest) - 1;
-        rest &= rest - 1;
-        centroid_tile<T, D>(p, X, (int)(t - lane + L));
+    const bool mixed = has && cur < 0;
+    const unsigned rest = __ballot_sync(0xffffffffu, mixed);
+    if (rest) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctl->mixed_cnt, (unsigned)__popc(rest));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (mixed) p.coop[base + __popc(rest & ((1u << lane) - 1u))] = (int)t;
     }
+}
+
+// The tiles the marker pass listed, one warp per tile (grid-stride over the list).
+template <typename T, int D>
+__global__ void __launch_bounds__(kAssignWarps * 32) centroid_list_kernel(Prob p) {
+    count_launch(p.ctl);
+    const int cnt = (int)p.ctl->mixed_cnt;
+    const T *X = sizeof(T) == 8 ? (const T *)p.X64 : (const T *)p.X32;
+    const int nw = gridDim.x * kAssignWarps;
+    for (int i = blockIdx.x * kAssignWarps + (threadIdx.x >> 5); i < cnt; i += nw)
+        centroid_tile<T, D>(p, X, p.coop[i]);
 }
 
 // The same without tile markers: one tile per warp, in the assignment's permuted tile
@@ -2266,6 +2355,7 @@ __global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
     __shared__ int r_cnt[32];
     Ctl *ctl = p.ctl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (blockIdx.x == 0 && tid == 0) ctl->mixed_cnt = 0u;  // the list of this movement is done
     int c = blockIdx.x * blockDim.x + tid;
     double dl = 0.0, sdiag = 0.0;
     int cnt = 0;
@@ -2446,9 +2536,16 @@ static void *centroid_fn(const Prob &p) {
         return p.d == 2 ? (void *)centroid_points_kernel<double, 2> : (void *)centroid_points_kernel<double, 3>;
     return p.d == 2 ? (void *)centroid_points_kernel<float, 2> : (void *)centroid_points_kernel<float, 3>;
 }
-// the movement's accumulation: one warp per 32 consecutive tiles, or per tile
+// the movement's list of point-by-point tiles (marker path only)
+static void *centroid_list_fn(const Prob &p) {
+    if (!p.a16) return nullptr;
+    if (p.dtype == 1) return p.d == 2 ? (void *)centroid_list_kernel<double, 2> : (void *)centroid_list_kernel<double, 3>;
+    return p.d == 2 ? (void *)centroid_list_kernel<float, 2> : (void *)centroid_list_kernel<float, 3>;
+}
+static int centroid_list_grid(const Prob &p) { return (p.nsm > 0 ? p.nsm : 1) * 8; }
+// the movement's accumulation: one warp per tpw consecutive tiles, or per tile
 static int tile_warp_grid(const Prob &p) {
-    const int per = p.a16 ? kAssignWarps * 32 : kAssignWarps;
+    const int per = kAssignWarps * (p.a16 ? centroid_tiles_per_warp(p.ntiles, p.nsm) : 1);
     return (p.ntiles + per - 1) / per;
 }
 
@@ -2537,8 +2634,12 @@ cudaError_t launch_block_weights(const Prob &p, cudaStream_t s) {
 
 cudaError_t launch_centroid(const Prob &p, cudaStream_t s) {
     void *args1[] = {(void *)&p};
-    return cudaLaunchKernel(centroid_fn(p), dim3(tile_warp_grid(p)), dim3(kAssignWarps * 32),
-                            args1, 0, s);
+    cudaError_t e = cudaLaunchKernel(centroid_fn(p), dim3(tile_warp_grid(p)), dim3(kAssignWarps * 32),
+                                     args1, 0, s);
+    if (e == cudaSuccess && centroid_list_fn(p))
+        e = cudaLaunchKernel(centroid_list_fn(p), dim3(centroid_list_grid(p)), dim3(kAssignWarps * 32),
+                             args1, 0, s);
+    return e;
 }
 cudaError_t launch_move_finish(const Prob &p, int mode, cudaStream_t s) {
     finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
@@ -2549,9 +2650,7 @@ cudaError_t launch_move_finish(const Prob &p, int mode, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_move(const Prob &p, int mode, cudaStream_t s) {
-    void *args1[] = {(void *)&p};
-    cudaError_t e = cudaLaunchKernel(centroid_fn(p), dim3(tile_warp_grid(p)),
-                                     dim3(kAssignWarps * 32), args1, 0, s);
+    cudaError_t e = launch_centroid(p, s);
     if (e != cudaSuccess) return e;
     finalize_a_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0, 0);
     if (mode == 0 || mode == 3) {
@@ -2662,6 +2761,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
             if (bl.err != cudaSuccess) mv.err = bl.err;
         }
         mv.kernel(centroid_fn(p), tg, tb, a_p);
+        if (centroid_list_fn(p)) mv.kernel(centroid_list_fn(p), dim3(centroid_list_grid(p)), tb, a_p);
         mv.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
         mv.kernel((void *)finalize_b_kernel, kg, kb, a_p);
         if (p.nsgroups > 0) mv.kernel((void *)supergroup_kernel, sgg, sgb, a_p);
@@ -2725,6 +2825,7 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
         if (bl.err != cudaSuccess) top.err = bl.err;
     }
     top.kernel(centroid_fn(ps), tg, tb, a_p);
+    if (centroid_list_fn(ps)) top.kernel(centroid_list_fn(ps), dim3(centroid_list_grid(ps)), tb, a_p);
     top.kernel((void *)finalize_a_kernel, kg, kb, a_fin);
     top.kernel((void *)finalize_b_kernel, kg, kb, a_p);
     if (ps.nsgroups > 0) top.kernel((void *)supergroup_kernel, sgg, sgb, a_p);

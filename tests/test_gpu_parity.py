@@ -577,6 +577,13 @@ def test_every_launch_shape_gives_the_same_partition(gk, shape, d, dtype, n, k, 
     _, _, _, res2 = gk.partition(_dev(x), k, 0.03, options=o)
     assert res2["tune_ms"] == 0.0 and res2["supertile_tiles"] == res["supertile_tiles"]
     assert res2["assign_ctas_per_sm"] == res["assign_ctas_per_sm"]
+    # a shape the caller fixes holds although the same kind of problem was tuned before
+    other = 16 if res["supertile_tiles"] == 32 else 32
+    hy = 2 if res["hypertiles"] == 1 else 1
+    b3, _, _, res3 = gk.partition(_dev(x), k, 0.03, options=gk.default_options(
+        assign_dtype=assign, supertile_tiles=other, hypertiles=hy))
+    assert res3["supertile_tiles"] == other and res3["hypertiles"] == hy
+    assert np.array_equal(_np(b3), outs[0][0])
 
 
 def test_launch_shape_options_are_checked(gk):
