@@ -424,6 +424,15 @@ int ilog2(long long v) {
     return e;
 }
 
+// The loop's sums are kept in the carry-free form (two words per value, see
+// red_add_s64); the exchange between shards sums them as 128-bit integers.
+static void splits_to_i128(std::vector<unsigned long long> &v) {
+    for (size_t i = 0; i + 1 < v.size(); i += 2) split_to_i128(v[i], v[i + 1], v[i], v[i + 1]);
+}
+static void i128s_to_split(std::vector<unsigned long long> &v) {
+    for (size_t i = 0; i + 1 < v.size(); i += 2) i128_to_split(v[i], v[i + 1], v[i], v[i + 1]);
+}
+
 // State shared by the entry points of one call.
 struct Call {
     cudaStream_t s;
@@ -541,8 +550,10 @@ struct Call {
         std::vector<unsigned long long> w(2 * (size_t)p.k);
         GK_CUDA(cudaMemcpyAsync(w.data(), p.Sfix, w.size() * 8, cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
+        splits_to_i128(w);
         gk_status st = ex->sum128(w.data(), p.k);
         if (st != GK_OK) return st;
+        i128s_to_split(w);
         GK_CUDA(cudaMemcpyAsync(p.Sfix, w.data(), w.size() * 8, cudaMemcpyHostToDevice, s));
         GK_CUDA(cudaStreamSynchronize(s));
         return GK_OK;
@@ -557,9 +568,11 @@ struct Call {
         GK_CUDA(cudaMemcpyAsync(hi.data(), p.BBhi, kd * 8, cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
         gk_status st;
+        splits_to_i128(sx);
         if ((st = ex->sum128(sx.data(), kd)) != GK_OK || (st = ex->keys(lo.data(), kd, false)) != GK_OK ||
             (st = ex->keys(hi.data(), kd, true)) != GK_OK)
             return st;
+        i128s_to_split(sx);
         GK_CUDA(cudaMemcpyAsync(p.SXfix, sx.data(), sx.size() * 8, cudaMemcpyHostToDevice, s));
         GK_CUDA(cudaMemcpyAsync(p.BBlo, lo.data(), kd * 8, cudaMemcpyHostToDevice, s));
         GK_CUDA(cudaMemcpyAsync(p.BBhi, hi.data(), kd * 8, cudaMemcpyHostToDevice, s));

@@ -166,8 +166,8 @@ struct Prob {
     int nsm;                    // streaming multiprocessors of the device
     // per-center state
     double *C, *Cm, *delta, *S64, *Iin, *I2, *g64_2, *part;
-    unsigned long long *Sfix;   // 2 per block (lo, hi)
-    unsigned long long *SXfix;  // 2 per (block, axis)
+    unsigned long long *Sfix;   // 2 per block, the carry-free form (red_add_*)
+    unsigned long long *SXfix;  // 2 per (block, axis), the carry-free form
     unsigned long long *BBlo, *BBhi;  // per (block, axis) ordered keys (input precision)
     float4 *cdata2;             // 2 buffers x 2 float4 per block
     float4 *gdata2;             // 2 buffers x 2 float4 per group of kGroup blocks
@@ -298,6 +298,45 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long *lohi, unsign
     if (old + v < old) atomicAdd(lohi + 1, 1ull);
 }
 // Value of a 128-bit two's-complement integer times 2^-F, as FP64.
+// Exact sums without carries (the loop's block weights and coordinate sums): word 0
+// gathers the low 32 bits of every addend, word 1 the rest (an arithmetic shift by 32,
+// wrapping in 64 bits), so every update is a plain add whose result is not waited for.
+// The sum is word1 * 2^32 + word0 while fewer than 2^32 values are added and the high
+// parts total below 2^63 in magnitude.
+__device__ __forceinline__ void red_add_s64(unsigned long long *w, long long v) {
+    atomicAdd(w, (unsigned long long)v & 0xffffffffull);
+    const long long h = v >> 32;
+    if (h) atomicAdd(w + 1, (unsigned long long)h);
+}
+__device__ __forceinline__ void red_add_u64(unsigned long long *w, unsigned long long v) {
+    atomicAdd(w, v & 0xffffffffull);
+    if (v >> 32) atomicAdd(w + 1, v >> 32);
+}
+// a 128-bit two's-complement addend (lo, hi) of magnitude below 2^95
+__device__ __forceinline__ void red_add_s128(unsigned long long *w, unsigned long long lo, unsigned long long hi) {
+    atomicAdd(w, lo & 0xffffffffull);
+    const unsigned long long h = (hi << 32) | (lo >> 32);
+    if (h) atomicAdd(w + 1, h);
+}
+// (word0, word1) of the carry-free form -> 128-bit two's complement (lo, hi)
+__host__ __device__ __forceinline__ void split_to_i128(unsigned long long w0, unsigned long long w1,
+                                                       unsigned long long &lo, unsigned long long &hi) {
+    const unsigned long long a = w1 << 32;
+    const unsigned long long b = (unsigned long long)((long long)w1 >> 32);
+    lo = a + w0;
+    hi = b + (lo < a ? 1ull : 0ull);
+}
+// 128-bit two's complement (lo, hi) of magnitude below 2^95 -> the carry-free form
+__host__ __device__ __forceinline__ void i128_to_split(unsigned long long lo, unsigned long long hi,
+                                                       unsigned long long &w0, unsigned long long &w1) {
+    w0 = lo & 0xffffffffull;
+    w1 = (hi << 32) | (lo >> 32);
+}
+__device__ __forceinline__ double split_to_f64(unsigned long long w0, unsigned long long w1, int F) {
+    unsigned long long lo, hi;
+    split_to_i128(w0, w1, lo, hi);
+    return ldexp((double)(long long)hi * 18446744073709551616.0 + (double)lo, -F);
+}
 __device__ __forceinline__ double i128_to_f64(unsigned long long lo, unsigned long long hi, int F) {
     double v = (double)(long long)hi * 18446744073709551616.0 + (double)lo;
     return ldexp(v, -F);

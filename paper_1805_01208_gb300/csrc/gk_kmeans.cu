@@ -894,7 +894,7 @@ __device__ __forceinline__ void seg_flush_u64(int id, unsigned long long v, unsi
     bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
     if (end && id >= 0) {
         if (wide)
-            atomic_add_u128(&acc[2 * id], v);
+            red_add_u64(&acc[2 * id], v);
         else
             atomicAdd(&acc[2 * id], v);
     }
@@ -1002,7 +1002,7 @@ __device__ __forceinline__ bool store_blocks_tile(const Prob &p, int t, long lon
 // conversion of every weight as tile_histogram uses.
 __device__ __forceinline__ void tile_weight_to(const Prob &p, int t, int b) {
     if (p.weighted) {
-        atomic_add_u128(&p.Sfix[2 * b], p.tws[t]);
+        red_add_u64(&p.Sfix[2 * b], p.tws[t]);
     } else {
         const long long nv = p.n - (long long)t * kTile;
         atomicAdd(&p.Sfix[2 * b], (unsigned long long)(nv < kTile ? nv : kTile));
@@ -1024,7 +1024,7 @@ __device__ __forceinline__ void tile_histogram(const Prob &p, long long i0, int 
             if (best[q] != cur) {
                 if (cur >= 0) {
                     if (p.weighted)
-                        atomic_add_u128(&p.Sfix[2 * cur], acc);
+                        red_add_u64(&p.Sfix[2 * cur], acc);
                     else
                         atomicAdd(&p.Sfix[2 * cur], acc);
                 }
@@ -1898,7 +1898,7 @@ __global__ void block_weights_kernel(Prob p) {
     if (valid && p.weighted)
         v = (unsigned long long)(p.dtype == 1 ? fix_f64(((const double *)p.Ws)[i], p.Fw)
                                               : fix_f32(((const float *)p.Ws)[i], p.Fw));
-    if (valid) atomic_add_u128(&p.Sfix[2 * b], v);
+    if (valid) red_add_u64(&p.Sfix[2 * b], v);
 }
 
 // ------------------------------------------------------------------------------
@@ -1930,8 +1930,8 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
     double S = 0.0, gnew = 0.0;
     float4 hc = make_float4(0.f, 0.f, 0.f, 0.f);
     if (c < p.k) {
-        unsigned long long lo = p.Sfix[2 * c], hi = p.Sfix[2 * c + 1];
-        S = p.weighted ? i128_to_f64(lo, hi, p.Fw) : (double)lo;
+        const unsigned long long w0 = p.Sfix[2 * c], w1 = p.Sfix[2 * c + 1];
+        S = p.weighted ? split_to_f64(w0, w1, p.Fw) : (double)(w0 + (w1 << 32));  // counts < 2^53
         p.S64[c] = S;
         p.Sfix[2 * c] = 0ull;
         p.Sfix[2 * c + 1] = 0ull;
@@ -2136,6 +2136,9 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     load_ids8(p, i0, nval, ids);
     T wv[8];
     if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
+    T xv[D][8];  // every plane, loaded with the ids (one round trip)
+#pragma unroll
+    for (int j = 0; j < D; ++j) load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv[j]);
     const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
     bool same = true, bad = false;
     int last = -1;  // block of the lane's last run
@@ -2151,15 +2154,13 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     if (__all_sync(0xffffffffu, same) && (unsigned)b0 < (unsigned)p.k) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            T xv[8];
-            load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
             long long sum = 0;
             unsigned long long kmin = ~0ull, kmax = 0ull;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (q < nval) {
-                    sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[q]);
-                    const unsigned long long kk = KeyOf<T>::key(xv[q]);
+                    sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
+                    const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
                     kmin = kk < kmin ? kk : kmin;
                     kmax = kk > kmax ? kk : kmax;
                 }
@@ -2172,7 +2173,7 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
                 kmax = b > kmax ? b : kmax;
             }
             if (lane == 0) {
-                atomic_add_i128(&p.SXfix[2 * (b0 * D + j)], sum);
+                red_add_s64(&p.SXfix[2 * (b0 * D + j)], sum);
                 atomicMin(&p.BBlo[b0 * D + j], kmin);
                 atomicMax(&p.BBhi[b0 * D + j], kmax);
             }
@@ -2187,8 +2188,6 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     const bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        T xv[8];
-        load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv);
         int cur = -1;
         long long sum = 0;
         unsigned long long kmin = ~0ull, kmax = 0ull;
@@ -2197,7 +2196,7 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
             if (q < nval && (unsigned)ids[q] < (unsigned)p.k) {
                 if (ids[q] != cur) {
                     if (cur >= 0) {  // a run that ends inside the lane
-                        atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum);
+                        red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
                         atomicMin(&p.BBlo[cur * D + j], kmin);
                         atomicMax(&p.BBhi[cur * D + j], kmax);
                     }
@@ -2206,8 +2205,8 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
                     kmin = ~0ull;
                     kmax = 0ull;
                 }
-                sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[q]);
-                const unsigned long long kk = KeyOf<T>::key(xv[q]);
+                sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
+                const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
                 kmin = kk < kmin ? kk : kmin;
                 kmax = kk > kmax ? kk : kmax;
             }
@@ -2226,7 +2225,7 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
             }
         }
         if (end && cur >= 0) {
-            atomic_add_i128(&p.SXfix[2 * (cur * D + j)], sum);
+            red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
             atomicMin(&p.BBlo[cur * D + j], kmin);
             atomicMax(&p.BBhi[cur * D + j], kmax);
         }
@@ -2297,7 +2296,7 @@ __global__ void __launch_bounds__(kAssignWarps * 32) centroid_kernel(Prob p) {
     bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
     if (end && cur >= 0) {
         for (int j = 0; j < D; ++j) {
-            atomic_add_i128_full(&p.SXfix[2 * (cur * D + j)], slo[j], shi[j]);
+            red_add_s128(&p.SXfix[2 * (cur * D + j)], slo[j], shi[j]);
             atomicMin(&p.BBlo[cur * D + j], kmin[j]);
             atomicMax(&p.BBhi[cur * D + j], kmax[j]);
         }
@@ -2366,7 +2365,7 @@ __global__ void __launch_bounds__(kKThreads) finalize_a_kernel(Prob p, int mode,
             double diag = 0.0;
             for (int j = 0; j < p.d; ++j) {
                 size_t q = 2 * ((size_t)c * p.d + j);
-                double cm = i128_to_f64(p.SXfix[q], p.SXfix[q + 1], p.Fx) / S;
+                double cm = split_to_f64(p.SXfix[q], p.SXfix[q + 1], p.Fx) / S;
                 double m = cm - p.C[c * p.d + j];
                 dd += m * m;
                 p.Cm[c * p.d + j] = cm;

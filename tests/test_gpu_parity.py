@@ -409,6 +409,23 @@ def test_full_size_gmm3d_1e7_k1024(gk):
 
 
 # ----------------------------------------------------------------------------------------
+# The two-pass scatter of the block ids to input order (problems of 2^22 points or more):
+# every returned id, in input order, against the FP64 assignment of the same points under
+# the returned centers and influence computed without any sort (gk_assign keeps the
+# input order); n just above 2^22 and a ragged count.
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [(1 << 22) + 1, 5_000_003])
+def test_two_pass_scatter_returns_input_order(gk, n):
+    x = _points("spots", n, 2, 91, "f32")
+    xt = _dev(x)
+    block, C, I, res = gk.partition(xt, 96, 0.03, options=gk.default_options(assign_dtype="f64"))
+    assert res["status"] == 0
+    ref, _ = gk.assign(xt, C, I, assign_dtype="f64")
+    assert np.array_equal(_np(block), _np(ref))
+    assert np.bincount(_np(block), minlength=96).sum() == n
+
+
+# ----------------------------------------------------------------------------------------
 # Full size of the FP32-form workloads (2-D, n = 1e8 with k = 4096, and n = 1e9 with
 # k = 16384), checked on sampled outputs: Hilbert keys bit-exact on a sample (the sample
 # carries the points that attain the bounding box, so the oracle quantises with the
