@@ -14,7 +14,8 @@ Prints one JSON line (rank 0):
                whole job: sum over steps of n * (assignment passes) / sum of step times
                (bootstrap and movement time included in the denominator)
   e2e          the same through the C ABI with pinned host buffers (copies in the region)
-  roofline     the assignment kernel: algorithmic bytes per launch / mean launch time
+  roofline     the assignment pass (filter, assignment and balance kernels, which together
+               assign every point once): algorithmic bytes per pass / mean pass time
   fp32_form    the FP32 form's statistics: fraction of points assigned differently from
                the FP64 argmin under the returned centers and influence (all points), the
                largest error of the centroid step against FP64 means, the exact imbalance
@@ -309,33 +310,33 @@ def _timed(stream, flush, fn, steps):
 
 
 def _roofline(gk, xt, wt, spec, workload):
-    """The assignment kernel's HBM roofline: algorithmic bytes of one balance pass (every
-    point's coordinates and weight read once) over the mean CUDA-event duration of its
-    launches in a host-driven run of the same partition (events on the library's stream)."""
+    """The HBM roofline of the assignment pass, the unit that assigns every point once:
+    the filter kernels (which also finish the tiles with a single candidate), the
+    assignment kernel (the tiles of the filter's work list) and the balance kernel.
+    achieved = algorithmic bytes of one pass (every point's coordinates and weight read
+    once) over the mean CUDA-event duration of those launches per pass, in a host-driven
+    run of the same partition (events on the library's stream)."""
     n, d, k = int(xt.shape[0]), spec["d"], spec["k"]
     timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1)
     _, _, _, tres = gk.partition(xt, k, spec["eps"], weights=wt, options=timed)
-    ev_avg = tres["time_assign_ms"] / max(1, tres["assign_launches"])
+    npass = max(1, tres["assign_launches"])
+    ev_assign = tres["time_assign_ms"] / npass
+    ev_filter = tres["time_filter_ms"] / max(1, tres["filter_launches"])
+    ev_balance = tres["time_balance_ms"] / max(1, tres["balance_launches"])
+    pass_ms = (tres["time_assign_ms"] + tres["time_filter_ms"] + tres["time_balance_ms"]) / npass
     es = 8 if spec["dtype"] == "f64" else 4
     sw = es if spec["weighted"] else 0
-    bytes_per_launch = n * (d * es + sw)
-    # what the assignment kernel itself streams: FP32 frame coordinates, 16-bit block ids
-    # (k <= 65535), weights
-    kernel_bytes = n * (d * 4 + (2 if k <= 65535 else 4) + sw)
+    bytes_per_pass = n * (d * es + sw)
     peak, peak_kind = _peaks()
-    achieved = bytes_per_launch / (ev_avg * 1e-3) / 1e9
+    achieved = bytes_per_pass / (pass_ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "assign_kernel",
-            "bytes_per_launch": bytes_per_launch, "kernel_stream_bytes_per_launch": kernel_bytes,
-            "kernel_stream_frac": kernel_bytes / (ev_avg * 1e-3) / 1e9 / peak,
-            "launch_ms_events": ev_avg, "peak_source": peak_kind,
-            "other_kernels_ms_per_pass": {
-                "filter": tres["time_filter_ms"] / max(1, tres["filter_launches"]),
-                "balance": tres["time_balance_ms"] / max(1, tres["balance_launches"]),
-                "move_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])},
-            "pass_ms_events": (tres["time_assign_ms"] + tres["time_filter_ms"]
-                               + tres["time_balance_ms"]) / max(1, tres["assign_launches"])}
-    roof["pass_frac"] = bytes_per_launch / (roof["pass_ms_events"] * 1e-3) / 1e9 / peak
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "assignment pass (filter_kernel + filter_big_kernel [+ hyper_kernel] "
+                      "+ assign_kernel + balance_kernel)",
+            "bytes_per_launch": bytes_per_pass, "launch_ms_events": pass_ms,
+            "peak_source": peak_kind,
+            "kernels_ms_per_pass": {"filter": ev_filter, "assign": ev_assign, "balance": ev_balance},
+            "move_ms_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])}
     _attach_traffic(roof, workload)
     return roof
 
@@ -421,7 +422,7 @@ def _fp32_stats(gk, xt, wt, spec, block, C, I, block_host, w_host):
 
 def _config_leg(gk, name, stream, flush, steps, x=None, w=None, spec=None):
     """One workload as a leg of the line: partition time and points/s over `steps` timed
-    calls, its assignment kernel's roofline and, for the FP32 form, its statistics."""
+    calls, its assignment pass's roofline and, for the FP32 form, its statistics."""
     import torch
     from paper_1805_01208_gb300 import synth
     if name == BATCHED_WORKLOAD:
@@ -574,11 +575,11 @@ def main():
     # ---- end to end through the C ABI with pinned host buffers -------------------------
     e2e = _e2e(gk, x, w, spec, opts, stream, max(1, min(3, args.steps)))
 
-    # ---- roofline of the assignment kernel ---------------------------------------------
+    # ---- roofline of the assignment pass -----------------------------------------------
     roof = _roofline(gk, xt, wt, spec, args.workload)
     live_ms = sum(r["assign_live_ms"] for r in results)
     live_n = sum(r["assign_live_launches"] for r in results)
-    roof["launch_ms_live_graph"] = live_ms / max(1, live_n)
+    roof["assign_kernel_ms_live_graph"] = live_ms / max(1, live_n)
 
     # ---- FP32-form statistics under the returned state ----------------------------------
     fp32 = None
@@ -895,12 +896,12 @@ def _quality(gk, synth, spec, stream, k=1024, seed=2):
 
 
 def _attach_traffic(roof, workload):
-    """DRAM traffic per launch from the committed ncu summary of this kernel, if any."""
-    path = os.path.join(ROOT, "profiles", f"assign_kernel_{workload}.md")
+    """DRAM traffic of one assignment pass from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", f"assignment_pass_{workload}.md")
     try:
         with open(path) as f:
             for line in f:
-                if line.strip().startswith("dram_bytes_per_launch:"):
+                if line.strip().startswith("dram_bytes_per_pass:"):
                     val = line.split(":", 1)[1].strip().split()[0]
                     roof["traffic"] = None if val == "null" else float(val)
                     roof["traffic_source"] = os.path.relpath(path, ROOT)

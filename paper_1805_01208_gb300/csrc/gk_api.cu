@@ -214,6 +214,7 @@ size_t layout(Prob &p, Bufs &b, char *base, bool sort, bool stage_coords, bool s
     p.supers = (float4 *)take((size_t)p.nsupers * 32);
     p.trec = (float4 *)take((size_t)p.ntiles * kRecF4 * 16);
     p.coop = (int *)take((size_t)p.ntiles * 4);
+    p.mlist = (int2 *)take((size_t)p.ntiles * 8);
     p.bigs = (int *)take((size_t)p.nsupers * 16);
     p.blists = (int *)take((size_t)p.nsupers * kWarpList * 4);
     {
@@ -270,6 +271,7 @@ struct SampleBufs {
     long long *tsx = nullptr;
     unsigned long long *tlo = nullptr, *thi = nullptr;
     int *coop = nullptr, *bigs = nullptr, *blists = nullptr;
+    int2 *mlist = nullptr;
     float4 *hypers = nullptr;
     int *hlists = nullptr, *hlen = nullptr;
     float *hlam = nullptr;
@@ -307,6 +309,7 @@ size_t layout_sample(const Prob &p, SampleBufs &sb, char *base, bool stage_order
     sb.supers = (float4 *)take((size_t)ns * 32);
     sb.trec = (float4 *)take((size_t)nt * kRecF4 * 16);
     sb.coop = (int *)take((size_t)nt * 4);
+    sb.mlist = (int2 *)take((size_t)nt * 8);
     sb.bigs = (int *)take((size_t)ns * 16);
     sb.blists = (int *)take((size_t)ns * kWarpList * 4);
     {
@@ -642,7 +645,7 @@ struct Call {
                         GK_CUDA(launch_assign(p, s));
                         GK_CUDA(cudaEventRecord(e1, s));
                         GK_CUDA(cudaMemsetAsync(p.Sfix, 0, (size_t)p.k * 16, s));
-                        GK_CUDA(cudaMemsetAsync(&p.ctl->coop_cnt, 0, 2 * sizeof(unsigned), s));
+                        GK_CUDA(cudaMemsetAsync(&p.ctl->coop_cnt, 0, 3 * sizeof(unsigned), s));
                         GK_CUDA(cudaEventSynchronize(e1));
                         float ms = 0.f;
                         GK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -863,6 +866,7 @@ Prob sample_prob(const Prob &p, const SampleBufs &sb, long long m) {
     ps.supers = sb.supers;
     ps.trec = sb.trec;
     ps.coop = sb.coop;
+    ps.mlist = sb.mlist;
     ps.bigs = sb.bigs;
     ps.blists = sb.blists;
     ps.hypers = sb.hypers;

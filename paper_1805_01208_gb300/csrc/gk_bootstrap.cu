@@ -978,95 +978,7 @@ cudaError_t launch_centers(const Prob &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------
-// Scatter of a large problem's block ids to input order in two passes, so that the
-// output is written in whole lines instead of one 4-byte word per random address.
-// Pass 1 reads the curve-ordered (destination, id) pairs in order and appends each
-// to the region of its destination bucket (destinations [b 2^S, (b+1) 2^S), at most
-// 256 buckets): a tile of kBucketTile pairs per CTA iteration counts its buckets in
-// shared memory and reserves a run in each bucket's region with one atomic per
-// bucket, then writes its pairs into those runs (the order inside a bucket does not
-// matter: every pair carries its destination).  Every destination occurs once, so
-// bucket b receives exactly the size of its range and its region starts at b 2^S.
-// Pass 2 writes out[dst] = id in bucket order: the writes in flight stay inside a few
-// buckets' 2^S-word windows, which the L2 holds until whole lines are written back.
-// ------------------------------------------------------------------------------
-constexpr int kBucketItems = 16;
-constexpr int kBucketTile = 256 * kBucketItems;
-
-__global__ void __launch_bounds__(256) scatter_bucket_kernel(const int *A_sorted, const unsigned short *A16_sorted,
-                                                             const unsigned *perm, long long n, int S,
-                                                             unsigned *fill, unsigned *bdst, unsigned *bid,
-                                                             Ctl *ctl) {
-    count_launch(ctl);
-    __shared__ unsigned cnt[256], base[256];
-    const int tid = threadIdx.x;
-    const long long ntile = (n + kBucketTile - 1) / kBucketTile;
-    for (long long tl = blockIdx.x; tl < ntile; tl += gridDim.x) {
-        cnt[tid] = 0u;
-        __syncthreads();
-        unsigned dst[kBucketItems], id[kBucketItems], br[kBucketItems];
-#pragma unroll
-        for (int q = 0; q < kBucketItems; ++q) {
-            const long long i = tl * kBucketTile + (long long)q * 256 + tid;  // coalesced
-            br[q] = 0xffffffffu;
-            if (i < n) {
-                dst[q] = perm[i];
-                id[q] = A16_sorted ? (unsigned)A16_sorted[i] : (unsigned)A_sorted[i];
-                const unsigned b = dst[q] >> S;  // < 256 for a destination < n <= 256 2^S
-                br[q] = (b << 24) | atomicAdd(&cnt[b], 1u);  // rank < kBucketTile < 2^24
-            }
-        }
-        __syncthreads();
-        if (cnt[tid]) base[tid] = ((unsigned)tid << S) + atomicAdd(&fill[tid], cnt[tid]);
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kBucketItems; ++q) {
-            if (br[q] != 0xffffffffu) {
-                const unsigned at = base[br[q] >> 24] + (br[q] & 0xffffffu);
-                if ((long long)at < n) {  // always true: bucket b gets exactly its range
-                    bdst[at] = dst[q];
-                    bid[at] = id[q];
-                }
-            }
-        }
-        __syncthreads();  // cnt and base are reused by the next tile
-    }
-}
-
-__global__ void scatter_write_kernel(const unsigned *bdst, const unsigned *bid, long long n, int *out,
-                                     Ctl *ctl) {
-    count_launch(ctl);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const unsigned j = bdst[i];
-        if ((long long)j < n) out[j] = (int)bid[i];
-    }
-}
-
-// Problems of at least this many points take the two-pass scatter (the keys of the
-// bootstrap's sort, free by then, hold the bucketed pairs).
-constexpr long long kBucketScatterMin = 1ll << 22;
-
 cudaError_t launch_scatter(const Prob &p, const unsigned *perm, int *out, cudaStream_t s) {
-    if (perm && p.keys[0] && p.keys[1] && p.n >= kBucketScatterMin) {
-        int S = 0;
-        while ((((long long)256) << S) < p.n) ++S;  // 256 buckets of 2^S destinations cover [0, n)
-        unsigned *fill = reinterpret_cast<unsigned *>(p.keys[1]);  // 256 counters
-        unsigned *bdst = reinterpret_cast<unsigned *>(p.keys[0]);
-        unsigned *bid = bdst + p.n;  // keys[0] holds 2 n words
-        cudaError_t e = cudaMemsetAsync(fill, 0, 256 * sizeof(unsigned), s);
-        if (e != cudaSuccess) return e;
-        const long long ntile = (p.n + kBucketTile - 1) / kBucketTile;
-        const long long gmax = (long long)(p.nsm > 0 ? p.nsm : 1) * 8;
-        const int g1 = (int)(ntile < gmax ? ntile : gmax);
-        scatter_bucket_kernel<<<g1, 256, 0, s>>>(p.A, p.a16 ? p.A16 : nullptr, perm, p.n, S, fill, bdst, bid,
-                                                 p.ctl);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        scatter_write_kernel<<<(p.nsm > 0 ? p.nsm : 1) * 16, 256, 0, s>>>(bdst, bid, p.n, out, p.ctl);
-        return cudaGetLastError();
-    }
     scatter_kernel<<<blocks_for(p.n, 256), 256, 0, s>>>(p.A, p.a16 ? p.A16 : nullptr, perm, p.n, out, p.ctl);
     return cudaGetLastError();
 }

@@ -95,6 +95,7 @@ struct Ctl {
     unsigned int done_count;                // last-block-done counter (reset by the last block)
     unsigned int coop_cnt;                  // tiles in the cooperative list (reset before each filter)
     unsigned int big_cnt;                   // supertiles with long candidate lists (same)
+    unsigned int multi_cnt;                 // tiles in the assignment's work list (same)
     unsigned int mixed_cnt;                 // tiles the movement takes point by point (reset
                                             //   by the movement's finalize kernel)
     int nonempty;                           // non-empty blocks of the last movement
@@ -160,6 +161,8 @@ struct Prob {
     // per-tile candidate records; tiles that need more than the inline candidates
     float4 *trec;
     int *coop;                  // tiles of the cooperative path (ntiles entries)
+    int2 *mlist;                // the assignment's work list: (tile, candidate count) of
+                                // every tile it evaluates per warp (ntiles entries)
     int *bigs;                  // per long-list supertile: index, list length, largest g, smallest
                                 // dropped lower bound (bits)
     int *blists;                // their candidate lists, kWarpList entries each

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->nonempty = 0;
         ctl->coop_cnt = 0u;
         ctl->big_cnt = 0u;
+        ctl->multi_cnt = 0u;
         ctl->phase_pass = 0;
         ctl->min_lr_key = 0xffffffffu;
         ctl->max_lr_key = 0u;
@@ -571,39 +572,45 @@ __device__ __forceinline__ int list_from_hyper(const Prob &p, const float4 *box,
         sh[1] = __fadd_ru(b.y, infl);
         sh[2] = __fadd_ru(b.z, infl);
     }
+    // one pass of loads: the lane's list entries (at most kHyperList / 32) and their
+    // bounds stay in registers for the keep pass
+    constexpr int kR = kHyperList / 32;
+    int cs[kR];
+    float lbs[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int i = r * 32 + lane;
+        cs[r] = i < Lh ? hl[i] : -1;
+    }
     float tc = INFINITY;
-    for (int i = lane; i < Lh; i += 32) {
-        const int c = hl[i];
-        float lb, ub;
-        box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
-        tc = fminf(tc, ub);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        lbs[r] = INFINITY;
+        if (cs[r] >= 0) {
+            float lb, ub;
+            box_bounds<D>(__ldg(&cd[2 * cs[r]]), __ldg(&cd[2 * cs[r] + 1]), so, sh, lb, ub);
+            lbs[r] = lb;
+            tc = fminf(tc, ub);
+        }
     }
     for (int off = 16; off; off >>= 1) tc = fminf(tc, __shfl_xor_sync(0xffffffffu, tc, off));
     const float tauS = __fmul_ru(tc, 1.0f + 64.0f * kU);
     float lam = lamH;
     int L = 0;
-    for (int base = 0; base < Lh; base += 32) {
-        const int i = base + lane;
-        bool keep = false;
-        int c = 0;
-        float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = ch;
-        if (i < Lh) {
-            c = hl[i];
-            ch = __ldg(&cd[2 * c]);
-            cl = __ldg(&cd[2 * c + 1]);
-            float lb, ub;
-            box_bounds<D>(ch, cl, so, sh, lb, ub);
-            keep = !(lb > tauS);
-            if (!keep) lam = fminf(lam, lb);
-        }
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        if (r * 32 >= Lh) break;
+        const int c = cs[r];
+        const bool keep = c >= 0 && !(lbs[r] > tauS);  // a NaN bound keeps the center
+        if (c >= 0 && !keep) lam = fminf(lam, lbs[r]);
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int pos = L + __popc(bal & lt);
         if (keep) {
             glist_out[pos] = c;  // L <= Lh <= kHyperList <= kWarpList
             if (pos < kLaneMax) {
                 list[pos] = c;
-                lcd[2 * pos] = ch;
-                lcd[2 * pos + 1] = cl;
+                lcd[2 * pos] = __ldg(&cd[2 * c]);
+                lcd[2 * pos + 1] = __ldg(&cd[2 * c + 1]);
             }
         }
         L += __popc(bal);
@@ -668,6 +675,49 @@ __device__ __forceinline__ void add_candidates(const Prob &p, int stripe, unsign
     if (v) atomicAdd(&p.ctl->cand_stripes[(stripe % kStripes) * kStripeStride], v);
 }
 
+// Block weights of a tile all of whose points went to block b (called by lane 0): the
+// tile's point count, or its weight sum formed at the bootstrap with the same fixed-point
+// conversion of every weight as tile_histogram uses.
+__device__ __forceinline__ void tile_weight_to(const Prob &p, int t, int b) {
+    if (p.weighted) {
+        red_add_u64(&p.Sfix[2 * b], p.tws[t]);
+    } else {
+        const long long nv = p.n - (long long)t * kTile;
+        atomicAdd(&p.Sfix[2 * b], (unsigned long long)(nv < kTile ? nv : kTile));
+    }
+}
+
+// A tile whose only candidate is c1 (without per-point bounds to keep up) is finished by
+// the filter, and the assignment never sees it: every point of the tile goes to c1, so
+// the tile adds its point count (or weight sum) to block c1, and its stored ids are
+// written only when its marker (every stored 16-bit id equal to it) does not already
+// name c1.  One thread; returns the tile's points.
+__device__ __forceinline__ long long single_tile_finish(const Prob &p, int t, int c1, int marker) {
+    tile_weight_to(p, t, c1);
+    const long long i0 = (long long)t * kTile;
+    long long nv = p.n - i0;
+    nv = nv > kTile ? kTile : nv;
+    if (p.a16) {
+        if (marker == c1) return nv;
+        if (nv == kTile) {
+            const unsigned u = (unsigned)c1 | ((unsigned)c1 << 16);
+            uint4 *dst = reinterpret_cast<uint4 *>(p.A16 + i0);
+#pragma unroll 4
+            for (int q = 0; q < kTile / 8; ++q) dst[q] = make_uint4(u, u, u, u);
+        } else {
+            for (int q = 0; q < (int)nv; ++q) p.A16[i0 + q] = (unsigned short)c1;
+        }
+        reinterpret_cast<int *>(p.tiles)[8 * t + 7] = c1;
+    } else if (nv == kTile) {
+        int4 *dst = reinterpret_cast<int4 *>(p.A + i0);
+#pragma unroll 4
+        for (int q = 0; q < kTile / 4; ++q) dst[q] = make_int4(c1, c1, c1, c1);
+    } else {
+        for (int q = 0; q < (int)nv; ++q) p.A[i0 + q] = c1;
+    }
+    return nv;
+}
+
 // One warp per supertile, with no block-wide synchronisation: level 1; then, for a
 // list of at most kLaneMax centers, level 2 with one lane per tile (lanes 0-15), each
 // walking the list.  A longer list is handed to filter_big_kernel.
@@ -719,6 +769,9 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     }
     // level 2, short list: lane = tile
     unsigned long long cs = 0;  // candidates x points of the lane's tile
+    long long ev = 0;           // points of a tile finished here (one candidate)
+    int cnt_t = 0;              // the lane's candidate count
+    bool multi = false;         // the lane's tile goes to the assignment's work list
     const int *list = s_list[warp];
     const float4 *lcd = s_lcd[warp];
     if (has_tile) {
@@ -732,7 +785,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
             tt = fminf(tt, ub);
         }
         const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
-        int cnt = 0;
+        int cnt = 0, c1 = -1;
         float gkept = 0.0f, lamT = lamS;
         float4 *rec = p.trec + (size_t)t * kRecF4;
         for (int i = 0; i < L; ++i) {
@@ -748,17 +801,47 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
                 rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
                 rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
                 gkept = fmaxf(gkept, ch.w);
+                if (cnt == 0) c1 = c;
                 ++cnt;
             }
         }
         cs = finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
+        cnt_t = cnt;
+        if (!p.bounds && cnt == 1)
+            ev = single_tile_finish(p, t, c1, __float_as_int(tb1.w));
+        else
+            multi = cnt <= kCoopCands;  // L <= kLaneMax <= kCap: never an overflowed list
+    }
+    // the work list: one atomic per supertile
+    const unsigned mb = __ballot_sync(0xffffffffu, multi);
+    if (mb) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctl->multi_cnt, (unsigned)__popc(mb));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (multi) p.mlist[base + __popc(mb & ((1u << lane) - 1u))] = make_int2(t, cnt_t);
     }
     // the statistics: one atomic per supertile (one per tile contended at 1e9 points)
-    for (int off = 16; off; off >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, off);
-    if (lane == 0) add_candidates(p, s, cs);
+    for (int off = 16; off; off >>= 1) {
+        cs += __shfl_xor_sync(0xffffffffu, cs, off);
+        ev += __shfl_xor_sync(0xffffffffu, ev, off);
+    }
+    if (lane == 0) {
+        add_candidates(p, s, cs);
+        if (ev) atomicAdd(&p.ctl->evaluated, (unsigned long long)ev);
+    }
 }
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
 static_assert(kMaxSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
+
+// A tile of filter_big_kernel once its record is written (lane 0): finished here with one
+// candidate c1, or put on the assignment's work list.
+__device__ __forceinline__ void big_tile_done(const Prob &p, int t, int cnt, int c1, int marker) {
+    if (!p.bounds && cnt == 1) {
+        atomicAdd(&p.ctl->evaluated, (unsigned long long)single_tile_finish(p, t, c1, marker));
+    } else if (cnt <= kCoopCands) {
+        p.mlist[atomicAdd(&p.ctl->multi_cnt, 1u)] = make_int2(t, cnt);
+    }
+}
 
 // Level 2 of the supertiles with long lists: one warp per tile, lanes over chunks
 // of 32 candidates (tau pass, then the ascending keep pass with ballots).  A split
@@ -810,7 +893,10 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
                 for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
             }
             __syncwarp();
-            if (lane == 0) add_candidates(p, t, finish_tile(p, t, L, gkept, gall, tb0, lamT, tb1.w));
+            if (lane == 0) {
+                add_candidates(p, t, finish_tile(p, t, L, gkept, gall, tb0, lamT, tb1.w));
+                big_tile_done(p, t, L, L >= 1 && L <= kCap ? s_tl[warp][0] : -1, __float_as_int(tb1.w));
+            }
             continue;
         }
         const float gall = __int_as_float(p.bigs[4 * slot + 2]);
@@ -838,7 +924,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
         }
         for (int off = 16; off; off >>= 1) tt = fminf(tt, __shfl_xor_sync(0xffffffffu, tt, off));
         const float tauT = __fmul_ru(tt, 1.0f + 64.0f * kU);
-        int cnt = 0;
+        int cnt = 0, c1 = -1;
         float gkept = 0.0f;
         float4 *rec = p.trec + (size_t)t * kRecF4;
 #pragma unroll 2
@@ -864,13 +950,18 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
                 rec[3 + 2 * pos] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
             }
             if (keep) gkept = fmaxf(gkept, ch.w);
+            if (keep && pos == 0) c1 = c;
             cnt += __popc(bal);
         }
+        c1 = __reduce_max_sync(0xffffffffu, c1);  // the first kept center
         for (int off = 16; off; off >>= 1) {
             gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
             lamT = fminf(lamT, __shfl_xor_sync(0xffffffffu, lamT, off));
         }
-        if (lane == 0) add_candidates(p, t, finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w));
+        if (lane == 0) {
+            add_candidates(p, t, finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w));
+            big_tile_done(p, t, cnt, c1, __float_as_int(tb1.w));
+        }
     }
 }
 
@@ -995,18 +1086,6 @@ __device__ __forceinline__ bool store_blocks_tile(const Prob &p, int t, long lon
     const int now = uni ? b0 : -1;
     if ((threadIdx.x & 31) == 0 && now != prev) reinterpret_cast<int *>(p.tiles)[8 * t + 7] = now;
     return uni;
-}
-
-// Block weights of a tile all of whose points went to block b (called by lane 0): the
-// tile's point count, or its weight sum formed at the bootstrap with the same fixed-point
-// conversion of every weight as tile_histogram uses.
-__device__ __forceinline__ void tile_weight_to(const Prob &p, int t, int b) {
-    if (p.weighted) {
-        red_add_u64(&p.Sfix[2 * b], p.tws[t]);
-    } else {
-        const long long nv = p.n - (long long)t * kTile;
-        atomicAdd(&p.Sfix[2 * b], (unsigned long long)(nv < kTile ? nv : kTile));
-    }
 }
 
 // Block weights of one tile's assignment: runs inside the lane, then a segmented
@@ -1372,46 +1451,36 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             }
         }
     };
-    // Tiles come from kQueues interleaved queues: queue q serves positions q, q + kQueues,
-    // ... A warp claims qch positions at a time (one atomic per chunk) and resolves them
-    // in parallel: lane j of a half of the ring below reads the record header (candidate
-    // count, stored-id marker) and first candidate of one position's tile.  The ring has
-    // two halves of qch entries; a half is claimed and resolved again as soon as its last
-    // entry is taken, so its loads have the other half's tiles of work to arrive.  A
-    // warp's positions increase, so the first position past the end means that the warp
-    // is done.
-    // A tile with more than kFastCands candidates was taken by a cooperative CTA above
-    // and is passed over.  A tile with a single candidate needs neither its coordinates
-    // nor its record: the filter has proven that every point of the tile goes to that
-    // center (without per-point bounds to keep up), so it is finished from the ring's
-    // registers.  The other tiles go through the warp's two shared-memory stages in
-    // order of arrival: a tile's copy is issued when it is taken from the ring, and it is
-    // evaluated when a later tile needs its stage (or at the end), so the one-candidate
-    // tiles in between cover the copy's latency.
+    // The tiles come from the filter's work list: (tile, candidate count) of every tile
+    // with 2 to kFastCands candidates (with per-point bounds, 1 to kFastCands); a tile
+    // with one candidate was finished by the filter, a longer list goes to the
+    // cooperative CTAs above.  The list is served as kQueues interleaved queues: queue q
+    // serves positions q, q + kQueues, ...  A warp claims qch positions at a time (one
+    // atomic per chunk) and reads them in parallel, lane j of a half of the ring below
+    // one position.  The ring has two halves of qch entries; a half is claimed and read
+    // again as soon as its last entry is taken, so its loads have the other half's tiles
+    // of work to arrive.  A warp's positions increase, so the first position past the end
+    // means that the warp is done.  The tiles go through the warp's two shared-memory
+    // stages in order of arrival: a tile's copy is issued when it is taken from the ring
+    // and it is evaluated when a later tile needs its stage (or at the end).
     const int qi = (blockIdx.x * kAWarps + w) & (kQueues - 1);
     unsigned *qctr = &p.ctl->tile_q[qi * kQueueStride];
-    // Positions map to tiles through the permutation t = pos * qmul mod ntiles (qmul
-    // coprime to ntiles, near 0.618 ntiles): the warps working at the same time then
-    // hold tiles from all over the curve, whose blocks differ, instead of neighbouring
-    // tiles that all add to the weights of the same few blocks.
-    auto resolve = [&](unsigned m, int &tile, int &cnt, int &c1, int &pv) {
+    const long long mcnt = (long long)p.ctl->multi_cnt;
+    auto resolve = [&](unsigned m, int &tile, int &cnt) {
         const long long pos = (long long)qi + (long long)kQueues * m;
-        if (pos >= p.ntiles) {
+        if (pos >= mcnt) {
             tile = p.ntiles;
             cnt = 0;
             return;
         }
-        tile = tile_of(p, pos);
-        const float4 h = __ldcg(&p.trec[(size_t)tile * kRecF4]);
-        cnt = __float_as_int(h.x);
-        pv = __float_as_int(h.w);
-        c1 = __float_as_int(__ldcg(&p.trec[(size_t)tile * kRecF4 + 3].x));
+        const int2 e = __ldcg(&p.mlist[pos]);
+        tile = e.x;
+        cnt = e.y;
     };
-    // A chunk is at most 8 positions and at most 1/16 of a warp's share of the tiles, so
-    // that a warp with few tiles (n of a few million) does not hold work the others could
-    // take.
-    const int qch = (int)min(8LL, max(1LL, (long long)p.ntiles / ((long long)gridDim.x * kAWarps * 16)));
-    int r_tile = p.ntiles, r_cnt = 0, r_c1 = 0, r_pv = -1;  // this lane's ring entry
+    // A chunk is at most 8 positions and at most 1/16 of a warp's share of the list, so
+    // that a warp with few tiles does not hold work the others could take.
+    const int qch = (int)min(8LL, max(1LL, mcnt / ((long long)gridDim.x * kAWarps * 16)));
+    int r_tile = p.ntiles, r_cnt = 0;  // this lane's ring entry
     // chunk bases are claimed one chunk ahead of their use (lane 0), so that the atomic's
     // latency is not waited for
     unsigned nb = lane == 0 ? atomicAdd(qctr, (unsigned)qch) : 0u;
@@ -1419,7 +1488,7 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         const unsigned base = __shfl_sync(0xffffffffu, nb, 0);
         if (lane == 0) nb = atomicAdd(qctr, (unsigned)qch);
         const int j = lane - h * qch;
-        if (j >= 0 && j < qch) resolve(base + (unsigned)j, r_tile, r_cnt, r_c1, r_pv);
+        if (j >= 0 && j < qch) resolve(base + (unsigned)j, r_tile, r_cnt);
     };
     resolve_half(0);
     resolve_half(1);
@@ -1827,56 +1896,49 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         }
         return true;
     };
+    // One call site of process (the evaluation is long: a second inlined copy would only
+    // crowd the instruction cache).  Until the ring runs out, a tile goes into a free
+    // stage, or the older busy stage is evaluated and then takes it; after that the busy
+    // stages are evaluated in order of their copies.
+    bool done = false;
     for (;;) {
-        // the next ring entry (every lane holds the same warp-wide state)
-        const int tile = __shfl_sync(0xffffffffu, r_tile, cc);
-        const int cnt = __shfl_sync(0xffffffffu, r_cnt, cc);
-        const int c1 = __shfl_sync(0xffffffffu, r_c1, cc);
-        const int pv = __shfl_sync(0xffffffffu, r_pv, cc);
-        ++cc;
-        if (cc == qch) {
-            resolve_half(0);
-        } else if (cc == 2 * qch) {
-            resolve_half(1);
-            cc = 0;
+        int tile = -1, cnt = 0;
+        if (!done) {
+            // the next ring entry (every lane holds the same warp-wide state)
+            tile = __shfl_sync(0xffffffffu, r_tile, cc);
+            cnt = __shfl_sync(0xffffffffu, r_cnt, cc);
+            ++cc;
+            if (cc == qch) {
+                resolve_half(0);
+            } else if (cc == 2 * qch) {
+                resolve_half(1);
+                cc = 0;
+            }
+            if (tile >= p.ntiles) done = true;
+            else if (cnt < 0 || cnt > kFastCands) continue;  // never on the list: cooperative tiles
         }
-        if (tile >= p.ntiles) break;
-        if (cnt < 0 || cnt > kFastCands) continue;  // taken by a cooperative CTA
-        if (!BOUNDS && cnt == 1) {  // every point of the tile goes to center c1
-            const long long t0 = (long long)tile * kTile, i0 = t0 + lane * 8;
-            const long long nv = p.n - i0;
-            const int nval = nv <= 0 ? 0 : (nv >= 8 ? 8 : (int)nv);
-            nevl += (unsigned long long)(p.n - t0 < kTile ? p.n - t0 : kTile);
-            int best[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) best[q] = c1;
-            store_blocks_tile(p, tile, i0, nval, best, pv);
-            if (lane == 0) tile_weight_to(p, tile, c1);
-            continue;
-        }
-        if (s_t0 >= 0 && s_t1 >= 0) {
-            // both stages busy: evaluate the older one and copy this tile into it
-            const int b = s_old;
+        int b;
+        if (!done) {
+            if (s_t0 < 0 || s_t1 < 0) {  // a free stage: copy the tile in
+                const int fb = s_t0 < 0 ? 0 : 1;
+                if (stile(fb ^ 1) < 0) s_old = fb;  // the only busy stage is the older one
+                issue(tile, cnt, fb);
+                set_stile(fb, tile);
+                continue;
+            }
+            b = s_old;  // both busy: evaluate the older one and copy this tile into it
             pend = tile;
             pend_cnt = cnt;
-            if (!process(b)) return;
+        } else {
+            if (stile(s_old) >= 0) b = s_old;
+            else if (stile(s_old ^ 1) >= 0) b = s_old ^ 1;
+            else break;
             pend = -1;
-            set_stile(b, tile);
-            s_old = b ^ 1;
-            continue;
         }
-        const int b = s_t0 < 0 ? 0 : 1;
-        if (stile(b ^ 1) < 0) s_old = b;  // the only busy stage is the older one
-        issue(tile, cnt, b);
-        set_stile(b, tile);
-    }
-    // the tiles still in the stages, in order of their copies
-    if (stile(s_old) >= 0) {
-        if (!process(s_old)) return;
-        set_stile(s_old, -1);
-    }
-    if (stile(s_old ^ 1) >= 0) {
-        if (!process(s_old ^ 1)) return;
+        if (!process(b)) return;
+        set_stile(b, pend);  // the tile copied into it, or -1 once the ring ran out
+        s_old = b ^ 1;
+        pend = -1;
     }
     if (F64MODE) {
         for (int off = 16; off; off >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, off);
@@ -1998,6 +2060,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         ctl->maxg_key = 0ull;
         ctl->coop_cnt = 0u;  // the next filter rebuilds the cooperative list
         ctl->big_cnt = 0u;
+        ctl->multi_cnt = 0u;  // and the work list
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
         if (mode == 2) return;
