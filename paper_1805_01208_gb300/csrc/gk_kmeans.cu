@@ -689,11 +689,18 @@ __device__ __forceinline__ void tile_weight_to(const Prob &p, int t, int b) {
 
 // A tile whose only candidate is c1 (without per-point bounds to keep up) is finished by
 // the filter, and the assignment never sees it: every point of the tile goes to c1, so
-// the tile adds its point count (or weight sum) to block c1, and its stored ids are
-// written only when its marker (every stored 16-bit id equal to it) does not already
-// name c1.  One thread; returns the tile's points.
-__device__ __forceinline__ long long single_tile_finish(const Prob &p, int t, int c1, int marker) {
-    tile_weight_to(p, t, c1);
+// its stored ids are written only when its marker (every stored 16-bit id equal to it)
+// does not already name c1.  The tile's point count (or weight sum) goes to block c1:
+// here when add_weight, else the caller adds it (single_weight).  One thread; returns
+// the tile's points.
+__device__ __forceinline__ unsigned long long single_weight(const Prob &p, int t) {
+    if (p.weighted) return p.tws[t];
+    const long long nv = p.n - (long long)t * kTile;
+    return (unsigned long long)(nv < kTile ? nv : kTile);
+}
+__device__ __forceinline__ long long single_tile_finish(const Prob &p, int t, int c1, int marker,
+                                                        bool add_weight = true) {
+    if (add_weight) tile_weight_to(p, t, c1);
     const long long i0 = (long long)t * kTile;
     long long nv = p.n - i0;
     nv = nv > kTile ? kTile : nv;
@@ -770,6 +777,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
     // level 2, short list: lane = tile
     unsigned long long cs = 0;  // candidates x points of the lane's tile
     long long ev = 0;           // points of a tile finished here (one candidate)
+    int sb = -1;                // its block
     int cnt_t = 0;              // the lane's candidate count
     bool multi = false;         // the lane's tile goes to the assignment's work list
     const int *list = s_list[warp];
@@ -807,10 +815,36 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         }
         cs = finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
         cnt_t = cnt;
-        if (!p.bounds && cnt == 1)
-            ev = single_tile_finish(p, t, c1, __float_as_int(tb1.w));
-        else
+        if (!p.bounds && cnt == 1) {
+            ev = single_tile_finish(p, t, c1, __float_as_int(tb1.w), false);
+            sb = c1;
+        } else {
             multi = cnt <= kCoopCands;  // L <= kLaneMax <= kCap: never an overflowed list
+        }
+    }
+    // block weights of the one-candidate tiles: neighbouring tiles mostly share the block,
+    // so runs of equal blocks over the lanes are summed first (low and high 32-bit parts
+    // apart, the carry-free form), then one atomic per run
+    {
+        const unsigned long long wv = sb >= 0 ? single_weight(p, t) : 0ull;
+        unsigned long long wlo = wv & 0xffffffffull, whi = wv >> 32;
+        const int prev = __shfl_up_sync(0xffffffffu, sb, 1);
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || sb != prev);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long a = __shfl_up_sync(0xffffffffu, wlo, off);
+            const unsigned long long b = __shfl_up_sync(0xffffffffu, whi, off);
+            if (lane - off >= start) {
+                wlo += a;
+                whi += b;
+            }
+        }
+        const bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        if (end && sb >= 0) {
+            atomicAdd(&p.Sfix[2 * sb], wlo);
+            if (whi) atomicAdd(&p.Sfix[2 * sb + 1], whi);
+        }
     }
     // the work list: one atomic per supertile
     const unsigned mb = __ballot_sync(0xffffffffu, multi);
@@ -2182,13 +2216,28 @@ __device__ __forceinline__ long long cent_fix(const Prob &p, T w, T x) {
     return p.weighted ? fix_prod_f32((float)w, (float)x, p.Fx) : fix_f32((float)x, p.Fx);
 }
 
+// An empty asm that the compiler must assume changes the values: computations that
+// depend on them are not hoisted out of the loop that calls it.
+template <typename T, int D>
+__device__ __forceinline__ void opaque_values(T (&v)[D][8]) {
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if constexpr (sizeof(T) == 8)
+                asm volatile("" : "+d"(v[j][q]));
+            else
+                asm volatile("" : "+f"(v[j][q]));
+        }
+}
+
 // One tile (called by the whole warp): lane l takes points 8l..8l+7, loaded with vector
-// loads (ids, weights, one coordinate plane at a time) so that each group of loads is in
-// flight together.  A tile all of whose points lie in one block (most tiles: a block of
-// curve-sorted points spans many tiles) takes one warp reduction and one set of atomics.
-// Otherwise the runs of equal block ids inside each lane are added directly, except the
-// lane's last run, which goes through a segmented reduction over the lanes (runs continue
-// across lanes).  Sums are 128-bit fixed point, extremes ordered keys.
+// loads (ids, weights and every coordinate plane, one round trip).  The tile's points are
+// then taken block by block: the block of the first point still open, every lane's points
+// of that block summed (fixed point) with their extreme keys, a warp reduction and one
+// set of atomics per block.  A tile holds few distinct blocks (one for most, two or three
+// at a boundary, however often the curve crosses it), so this takes a few rounds and
+// few atomics; a sum over one block of the tile is below 2^62 (256 values below 2^54).
 template <typename T, int D>
 __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     const int lane = threadIdx.x & 31;
@@ -2199,29 +2248,42 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     load_ids8(p, i0, nval, ids);
     T wv[8];
     if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
-    T xv[D][8];  // every plane, loaded with the ids (one round trip)
+    T xv[D][8];
 #pragma unroll
     for (int j = 0; j < D; ++j) load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv[j]);
-    const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
-    bool same = true, bad = false;
-    int last = -1;  // block of the lane's last run
+    unsigned rem = 0;  // the lane's points not yet added
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         if (q < nval) {
-            same &= ids[q] == b0;
-            if ((unsigned)ids[q] >= (unsigned)p.k) bad = true;
-            else last = ids[q];
+            if ((unsigned)ids[q] < (unsigned)p.k) rem |= 1u << q;
+            else bad = true;
         }
     }
     if (bad) atomicOr(&p.ctl->bad_block, 1);
-    if (__all_sync(0xffffffffu, same) && (unsigned)b0 < (unsigned)p.k) {
+    for (;;) {
+        const unsigned open = __ballot_sync(0xffffffffu, rem != 0u);
+        if (!open) break;
+        int first = -1;
+#pragma unroll
+        for (int q = 7; q >= 0; --q)
+            if ((rem >> q) & 1u) first = ids[q];
+        const int b = __shfl_sync(0xffffffffu, first, __ffs(open) - 1);
+        // the conversions below are redone each round (a few ALU operations) instead of
+        // being kept for every point and plane, which would triple the registers
+        opaque_values<T, D>(xv);
+        unsigned m = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (((rem >> q) & 1u) && ids[q] == b) m |= 1u << q;
+        rem &= ~m;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             long long sum = 0;
             unsigned long long kmin = ~0ull, kmax = 0ull;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                if (q < nval) {
+                if ((m >> q) & 1u) {
                     sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
                     const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
                     kmin = kk < kmin ? kk : kmin;
@@ -2230,67 +2292,16 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
             }
             for (int off = 16; off; off >>= 1) {
                 sum += __shfl_xor_sync(0xffffffffu, sum, off);
-                const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
-                const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
-                kmin = a < kmin ? a : kmin;
-                kmax = b > kmax ? b : kmax;
+                const unsigned long long x0 = __shfl_xor_sync(0xffffffffu, kmin, off);
+                const unsigned long long x1 = __shfl_xor_sync(0xffffffffu, kmax, off);
+                kmin = x0 < kmin ? x0 : kmin;
+                kmax = x1 > kmax ? x1 : kmax;
             }
             if (lane == 0) {
-                red_add_s64(&p.SXfix[2 * (b0 * D + j)], sum);
-                atomicMin(&p.BBlo[b0 * D + j], kmin);
-                atomicMax(&p.BBhi[b0 * D + j], kmax);
+                red_add_s64(&p.SXfix[2 * (b * D + j)], sum);
+                atomicMin(&p.BBlo[b * D + j], kmin);
+                atomicMax(&p.BBhi[b * D + j], kmax);
             }
-        }
-        return;
-    }
-    // segments of the lanes' last runs (the same for every plane)
-    const int prev = __shfl_up_sync(0xffffffffu, last, 1);
-    const bool head = lane == 0 || last != prev;
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-    const bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        int cur = -1;
-        long long sum = 0;
-        unsigned long long kmin = ~0ull, kmax = 0ull;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q < nval && (unsigned)ids[q] < (unsigned)p.k) {
-                if (ids[q] != cur) {
-                    if (cur >= 0) {  // a run that ends inside the lane
-                        red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
-                        atomicMin(&p.BBlo[cur * D + j], kmin);
-                        atomicMax(&p.BBhi[cur * D + j], kmax);
-                    }
-                    cur = ids[q];
-                    sum = 0;
-                    kmin = ~0ull;
-                    kmax = 0ull;
-                }
-                sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
-                const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
-                kmin = kk < kmin ? kk : kmin;
-                kmax = kk > kmax ? kk : kmax;
-            }
-        }
-        // the lanes' last runs: a run covers at most 256 values below 2^54, so 64 bits
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const bool take = lane - off >= start;
-            const long long s2 = __shfl_up_sync(0xffffffffu, sum, off);
-            const unsigned long long a = __shfl_up_sync(0xffffffffu, kmin, off);
-            const unsigned long long b = __shfl_up_sync(0xffffffffu, kmax, off);
-            if (take) {
-                sum += s2;
-                kmin = a < kmin ? a : kmin;
-                kmax = b > kmax ? b : kmax;
-            }
-        }
-        if (end && cur >= 0) {
-            red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
-            atomicMin(&p.BBlo[cur * D + j], kmin);
-            atomicMax(&p.BBhi[cur * D + j], kmax);
         }
     }
 }
