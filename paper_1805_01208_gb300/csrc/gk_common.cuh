@@ -96,6 +96,7 @@ struct Ctl {
     unsigned int coop_cnt;                  // tiles in the cooperative list (reset before each filter)
     unsigned int big_cnt;                   // supertiles with long candidate lists (same)
     unsigned int multi_cnt;                 // tiles in the assignment's work list (same)
+    unsigned int jump_cnt;                  // tiles for a level 1 on their own box (same)
     unsigned int mixed_cnt;                 // tiles the movement takes point by point (reset
                                             //   by the movement's finalize kernel)
     int nonempty;                           // non-empty blocks of the last movement
@@ -163,6 +164,8 @@ struct Prob {
     int *coop;                  // tiles of the cooperative path (ntiles entries)
     int2 *mlist;                // the assignment's work list: (tile, candidate count) of
                                 // every tile it evaluates per warp (ntiles entries)
+    int *tlist;                 // tiles whose record comes from a level 1 on their own box
+                                // (ntiles entries)
     int *bigs;                  // per long-list supertile: index, list length, largest g, smallest
                                 // dropped lower bound (bits)
     int *blists;                // their candidate lists, kWarpList entries each

@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(kKThreads) init_a_kernel(Prob p, cudaGraphCond
         ctl->coop_cnt = 0u;
         ctl->big_cnt = 0u;
         ctl->multi_cnt = 0u;
+        ctl->jump_cnt = 0u;
         ctl->phase_pass = 0;
         ctl->min_lr_key = 0xffffffffu;
         ctl->max_lr_key = 0u;
@@ -796,6 +797,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
         int cnt = 0, c1 = -1;
         float gkept = 0.0f, lamT = lamS;
         float4 *rec = p.trec + (size_t)t * kRecF4;
+        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f);  // the first candidate's entry, written
+                                                       // once the tile is known to need it
         for (int i = 0; i < L; ++i) {
             const int c = list[i];
             const float4 ch = lcd[2 * i], cl = lcd[2 * i + 1];
@@ -806,19 +809,29 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
                 const float q0 = (ch.x - o[0]) + cl.x;
                 const float q1 = (ch.y - o[1]) + cl.y;
                 const float q2 = D == 3 ? (ch.z - o[2]) + cl.z : 0.0f;
-                rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
-                rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                if (cnt == 0) {
+                    e0 = make_float4(q0, q1, q2, ch.w);
+                    c1 = c;
+                } else {
+                    rec[2 + 2 * cnt] = make_float4(q0, q1, q2, ch.w);
+                    rec[3 + 2 * cnt] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                }
                 gkept = fmaxf(gkept, ch.w);
-                if (cnt == 0) c1 = c;
                 ++cnt;
             }
         }
-        cs = finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
         cnt_t = cnt;
         if (!p.bounds && cnt == 1) {
-            ev = single_tile_finish(p, t, c1, __float_as_int(tb1.w), false);
+            // finished here: the record is never read, so it is not written
+            cs = (unsigned long long)single_tile_finish(p, t, c1, __float_as_int(tb1.w), false);
+            ev = (long long)cs;
             sb = c1;
         } else {
+            if (cnt > 0) {
+                rec[2] = e0;
+                rec[3] = make_float4(__int_as_float(c1), 0.0f, 0.0f, 0.0f);
+            }
+            cs = finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w);
             multi = cnt <= kCoopCands;  // L <= kLaneMax <= kCap: never an overflowed list
         }
     }
@@ -890,7 +903,6 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
     __shared__ float4 s_lcd[kFilterWarps][2 * kLaneMax];
     __shared__ int s_grp[kFilterWarps][kWarpGroups];
     __shared__ int s_sg[kFilterWarps][kWarpSG];
-    __shared__ int s_tl[kFilterWarps][kCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int total = (int)p.ctl->big_cnt * p.stiles;
@@ -904,33 +916,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
         const int s = p.bigs[4 * slot], Lr = p.bigs[4 * slot + 1];
         const int t = s * p.stiles + item % p.stiles;
         if (t >= p.ntiles) continue;
-        if (Lr == kSplit) {
-            float gall, lamT;
-            int L = supertile_list<D>(p, p.tiles + 2 * t, cd, gd, s_list[warp], s_lcd[warp], s_grp[warp],
-                                      s_sg[warp], s_tl[warp], gall, lamT, 0, kCap);
-            const float4 tb0 = p.tiles[2 * t], tb1 = p.tiles[2 * t + 1];
-            float gkept = 0.0f;
-            if (L <= kCap) {
-                float4 *rec = p.trec + (size_t)t * kRecF4;
-                const bool inl = L <= kLaneMax;  // the level copied the list's center data
-                for (int i = lane; i < L; i += 32) {
-                    const int c = s_tl[warp][i];
-                    const float4 ch = inl ? s_lcd[warp][2 * i] : __ldg(&cd[2 * c]);
-                    const float4 cl = inl ? s_lcd[warp][2 * i + 1] : __ldg(&cd[2 * c + 1]);
-                    const float q0 = (ch.x - tb0.x) + cl.x;
-                    const float q1 = (ch.y - tb0.y) + cl.y;
-                    const float q2 = D == 3 ? (ch.z - tb0.z) + cl.z : 0.0f;
-                    rec[2 + 2 * i] = make_float4(q0, q1, q2, ch.w);
-                    rec[3 + 2 * i] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
-                    gkept = fmaxf(gkept, ch.w);
-                }
-                for (int off = 16; off; off >>= 1) gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
-            }
-            __syncwarp();
-            if (lane == 0) {
-                add_candidates(p, t, finish_tile(p, t, L, gkept, gall, tb0, lamT, tb1.w));
-                big_tile_done(p, t, L, L >= 1 && L <= kCap ? s_tl[warp][0] : -1, __float_as_int(tb1.w));
-            }
+        if (Lr == kSplit) {  // level 1 on the tile's own box, in filter_tile_kernel
+            if (lane == 0) p.tlist[atomicAdd(&p.ctl->jump_cnt, 1u)] = t;
             continue;
         }
         const float gall = __int_as_float(p.bigs[4 * slot + 2]);
@@ -988,6 +975,10 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             cnt += __popc(bal);
         }
         c1 = __reduce_max_sync(0xffffffffu, c1);  // the first kept center
+        if (cnt > kCap) {  // the list does not fit: the tile's own level 1 (rewrites the record)
+            if (lane == 0) p.tlist[atomicAdd(&p.ctl->jump_cnt, 1u)] = t;
+            continue;
+        }
         for (int off = 16; off; off >>= 1) {
             gkept = fmaxf(gkept, __shfl_xor_sync(0xffffffffu, gkept, off));
             lamT = fminf(lamT, __shfl_xor_sync(0xffffffffu, lamT, off));
@@ -996,6 +987,165 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             add_candidates(p, t, finish_tile(p, t, cnt, gkept, gall, tb0, lamT, tb1.w));
             big_tile_done(p, t, cnt, c1, __float_as_int(tb1.w));
         }
+    }
+}
+
+// Level 1 on a tile's own box, by a whole CTA per tile, for the tiles filter_big_kernel
+// listed: the tiles of a split supertile and the tiles whose list from their supertile's
+// list does not fit the record.  At 1e9 points these are the tiles of the sparse
+// background next to a dense spot: the nearest centers are far, so hundreds of the spot's
+// small groups pass the group test, yet the final list fits the record.  One warp sweeping
+// them took 300-600 us; handing such a tile every center made the assignment's
+// cooperative CTAs pay 0.29 ms per pass.  Here the eight warps share the sweeps:
+// 1. every group's bounds (threads over groups): tau_G = the smallest group upper bound
+//    (each group's bounds every member's, so tau_G >= tau), kept: the groups whose lower
+//    bound passes tau_G, in ascending order;
+// 2. tau = the smallest upper bound over the kept groups' centers (warps over groups);
+// 3. the kept centers (lower bound <= tau): each warp a contiguous range of the kept
+//    groups, then the warps' lists in order: the ascending list.
+// The center attaining tau lies in a kept group (its group's lower bound <= its own <=
+// tau <= tau_G), as does every center that passes tau, so the list is the one level 1
+// over all centers gives.  More than kTileGroups kept groups, or more than kCap
+// candidates: every center (an overflowed record).
+constexpr int kTileGroups = 2048;
+template <int D>
+__global__ void __launch_bounds__(kFilterThreads) filter_tile_kernel(Prob p) {
+    count_launch(p.ctl);
+    __shared__ int s_grp[kTileGroups];
+    __shared__ int s_cent[kFilterWarps][kCap];
+    __shared__ int s_cnt[kFilterWarps];
+    __shared__ float s_red[kFilterWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int total = (int)p.ctl->jump_cnt;
+    const int sel = p.ctl->isel;
+    const float4 *cd = p.cdata2 + (size_t)sel * 2 * p.k;
+    const float4 *gd = p.gdata2 + (size_t)sel * 2 * p.ngroups;
+    const float infl = 4.0f * kU * p.R;
+    const int ng = p.ngroups;
+    // CTA-wide minimum (op 0) or maximum (op 1) of one value per thread
+    auto cta_red = [&](float v, int op) -> float {
+        for (int off = 16; off; off >>= 1) {
+            const float o = __shfl_xor_sync(0xffffffffu, v, off);
+            v = op ? fmaxf(v, o) : fminf(v, o);
+        }
+        __syncthreads();
+        if (lane == 0) s_red[warp] = v;
+        __syncthreads();
+        float r = s_red[0];
+        for (int w = 1; w < kFilterWarps; ++w) r = op ? fmaxf(r, s_red[w]) : fminf(r, s_red[w]);
+        return r;
+    };
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int t = p.tlist[item];
+        const float4 tb0 = p.tiles[2 * t], tb1 = p.tiles[2 * t + 1];
+        const float so[3] = {tb0.x, tb0.y, tb0.z};
+        const float sh[3] = {__fadd_ru(tb1.x, infl), __fadd_ru(tb1.y, infl), __fadd_ru(tb1.z, infl)};
+        // 1. groups
+        float tg = INFINITY, ga = 0.0f;
+        for (int gi = tid; gi < ng; gi += kFilterThreads) {
+            float lb, ub;
+            const float4 gm = __ldg(&gd[2 * gi]), gh = __ldg(&gd[2 * gi + 1]);
+            group_bounds<D>(gm, gh, so, sh, lb, ub);
+            tg = fminf(tg, ub);
+            ga = fmaxf(ga, gh.w);
+        }
+        const float gall = cta_red(ga, 1);
+        const float tauG = __fmul_ru(cta_red(tg, 0), 1.0f + 256.0f * kU);
+        float lam = INFINITY;
+        int ngk = 0;
+        for (int base = 0; base < ng; base += kFilterThreads) {  // ascending, a CTA round at a time
+            const int gi = base + tid;
+            bool keep = false;
+            if (gi < ng) {
+                float lb, ub;
+                group_bounds<D>(__ldg(&gd[2 * gi]), __ldg(&gd[2 * gi + 1]), so, sh, lb, ub);
+                keep = !(lb > tauG);
+                if (!keep) lam = fminf(lam, lb);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) s_cnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = ngk;
+            for (int w = 0; w < warp; ++w) before += s_cnt[w];
+            int round = 0;
+            for (int w = 0; w < kFilterWarps; ++w) round += s_cnt[w];
+            const int pos = before + __popc(bal & lt);
+            if (keep && pos < kTileGroups) s_grp[pos] = gi;
+            ngk += round;
+            __syncthreads();
+        }
+        bool over = ngk > kTileGroups;
+        int L = 0;
+        if (!over) {
+            // 2. tau over the kept groups' centers (warp w: groups w, w + 8, ...)
+            float tc = INFINITY;
+            for (int i = warp; i < ngk; i += kFilterWarps) {
+                const int c = s_grp[i] * kGroup + lane;
+                if (c < p.k) {
+                    float lb, ub;
+                    box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+                    tc = fminf(tc, ub);
+                }
+            }
+            const float tauS = __fmul_ru(cta_red(tc, 0), 1.0f + 64.0f * kU);
+            // 3. the kept centers, warp w over kept groups [w ngk / 8, (w + 1) ngk / 8)
+            const int g0 = (int)((long long)warp * ngk / kFilterWarps);
+            const int g1 = (int)((long long)(warp + 1) * ngk / kFilterWarps);
+            int cw = 0;
+            for (int i = g0; i < g1; ++i) {
+                const int c = s_grp[i] * kGroup + lane;
+                bool keep = false;
+                if (c < p.k) {
+                    float lb, ub;
+                    box_bounds<D>(__ldg(&cd[2 * c]), __ldg(&cd[2 * c + 1]), so, sh, lb, ub);
+                    keep = !(lb > tauS);
+                    if (!keep) lam = fminf(lam, lb);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const int pos = cw + __popc(bal & lt);
+                if (keep && pos < kCap) s_cent[warp][pos] = c;
+                cw += __popc(bal);
+            }
+            if (lane == 0) s_cnt[warp] = cw;
+            __syncthreads();
+            int before = 0;
+            for (int w = 0; w < warp; ++w) before += s_cnt[w];
+            for (int w = 0; w < kFilterWarps; ++w) L += s_cnt[w];
+            over = L > kCap;
+            float gkept = 0.0f;
+            if (!over) {
+                float4 *rec = p.trec + (size_t)t * kRecF4;
+                for (int j = lane; j < cw; j += 32) {
+                    const int c = s_cent[warp][j];
+                    const float4 ch = __ldg(&cd[2 * c]), cl = __ldg(&cd[2 * c + 1]);
+                    const float q0 = (ch.x - so[0]) + cl.x;
+                    const float q1 = (ch.y - so[1]) + cl.y;
+                    const float q2 = D == 3 ? (ch.z - so[2]) + cl.z : 0.0f;
+                    rec[2 + 2 * (before + j)] = make_float4(q0, q1, q2, ch.w);
+                    rec[3 + 2 * (before + j)] = make_float4(__int_as_float(c), 0.0f, 0.0f, 0.0f);
+                    gkept = fmaxf(gkept, ch.w);
+                }
+            }
+            gkept = cta_red(gkept, 1);
+            lam = cta_red(lam, 0);
+            if (tid == 0) {
+                int c1 = -1;
+                for (int w = 0; w < kFilterWarps && c1 < 0; ++w)
+                    if (s_cnt[w] > 0) c1 = s_cent[w][0];
+                const int cnt = over ? p.k + kCap + 1 : L;  // more than kCap: overflowed
+                add_candidates(p, t, finish_tile(p, t, cnt, gkept, gall, tb0, lam, tb1.w));
+                big_tile_done(p, t, cnt, c1, __float_as_int(tb1.w));
+            }
+        } else {
+            lam = cta_red(lam, 0);
+            if (tid == 0) {
+                const int cnt = p.k + kCap + 1;
+                add_candidates(p, t, finish_tile(p, t, cnt, 0.0f, gall, tb0, lam, tb1.w));
+                big_tile_done(p, t, cnt, -1, __float_as_int(tb1.w));
+            }
+        }
+        __syncthreads();  // the shared lists are reused by the next tile
     }
 }
 
@@ -1423,9 +1573,11 @@ struct AStage<D, true> {
     unsigned char t1[kTile];
 };
 static_assert(sizeof(AStage<2, false>) * 2 * kAWarps >= 3 * kAWarps * kTile * 4,
-              "scratch of the cooperative tiles");
+              "scratch of the cooperative tiles (at least two stages per warp)");
+// shared-memory stages per warp: three (a tile evaluated while the next two copies are in
+// flight), two with the per-point bounds, whose stages are larger
 template <int D, bool BOUNDS>
-constexpr size_t assign_smem() { return sizeof(AStage<D, BOUNDS>) * 2 * kAWarps; }
+constexpr size_t assign_smem() { return sizeof(AStage<D, BOUNDS>) * (BOUNDS ? 2 : 3) * kAWarps; }
 
 // BOUNDS: per-point bounds across the passes of a phase (gk_options.bounds); without
 // them every point is evaluated every pass.
@@ -1434,12 +1586,12 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     count_launch(p.ctl);
     if (blockIdx.x == 0 && threadIdx.x == 0) p.ctl->t_assign0 = globaltimer_ns();
     extern __shared__ __align__(128) unsigned char a_dsm[];
-    AStage<D, BOUNDS> (*st)[2] = reinterpret_cast<AStage<D, BOUNDS> (*)[2]>(a_dsm);
-    __shared__ __align__(8) unsigned long long bar[kAWarps][2];
+    constexpr int kStg = BOUNDS ? 2 : 3;  // must match assign_smem
+    AStage<D, BOUNDS> (*st)[kStg] = reinterpret_cast<AStage<D, BOUNDS> (*)[kStg]>(a_dsm);
+    __shared__ __align__(8) unsigned long long bar[kAWarps][3];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) {
-        mbar_init(&bar[w][0], 1);
-        mbar_init(&bar[w][1], 1);
+        for (int i = 0; i < kStg; ++i) mbar_init(&bar[w][i], 1);
         fence_mbarrier_init();
     }
     __syncwarp();
@@ -1527,15 +1679,18 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     resolve_half(0);
     resolve_half(1);
     int cc = 0;  // ring entry taken next
-    int s_t0 = -1, s_t1 = -1;  // tile in each stage (-1: free)
-    auto stile = [&](int b) -> int { return b ? s_t1 : s_t0; };
+    // The stages form a ring used in order: the oldest busy stage is s_head, s_busy are
+    // in flight; a tile goes into stage (s_head + s_busy) mod kStg.
+    int s_t0 = -1, s_t1 = -1, s_t2 = -1;  // tile in each stage
+    auto stile = [&](int b) -> int { return b == 0 ? s_t0 : (b == 1 ? s_t1 : s_t2); };
     auto set_stile = [&](int b, int v) {
-        if (b) s_t1 = v;
-        else s_t0 = v;
+        if (b == 0) s_t0 = v;
+        else if (b == 1) s_t1 = v;
+        else s_t2 = v;
     };
-    int s_old = 0;             // of two busy stages, the one issued first
+    int s_head = 0, s_busy = 0;
     int pend = -1, pend_cnt = 0;  // the tile to copy into the stage being evaluated
-    unsigned ph0 = 0, ph1 = 0;
+    unsigned phs = 0;             // the stages' mbarrier phases (bit b)
     // once stage b has been read: its next tile's copy (lane 0)
     auto refill = [&](int b) {
         if (pend >= 0) issue(pend, pend_cnt, b);
@@ -1543,17 +1698,20 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
     // Evaluates the tile of stage b (waits for its copy); false when the copy timed out.
     auto process = [&](int b) -> bool {
         const int t = stile(b);
-        const unsigned phb = b ? ph1 : ph0;
+        const unsigned phb = (phs >> b) & 1u;
         bool ok = mbar_wait_bounded(&bar[w][b], phb);
         if (!__all_sync(0xffffffffu, ok)) {
             // A bulk copy did not arrive in time: record it and stop this warp after a
-            // bounded wait for the copies still in flight (this stage and the other).
+            // bounded wait for the copies still in flight (this stage and the others).
             if (lane == 0) atomicCAS(&p.ctl->status, kOk, kErrTimeout);
             mbar_wait_bounded(&bar[w][b], phb);
-            if (stile(b ^ 1) >= 0) mbar_wait_bounded(&bar[w][b ^ 1], b ? ph0 : ph1);
+            for (int i = 1; i < s_busy; ++i) {
+                const int o = (s_head + i) % kStg;
+                mbar_wait_bounded(&bar[w][o], (phs >> o) & 1u);
+            }
             return false;
         }
-        if (b) ph1 ^= 1u; else ph0 ^= 1u;
+        phs ^= 1u << b;
         AStage<D, BOUNDS> &S = st[w][b];
         const int ncand = __float_as_int(S.rec[0].x);  // 0 < ncand <= kFastCands
         const float gl = S.rec[0].y;    // largest g among the tile's candidates
@@ -1931,9 +2089,9 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
         return true;
     };
     // One call site of process (the evaluation is long: a second inlined copy would only
-    // crowd the instruction cache).  Until the ring runs out, a tile goes into a free
-    // stage, or the older busy stage is evaluated and then takes it; after that the busy
-    // stages are evaluated in order of their copies.
+    // crowd the instruction cache).  Until the ring of entries runs out, a tile goes into
+    // a free stage, or the oldest busy stage is evaluated and then takes it; after that the
+    // busy stages are evaluated in order of their copies.
     bool done = false;
     for (;;) {
         int tile = -1, cnt = 0;
@@ -1951,27 +2109,28 @@ __global__ void __launch_bounds__(kAWarps * 32, F64MODE ? kAMinBlocks64 : kAMinB
             if (tile >= p.ntiles) done = true;
             else if (cnt < 0 || cnt > kFastCands) continue;  // never on the list: cooperative tiles
         }
-        int b;
         if (!done) {
-            if (s_t0 < 0 || s_t1 < 0) {  // a free stage: copy the tile in
-                const int fb = s_t0 < 0 ? 0 : 1;
-                if (stile(fb ^ 1) < 0) s_old = fb;  // the only busy stage is the older one
+            if (s_busy < kStg) {  // a free stage: copy the tile in
+                const int fb = (s_head + s_busy) % kStg;
                 issue(tile, cnt, fb);
                 set_stile(fb, tile);
+                ++s_busy;
                 continue;
             }
-            b = s_old;  // both busy: evaluate the older one and copy this tile into it
-            pend = tile;
+            pend = tile;  // all busy: evaluate the oldest and copy this tile into it
             pend_cnt = cnt;
-        } else {
-            if (stile(s_old) >= 0) b = s_old;
-            else if (stile(s_old ^ 1) >= 0) b = s_old ^ 1;
-            else break;
-            pend = -1;
+        } else if (s_busy == 0) {
+            break;
         }
+        const int b = s_head;
         if (!process(b)) return;
-        set_stile(b, pend);  // the tile copied into it, or -1 once the ring ran out
-        s_old = b ^ 1;
+        if (pend >= 0) {
+            set_stile(b, pend);  // now the newest
+        } else {
+            set_stile(b, -1);
+            --s_busy;
+        }
+        s_head = (s_head + 1) % kStg;
         pend = -1;
     }
     if (F64MODE) {
@@ -2095,6 +2254,7 @@ __global__ void __launch_bounds__(kKThreads) balance_kernel(Prob p, int mode,
         ctl->coop_cnt = 0u;  // the next filter rebuilds the cooperative list
         ctl->big_cnt = 0u;
         ctl->multi_cnt = 0u;  // and the work list
+        ctl->jump_cnt = 0u;
         int bal = maxS <= ctl->bound;
         ctl->max_imbalance = maxS / ctl->ceil_avg - 1.0;
         if (mode == 2) return;
@@ -2216,28 +2376,15 @@ __device__ __forceinline__ long long cent_fix(const Prob &p, T w, T x) {
     return p.weighted ? fix_prod_f32((float)w, (float)x, p.Fx) : fix_f32((float)x, p.Fx);
 }
 
-// An empty asm that the compiler must assume changes the values: computations that
-// depend on them are not hoisted out of the loop that calls it.
-template <typename T, int D>
-__device__ __forceinline__ void opaque_values(T (&v)[D][8]) {
-#pragma unroll
-    for (int j = 0; j < D; ++j)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if constexpr (sizeof(T) == 8)
-                asm volatile("" : "+d"(v[j][q]));
-            else
-                asm volatile("" : "+f"(v[j][q]));
-        }
-}
-
 // One tile (called by the whole warp): lane l takes points 8l..8l+7, loaded with vector
-// loads (ids, weights and every coordinate plane, one round trip).  The tile's points are
-// then taken block by block: the block of the first point still open, every lane's points
-// of that block summed (fixed point) with their extreme keys, a warp reduction and one
-// set of atomics per block.  A tile holds few distinct blocks (one for most, two or three
-// at a boundary, however often the curve crosses it), so this takes a few rounds and
-// few atomics; a sum over one block of the tile is below 2^62 (256 values below 2^54).
+// loads (ids, weights and every coordinate plane, one round trip).  A tile all of whose
+// points lie in one block takes one warp reduction and one set of atomics.  Otherwise the
+// runs of equal block ids inside each lane are added directly, except the lane's last run,
+// which goes through a segmented reduction over the lanes (runs continue across lanes).
+// Sums are fixed point (the carry-free form), extremes ordered keys.  (Taking the tile's
+// points block by block instead, one warp reduction and one set of atomics per distinct
+// block, needed more instructions per tile and was slower at 1e9 points: 2.12 against
+// 1.90 ms per movement.)
 template <typename T, int D>
 __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     const int lane = threadIdx.x & 31;
@@ -2248,42 +2395,29 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
     load_ids8(p, i0, nval, ids);
     T wv[8];
     if (p.weighted) load8<T>((const T *)p.Ws, i0, nval, wv);
-    T xv[D][8];
+    T xv[D][8];  // every plane, loaded with the ids (one round trip)
 #pragma unroll
     for (int j = 0; j < D; ++j) load8<T>(X + (size_t)j * p.n_pad, i0, nval, xv[j]);
-    unsigned rem = 0;  // the lane's points not yet added
-    bool bad = false;
+    const int b0 = __shfl_sync(0xffffffffu, ids[0], 0);  // lane 0 holds a point of the tile
+    bool same = true, bad = false;
+    int last = -1;  // block of the lane's last run
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         if (q < nval) {
-            if ((unsigned)ids[q] < (unsigned)p.k) rem |= 1u << q;
-            else bad = true;
+            same &= ids[q] == b0;
+            if ((unsigned)ids[q] >= (unsigned)p.k) bad = true;
+            else last = ids[q];
         }
     }
     if (bad) atomicOr(&p.ctl->bad_block, 1);
-    for (;;) {
-        const unsigned open = __ballot_sync(0xffffffffu, rem != 0u);
-        if (!open) break;
-        int first = -1;
-#pragma unroll
-        for (int q = 7; q >= 0; --q)
-            if ((rem >> q) & 1u) first = ids[q];
-        const int b = __shfl_sync(0xffffffffu, first, __ffs(open) - 1);
-        // the conversions below are redone each round (a few ALU operations) instead of
-        // being kept for every point and plane, which would triple the registers
-        opaque_values<T, D>(xv);
-        unsigned m = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (((rem >> q) & 1u) && ids[q] == b) m |= 1u << q;
-        rem &= ~m;
+    if (__all_sync(0xffffffffu, same) && (unsigned)b0 < (unsigned)p.k) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             long long sum = 0;
             unsigned long long kmin = ~0ull, kmax = 0ull;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                if ((m >> q) & 1u) {
+                if (q < nval) {
                     sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
                     const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
                     kmin = kk < kmin ? kk : kmin;
@@ -2292,16 +2426,67 @@ __device__ __noinline__ void centroid_tile(const Prob &p, const T *X, int t) {
             }
             for (int off = 16; off; off >>= 1) {
                 sum += __shfl_xor_sync(0xffffffffu, sum, off);
-                const unsigned long long x0 = __shfl_xor_sync(0xffffffffu, kmin, off);
-                const unsigned long long x1 = __shfl_xor_sync(0xffffffffu, kmax, off);
-                kmin = x0 < kmin ? x0 : kmin;
-                kmax = x1 > kmax ? x1 : kmax;
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, off);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, off);
+                kmin = a < kmin ? a : kmin;
+                kmax = b > kmax ? b : kmax;
             }
             if (lane == 0) {
-                red_add_s64(&p.SXfix[2 * (b * D + j)], sum);
-                atomicMin(&p.BBlo[b * D + j], kmin);
-                atomicMax(&p.BBhi[b * D + j], kmax);
+                red_add_s64(&p.SXfix[2 * (b0 * D + j)], sum);
+                atomicMin(&p.BBlo[b0 * D + j], kmin);
+                atomicMax(&p.BBhi[b0 * D + j], kmax);
             }
+        }
+        return;
+    }
+    // segments of the lanes' last runs (the same for every plane)
+    const int prev = __shfl_up_sync(0xffffffffu, last, 1);
+    const bool head = lane == 0 || last != prev;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const bool end = lane == 31 || ((heads >> (lane + 1)) & 1u);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        int cur = -1;
+        long long sum = 0;
+        unsigned long long kmin = ~0ull, kmax = 0ull;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < nval && (unsigned)ids[q] < (unsigned)p.k) {
+                if (ids[q] != cur) {
+                    if (cur >= 0) {  // a run that ends inside the lane
+                        red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
+                        atomicMin(&p.BBlo[cur * D + j], kmin);
+                        atomicMax(&p.BBhi[cur * D + j], kmax);
+                    }
+                    cur = ids[q];
+                    sum = 0;
+                    kmin = ~0ull;
+                    kmax = 0ull;
+                }
+                sum += cent_fix<T>(p, p.weighted ? wv[q] : (T)1, xv[j][q]);
+                const unsigned long long kk = KeyOf<T>::key(xv[j][q]);
+                kmin = kk < kmin ? kk : kmin;
+                kmax = kk > kmax ? kk : kmax;
+            }
+        }
+        // the lanes' last runs: a run covers at most 256 values below 2^54, so 64 bits
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const bool take = lane - off >= start;
+            const long long s2 = __shfl_up_sync(0xffffffffu, sum, off);
+            const unsigned long long a = __shfl_up_sync(0xffffffffu, kmin, off);
+            const unsigned long long b = __shfl_up_sync(0xffffffffu, kmax, off);
+            if (take) {
+                sum += s2;
+                kmin = a < kmin ? a : kmin;
+                kmax = b > kmax ? b : kmax;
+            }
+        }
+        if (end && cur >= 0) {
+            red_add_s64(&p.SXfix[2 * (cur * D + j)], sum);
+            atomicMin(&p.BBlo[cur * D + j], kmin);
+            atomicMax(&p.BBhi[cur * D + j], kmax);
         }
     }
 }
@@ -2585,6 +2770,10 @@ static dim3 hyper_grid(const Prob &p) { return dim3((unsigned)((p.nhypers + kFil
 static void *filter_big_fn(int d) {
     return d == 2 ? (void *)filter_big_kernel<2> : (void *)filter_big_kernel<3>;
 }
+static void *filter_tile_fn(int d) {
+    return d == 2 ? (void *)filter_tile_kernel<2> : (void *)filter_tile_kernel<3>;
+}
+static dim3 filter_tile_grid(const Prob &p) { return dim3((unsigned)(p.nsm > 0 ? p.nsm : 152) * 2); }
 static dim3 filter_big_grid(const Prob &p) {
     const long long need = ((long long)p.nsupers * p.stiles + kFilterWarps - 1) / kFilterWarps;
     const long long cap = (long long)(p.nsm > 0 ? p.nsm : 152) * 8;
@@ -2654,11 +2843,14 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     }
     e = cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
+    e = cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), args1, 0, s);
 }
 // resident CTAs per SM: registers (FP64 mode) or the stages' shared memory (3-D)
 int assign_max_ctas(const Prob &p) {
-    return p.assign_f64 ? kAMinBlocks64 : ((p.bounds && p.d == 3) ? 4 : kAMinBlocks);
+    // 3-D stages (three, or two larger ones with bounds) fit four CTAs in shared memory
+    return p.assign_f64 ? kAMinBlocks64 : (p.d == 3 ? 4 : kAMinBlocks);
 }
 int assign_ctas(const Prob &p) {
     const int m = assign_max_ctas(p);
@@ -2827,6 +3019,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
             if (p.hyper) bl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
             bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
+            bl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
                       assign_smem_of(p));
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
@@ -2847,6 +3040,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
         if (p.hyper) fl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
+        fl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
                   assign_smem_of(p));
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
@@ -2891,6 +3085,7 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
         if (ps.hyper) bl.kernel(hyper_fn(ps.d), hyper_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(filter_fn(ps.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         bl.kernel(filter_big_fn(ps.d), filter_big_grid(ps), dim3(kFilterThreads), a_p);
+        bl.kernel(filter_tile_fn(ps.d), filter_tile_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(assign_fn(ps), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p,
                   assign_smem_of(ps));
         bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
