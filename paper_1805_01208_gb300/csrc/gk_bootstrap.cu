@@ -328,30 +328,19 @@ __global__ void __launch_bounds__(256) radix_scan(unsigned *hist, int G, unsigne
     if (t == 0) totals[blockIdx.x] = total;
 }
 
-// 16-byte asynchronous copy global -> shared of the first `bytes` bytes (the rest of
-// the 16 zero-filled); both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Dynamic shared memory of the downsweep: the current tile in digit order.  The tile
+// comes into registers straight from global memory (coalesced 8-byte loads); with no
+// staging copy in shared memory four CTAs fit an SM, whose other warps hide the loads.
+constexpr size_t kDownsweepSmem = (size_t)kSortTile * (8 + 4);
 
-// Dynamic shared memory of the downsweep: the next tile (keys, values) while the
-// current one is ranked, and the current tile in digit order.
-constexpr size_t kDownsweepSmem = (size_t)kSortTile * (8 + 4) * 2;
-
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
                 unsigned long long *keys_out, unsigned *vals_out, long long n, int shift,
                 int tiles_per_seg, int G, const unsigned *offs, const unsigned *totals, Ctl *ctl) {
     count_launch(ctl);
     extern __shared__ __align__(16) unsigned char dsm[];
-    unsigned long long *stk = reinterpret_cast<unsigned long long *>(dsm);  // next tile
-    unsigned *stv = reinterpret_cast<unsigned *>(dsm + (size_t)kSortTile * 8);
-    unsigned long long *skey = reinterpret_cast<unsigned long long *>(dsm + (size_t)kSortTile * 12);
-    unsigned *sval = reinterpret_cast<unsigned *>(dsm + (size_t)kSortTile * 20);  // digit order
+    unsigned long long *skey = reinterpret_cast<unsigned long long *>(dsm);  // digit order
+    unsigned *sval = reinterpret_cast<unsigned *>(dsm + (size_t)kSortTile * 8);
     __shared__ unsigned run_off[256];               // output position of the digit's next item
     __shared__ unsigned whist[kSortWarps][256];     // per-warp counts, then per-warp offsets
     __shared__ unsigned tstart[256];                // start of each digit in the tile's order
@@ -374,23 +363,6 @@ radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
         return before + x - v;
     };
     const long long seg_beg = (long long)blockIdx.x * tiles_per_seg * kSortTile;
-    // tile t of the segment into the stage (asynchronous copies, one commit group)
-    auto prefetch = [&](int t) {
-        const long long tb = seg_beg + (long long)t * kSortTile;
-        if (t < tiles_per_seg && tb < n) {
-            const int nt = (int)(n - tb < kSortTile ? n - tb : kSortTile);
-            for (int c = tid; c < kSortTile / 2; c += kSortThreads) {
-                const int b = min(16, nt * 8 - c * 16);
-                if (b > 0) cp_async16(stk + 2 * c, keys_in + tb + 2 * c, b);
-            }
-            for (int c = tid; c < kSortTile / 4; c += kSortThreads) {
-                const int b = min(16, nt * 4 - c * 16);
-                if (b > 0) cp_async16(stv + 4 * c, vals_in + tb + 4 * c, b);
-            }
-        }
-        cp_async_commit();
-    };
-    prefetch(0);
     // start of each digit: exclusive scan of the digit totals, plus this segment's prefix
     // within the digit
     run_off[tid] = digit_scan(totals[tid]) + offs[(long long)tid * G + blockIdx.x];
@@ -400,18 +372,17 @@ radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
         const long long tile_beg = seg_beg + (long long)t * kSortTile;
         if (tile_beg >= n) break;
         const int nt = (int)(n - tile_beg < kSortTile ? n - tile_beg : kSortTile);
-        cp_async_wait_all();
-        __syncthreads();
         unsigned long long k[kSortItems];
         unsigned v[kSortItems], dig[kSortItems], loc[kSortItems];
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
             const int li = warp * (32 * kSortItems) + r * 32 + lane;
-            k[r] = li < nt ? stk[li] : 0ull;
-            v[r] = li < nt ? stv[li] : 0u;
+            k[r] = li < nt ? __ldcs(keys_in + tile_beg + li) : 0ull;  // read once: streaming
+            v[r] = li < nt ? __ldcs(vals_in + tile_beg + li) : 0u;
         }
-        __syncthreads();  // the stage is free: bring in the next tile while this one is ranked
-        prefetch(t + 1);
+        // the per-warp counts were cleared by other threads (thread d clears digit d of every
+        // warp's row): they must be zero before any warp ranks
+        __syncthreads();
         // ranks inside the warp: items of a warp in order, equal digits counted with match_any
 #pragma unroll
         for (int r = 0; r < kSortItems; ++r) {
@@ -440,8 +411,10 @@ radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
         for (int r = 0; r < kSortItems; ++r) {
             if (dig[r] < 256u) {
                 const unsigned pos = tstart[dig[r]] + whist[warp][dig[r]] + loc[r];
-                skey[pos] = k[r];
-                sval[pos] = v[r];
+                if (pos < (unsigned)kSortTile) {  // always true when the counts are consistent
+                    skey[pos] = k[r];
+                    sval[pos] = v[r];
+                }
             }
         }
         __syncthreads();
@@ -459,7 +432,6 @@ radix_downsweep(const unsigned long long *keys_in, const unsigned *vals_in,
         run_off[tid] += tc;
         for (int w = 0; w < kSortWarps; ++w) whist[w][tid] = 0;
     }
-    cp_async_wait_all();  // no copy outlives the kernel
 }
 
 // ------------------------------------------------------------------------------
