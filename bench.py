@@ -336,6 +336,8 @@ def _roofline(gk, xt, wt, spec, workload):
             "bytes_per_launch": bytes_per_pass, "launch_ms_events": pass_ms,
             "peak_source": peak_kind,
             "kernels_ms_per_pass": {"filter": ev_filter, "assign": ev_assign, "balance": ev_balance},
+            "shapes": {"supertile_tiles": tres["supertile_tiles"], "hypertiles": tres["hypertiles"],
+                       "assign_ctas_per_sm": tres["assign_ctas_per_sm"]},
             "move_ms_per_phase": tres["time_move_ms"] / max(1, tres["move_launches"])}
     _attach_traffic(roof, workload)
     return roof

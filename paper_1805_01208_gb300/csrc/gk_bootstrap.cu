@@ -220,25 +220,62 @@ __host__ __device__ __forceinline__ unsigned long long skilling_key(unsigned X[D
     return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
 }
 
+// The 2-D curve of skilling_key<2, 32> as a four-state machine, one level (two key bits)
+// per step: entry 4 s + 2 xbit + ybit holds the level's digit and, shifted by two, the
+// next state; the walk starts in state 0 at the top level.  The states were read off
+// skilling_key level by level, and the walk gives its key for every input (the key tests
+// compare the keys of both dimensions with the oracle's independent level descent).  Four
+// levels per step come from a 1024-entry table each CTA builds from this one.
+__constant__ unsigned char kHilbertStep2[16] = {4, 1, 11, 2, 0, 15, 5, 6, 10, 9, 3, 12, 14, 7, 13, 8};
+
 template <typename T, int D>
-__global__ void keys_kernel(Prob p, unsigned long long *keys_out, unsigned *perm_out) {
+__global__ void __launch_bounds__(256) keys_kernel(Prob p, unsigned long long *keys_out, unsigned *perm_out) {
     count_launch(p.ctl);
-    const T *x = (const T *)p.coords;
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.n) return;
-    unsigned q[D];
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-        if (sizeof(T) == 8) {
-            double v = __dsub_rn((double)x[i * D + j], p.origin[j]);
-            q[j] = quant_bits_f64(v, p.grid_m, p.bits);
-        } else {
-            float v = __fsub_rn((float)x[i * D + j], (float)p.origin[j]);
-            q[j] = quant_bits_f32(v, p.grid_m, p.bits);
+    __shared__ unsigned short step4[D == 2 ? 1024 : 1];  // 2-D: state, x and y nibbles
+    if constexpr (D == 2) {
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int xn = (e >> 4) & 15, yn = e & 15;
+            int st = e >> 8, out = 0;
+            for (int l = 3; l >= 0; --l) {
+                const int v = kHilbertStep2[st * 4 + ((((xn >> l) & 1) << 1) | ((yn >> l) & 1))];
+                out = (out << 2) | (v & 3);
+                st = v >> 2;
+            }
+            step4[e] = (unsigned short)(out | (st << 8));
         }
+        __syncthreads();
     }
-    keys_out[i] = skilling_key<D, D == 2 ? 32 : 21>(q);
-    if (perm_out) perm_out[i] = (unsigned)i;
+    const T *x = (const T *)p.coords;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) {
+        unsigned q[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            if (sizeof(T) == 8) {
+                double v = __dsub_rn((double)x[i * D + j], p.origin[j]);
+                q[j] = quant_bits_f64(v, p.grid_m, p.bits);
+            } else {
+                float v = __fsub_rn((float)x[i * D + j], (float)p.origin[j]);
+                q[j] = quant_bits_f32(v, p.grid_m, p.bits);
+            }
+        }
+        unsigned long long key;
+        if constexpr (D == 2) {
+            key = 0ull;
+            unsigned st = 0u;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const unsigned e = (((q[0] >> (28 - 4 * c)) & 15u) << 4) | ((q[1] >> (28 - 4 * c)) & 15u);
+                const unsigned v = step4[(st << 8) | e];
+                key = (key << 8) | (v & 255u);
+                st = v >> 8;
+            }
+        } else {
+            key = skilling_key<D, 21>(q);
+        }
+        keys_out[i] = key;
+        if (perm_out) perm_out[i] = (unsigned)i;
+    }
 }
 
 // ------------------------------------------------------------------------------
@@ -821,6 +858,8 @@ cudaError_t launch_bbox(const Prob &p, cudaStream_t s) {
 
 cudaError_t launch_keys(const Prob &p, unsigned long long *keys, unsigned *perm, cudaStream_t s) {
     int grid = blocks_for(p.n, 256);
+    const int cap = (p.nsm > 0 ? p.nsm : 152) * 16;  // grid-stride: each CTA builds its table once
+    if (grid > cap) grid = cap;
     if (p.dtype == 1) {
         if (p.d == 2)
             keys_kernel<double, 2><<<grid, 256, 0, s>>>(p, keys, perm);
