@@ -53,6 +53,7 @@ DEFAULT_WORKLOAD = "spots2d_1e9_k16384_f32"
 BATCHED_WORKLOAD = "batched64_f32"
 EXTRA_LEGS = ("gmm3d_1e7_k1024_f64", "radial2d_1e8_k4096_f32", BATCHED_WORKLOAD)
 FLUSH_BYTES = 512 << 20  # written between timed steps: evicts the 129 MB L2
+FIXED_SHAPES: dict = {}  # --shapes: fixed launch shapes (with --no-legs: the headline's calls)
 
 
 def _args():
@@ -63,6 +64,10 @@ def _args():
     ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="override the number of points")
+    ap.add_argument("--shapes", default=None,
+                    help="fix the launch shapes as 'supertile_tiles,hypertiles,ctas_per_sm' for the "
+                         "headline workload's partitions and its roofline run (for profiles: the "
+                         "tuner's choice can differ under a profiler)")
     ap.add_argument("--k", type=int, default=None,
                     help="override the number of blocks (profiling a smaller n at the "
                          "workload's points per block)")
@@ -317,7 +322,7 @@ def _roofline(gk, xt, wt, spec, workload):
     once) over the mean CUDA-event duration of those launches per pass, in a host-driven
     run of the same partition (events on the library's stream)."""
     n, d, k = int(xt.shape[0]), spec["d"], spec["k"]
-    timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1)
+    timed = gk.default_options(assign_dtype=spec["assign"], use_graph=0, timing=1, **FIXED_SHAPES)
     _, _, _, tres = gk.partition(xt, k, spec["eps"], weights=wt, options=timed)
     npass = max(1, tres["assign_launches"])
     ev_assign = tres["time_assign_ms"] / npass
@@ -546,7 +551,10 @@ def main():
     n, d, k, eps = len(x), spec["d"], spec["k"], spec["eps"]
     xt = torch.from_numpy(x).to(dev)
     wt = None if w is None else torch.from_numpy(w).to(dev)
-    opts = gk.default_options(assign_dtype=spec["assign"])
+    if args.shapes:
+        stl, hy, ct = (int(v) for v in args.shapes.split(","))
+        FIXED_SHAPES.update(supertile_tiles=stl, hypertiles=hy, assign_ctas_per_sm=ct)
+    opts = gk.default_options(assign_dtype=spec["assign"], **FIXED_SHAPES)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
