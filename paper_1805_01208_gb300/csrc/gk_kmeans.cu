@@ -880,6 +880,11 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(Prob p) {
 static_assert(kLaneMax <= kCap, "a short list always fits the tile record");
 static_assert(kMaxSuperTiles <= 32, "level 2 of the filter takes one lane per tile");
 
+// Whether filter_tile_kernel runs: with at most kWarpGroups groups (k <= 2048) no supertile
+// is split, and a tile whose list does not fit its record takes every center (an
+// overflowed record), as it costs little at that k; the launch is then left out.
+__host__ __device__ __forceinline__ bool filter_tile_needed(const Prob &p) { return p.ngroups > kWarpGroups; }
+
 // A tile of filter_big_kernel once its record is written (lane 0): finished here with one
 // candidate c1, or put on the assignment's work list.
 __device__ __forceinline__ void big_tile_done(const Prob &p, int t, int cnt, int c1, int marker) {
@@ -975,7 +980,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_big_kernel(Prob p) {
             cnt += __popc(bal);
         }
         c1 = __reduce_max_sync(0xffffffffu, c1);  // the first kept center
-        if (cnt > kCap) {  // the list does not fit: the tile's own level 1 (rewrites the record)
+        if (cnt > kCap && filter_tile_needed(p)) {  // the tile's own level 1 rewrites the record
             if (lane == 0) p.tlist[atomicAdd(&p.ctl->jump_cnt, 1u)] = t;
             continue;
         }
@@ -2844,7 +2849,7 @@ cudaError_t launch_filter(const Prob &p, cudaStream_t s) {
     e = cudaLaunchKernel(filter_fn(p.d), grid, dim3(kFilterThreads), args1, smem, s);
     if (e != cudaSuccess) return e;
     e = cudaLaunchKernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), args1, 0, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || !filter_tile_needed(p)) return e;
     return cudaLaunchKernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), args1, 0, s);
 }
 // resident CTAs per SM: registers (FP64 mode) or the stages' shared memory (3-D)
@@ -3019,7 +3024,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
             if (p.hyper) bl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
             bl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
-            bl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
+            if (filter_tile_needed(p)) bl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
             bl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
                       assign_smem_of(p));
             bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
@@ -3040,7 +3045,7 @@ cudaError_t add_loop_chain(cudaGraph_t g, const Prob &pc, cudaGraphNode_t after 
         if (p.hyper) fl.kernel(hyper_fn(p.d), hyper_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(filter_fn(p.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         fl.kernel(filter_big_fn(p.d), filter_big_grid(p), dim3(kFilterThreads), a_p);
-        fl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
+        if (filter_tile_needed(p)) fl.kernel(filter_tile_fn(p.d), filter_tile_grid(p), dim3(kFilterThreads), a_p);
         fl.kernel(assign_fn(p), dim3(assign_grid(p)), dim3(kAWarps * 32), a_p,
                   assign_smem_of(p));
         fl.kernel((void *)balance_kernel, kg, kb, a_bal1);
@@ -3085,7 +3090,7 @@ static cudaError_t add_sample_round(NodeAdder &top, const Prob &psc, const Sampl
         if (ps.hyper) bl.kernel(hyper_fn(ps.d), hyper_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(filter_fn(ps.d), fgrid, dim3(kFilterThreads), a_p, fsmem);
         bl.kernel(filter_big_fn(ps.d), filter_big_grid(ps), dim3(kFilterThreads), a_p);
-        bl.kernel(filter_tile_fn(ps.d), filter_tile_grid(ps), dim3(kFilterThreads), a_p);
+        if (filter_tile_needed(ps)) bl.kernel(filter_tile_fn(ps.d), filter_tile_grid(ps), dim3(kFilterThreads), a_p);
         bl.kernel(assign_fn(ps), dim3(assign_grid(ps)), dim3(kAWarps * 32), a_p,
                   assign_smem_of(ps));
         bl.kernel((void *)balance_kernel, kg, kb, a_bal0);
