@@ -465,10 +465,10 @@ gk_status gk_set_allocator(gk_alloc_fn alloc, gk_free_fn free_fn, void *ctx);
  * Its scratch is one fixed array of about 450 KB in the library's device memory,
  * held by every GPU that loads the library until the process exits; hence the limit
  * 1 <= k <= GK_NOALLOC_MAX_K (larger k: GK_ERR_INVALID_ARG).  The first call on a
- * device looks up the array's device address (set-up); make that first call before
- * any stream capture.  Every call reuses the array and clears it first; calls whose
- * GPU work overlaps (other streams, other host threads) race on it.  The call waits
- * for its stream before it returns (it reads the input check and beta back).
+ * device looks up the array's device address (set-up).  Every call reuses the array
+ * and clears it first; calls whose GPU work overlaps (other streams, other host
+ * threads) race on it.  The call waits for its stream before it returns (it reads the
+ * input check and beta back), so it cannot be captured into a CUDA graph.
  *   coords, weights (nullable), block, centers, centers_out, delta_out (nullable):
  *   device memory of the current device; beta_out (nullable): host memory or device
  *   memory of the current device (written by a copy on the stream).
