@@ -4,6 +4,7 @@
 // then edge cut = sum ext / 2, total and maximum communication volume; and per block a
 // lower bound of diam(V_i), the largest distance between two vertices of V_i inside the
 // subgraph V_i induces, from breadth-first sweeps.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -214,7 +215,9 @@ cudaError_t launch_quality(const long long *row_ptr, const int *col, long long n
 // one search seeded with one vertex per block is k separate searches.  Each level expands
 // a frontier list; a vertex joins the next list when its distance moves from -1 to the
 // next level (compare-and-swap, so once per sweep), and the host reads the length of the
-// next list to size the next launch and to stop when it is empty.
+// next list to stop when it is empty.  A level's new vertices are gathered per CTA in
+// shared memory and appended with one global atomic per CTA and round: one counter that
+// every new vertex incremented took about one L2 atomic per vertex on a single address.
 // ----------------------------------------------------------------------------------------
 __global__ void diam_fill_kernel(int *a, long long m, int v) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,29 +257,59 @@ __global__ void diam_seed_kernel(int k, const int *start, int *dist, int *front,
     }
 }
 
-// One thread per frontier vertex of distance `level`.
-// One breadth-first level over the frontier list (its length read on the device, so that
-// the host can enqueue several levels without waiting; an empty frontier does nothing).
-// Grid-stride over the frontier; levels counts the non-empty levels.
-__global__ void diam_expand_kernel(const int *front, const unsigned *cnt_in, int level,
-                                   const long long *row_ptr, const int *col, const int *block,
-                                   int *dist, int *next, unsigned *cnt_out, int *ecc,
-                                   int *reached, unsigned long long *levels) {
+// One breadth-first level over the frontier list of distance `level` (its length read on
+// the device, so that the host can enqueue several levels without waiting; an empty
+// frontier does nothing).  The CTA takes kExpandThreads entries per round, one per thread;
+// the vertices a round finds go to a shared buffer (a warp-aggregated shared counter), which
+// one atomic on cnt_out places in the next list; a round that finds more than the buffer
+// holds appends the rest one by one.  levels counts the non-empty levels.
+constexpr int kExpandThreads = 256;
+constexpr unsigned kExpandBuf = 2048;
+
+__global__ void __launch_bounds__(kExpandThreads) diam_expand_kernel(
+    const int *front, const unsigned *cnt_in, int level, const long long *row_ptr,
+    const int *col, const int *block, int *dist, int *next, unsigned *cnt_out, int *ecc,
+    int *reached, unsigned long long *levels) {
+    namespace cg = cooperative_groups;
+    __shared__ int sbuf[kExpandBuf];
+    __shared__ unsigned scnt, sbase;
     const unsigned m = *cnt_in;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && m > 0) atomicAdd(levels, 1ull);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int v = front[i];
-        const int b = block[v];
-        const long long e1 = row_ptr[v + 1];
-        for (long long e = row_ptr[v]; e < e1; ++e) {
-            const int u = col[e];
-            if (u == v || block[u] != b) continue;
-            if (atomicCAS(&dist[u], -1, level + 1) == -1) {
-                next[atomicAdd(cnt_out, 1u)] = u;
-                atomicAdd(&reached[b], 1);
-                atomicMax(&ecc[b], level + 1);
+    if (m == 0) return;  // the same for every thread of the grid
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(levels, 1ull);
+    if (threadIdx.x == 0) scnt = 0;
+    __syncthreads();
+    const unsigned stride = gridDim.x * kExpandThreads;
+    for (unsigned i0 = blockIdx.x * kExpandThreads; i0 < m; i0 += stride) {  // CTA-uniform
+        const unsigned i = i0 + threadIdx.x;
+        if (i < m) {
+            const int v = front[i];
+            const int b = block[v];
+            const long long e1 = row_ptr[v + 1];
+            for (long long e = row_ptr[v]; e < e1; ++e) {
+                const int u = col[e];
+                if (u == v || block[u] != b) continue;
+                if (atomicCAS(&dist[u], -1, level + 1) == -1) {
+                    cg::coalesced_group g = cg::coalesced_threads();
+                    unsigned pos = 0;
+                    if (g.thread_rank() == 0) pos = atomicAdd(&scnt, g.size());
+                    pos = g.shfl(pos, 0) + g.thread_rank();
+                    if (pos < kExpandBuf)
+                        sbuf[pos] = u;
+                    else
+                        next[atomicAdd(cnt_out, 1u)] = u;
+                    atomicAdd(&reached[b], 1);
+                    atomicMax(&ecc[b], level + 1);
+                }
             }
         }
+        __syncthreads();
+        const unsigned c = min(scnt, kExpandBuf);
+        if (threadIdx.x == 0 && c > 0) sbase = atomicAdd(cnt_out, c);
+        __syncthreads();
+        for (unsigned j = threadIdx.x; j < c; j += kExpandThreads) next[sbase + j] = sbuf[j];
+        __syncthreads();  // every thread has read scnt and sbuf
+        if (threadIdx.x == 0) scnt = 0;
+        __syncthreads();
     }
 }
 
@@ -395,7 +428,7 @@ cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, 
         for (;;) {
             for (int g = 0; g < kLevelsPerWait; ++g, ++level) {
                 if ((e = cudaMemsetAsync(cnt + (cur ^ 1), 0, 4, s)) != cudaSuccess) return e;
-                diam_expand_kernel<<<grid, 256, 0, s>>>(front[cur], cnt + cur, level, row_ptr, col, block,
+                diam_expand_kernel<<<grid, kExpandThreads, 0, s>>>(front[cur], cnt + cur, level, row_ptr, col, block,
                                                         dist, front[cur ^ 1], cnt + (cur ^ 1), ecc,
                                                         reached, levels);
                 if ((e = cudaGetLastError()) != cudaSuccess) return e;

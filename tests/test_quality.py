@@ -334,6 +334,32 @@ def test_gpu_diameter_random_graph_and_random_blocks(gk):
 
 
 @pytest.mark.gpu
+def test_gpu_diameter_hubs_overflow_the_level_buffer(gk):
+    """Two trees whose hubs reach 20,000 and 3,000 leaves in one level: one CTA round finds
+    more new vertices than its shared buffer holds, so the rest are appended one by one.
+    On trees two sweeps give the exact diameter: 12 (leaf, hub, leaf 1 and a path of ten
+    hanging from it) and 2 (a star)."""
+    rng = np.random.default_rng(3)
+    leaves = 20_000
+    edges = [(0, i) for i in range(1, leaves + 1)]
+    prev = 1
+    for v in range(leaves + 1, leaves + 11):
+        edges.append((prev, v))
+        prev = v
+    h = leaves + 11
+    edges += [(h, h + i) for i in range(1, 3001)] + [(0, h)]  # the hub-hub edge is cut
+    n = h + 3001
+    perm = rng.permutation(n)
+    rp, col = _csr(n, [(int(perm[a]), int(perm[b])) for a, b in edges])
+    blk = np.zeros(n, dtype=np.int32)
+    blk[h:] = 1
+    block = np.empty(n, dtype=np.int32)
+    block[perm] = blk
+    q, d = _check_diam(gk, rp, col, block, 2, sweeps=2)
+    assert d.tolist() == [12, 2]
+
+
+@pytest.mark.gpu
 def test_gpu_diameter_rejects_malformed_input(gk):
     rp, col = _csr(4, [(0, 1), (1, 2), (2, 3)])
     with pytest.raises(gk.GKError):
