@@ -153,6 +153,21 @@ const char *gk_status_string(int32_t status);
 int32_t gk_abi_version(void);
 
 /*
+ * Self-check of the library's failure detection (no counterpart in the paper).  Every
+ * wait in the library's kernels (the assignment waits on an mbarrier for the bulk copies of
+ * its tiles) is bounded: after 2 s of device time (or 2^26 polls) it gives up, records
+ * GK_ERR_TIMEOUT, waits (bounded) for its own copies still in flight and returns, so the
+ * CUDA context stays usable and the call returns GK_ERR_TIMEOUT.  This call runs one such
+ * wait, limited to limit_us microseconds of device time, on an mbarrier that nothing
+ * completes (no copy is issued on it), so that the path can be exercised without a fault.
+ *   limit_us: 1 .. 10,000,000, else GK_ERR_INVALID_ARG;
+ *   waited_us (nullable, host memory): the device time the wait took, in microseconds.
+ * Returns GK_ERR_TIMEOUT when the wait gave up (the expected result), GK_OK if it
+ * completed, GK_ERR_CUDA on a CUDA error.  Waits for its stream before it returns.
+ */
+gk_status gk_check_wait_timeout(int64_t limit_us, int64_t *waited_us, void *stream);
+
+/*
  * Hilbert index of every point (Algorithm 2 "sfcIndex"; Section 4.1).
  * Each coordinate is mapped to a 2^b cell grid (b = 32 for d = 2, 21 for
  * d = 3) over the points' bounding box made isotropic with side 2^E, the

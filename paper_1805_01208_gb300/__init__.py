@@ -160,6 +160,8 @@ def lib():
         L.gk_status_string.argtypes = [i32]
         L.gk_status_string.restype = ctypes.c_char_p
         L.gk_abi_version.restype = i32
+        L.gk_check_wait_timeout.argtypes = [i64, P, P]
+        L.gk_check_wait_timeout.restype = i32
         L.gk_hilbert_keys.argtypes = [P, i32, i64, i32, P, P]
         L.gk_sfc_init.argtypes = [P, i32, i64, i32, i32, P, P, P]
         L.gk_assign.argtypes = [P, i32, P, i64, i32, i32, P, P, i32, P, P, P]
@@ -568,6 +570,15 @@ def partition_batched(problems, options: Options | None = None, stream=None):
                                     _stream(problems[0][0], stream))
     _check(st, "gk_partition_batched", allow=(GK_ERR_NOT_BALANCED,))
     return [(b, c, i_, res[j].as_dict()) for j, (b, c, i_) in enumerate(outs)], st
+
+
+def check_wait_timeout(limit_us=2000, stream=None):
+    """Runs one bounded device-side wait that nothing completes (gk_check_wait_timeout);
+    returns (status, device microseconds the wait took).  GK_ERR_TIMEOUT is expected."""
+    waited = ctypes.c_int64(0)
+    st = lib().gk_check_wait_timeout(int(limit_us), ctypes.byref(waited),
+                                     ctypes.c_void_p(int(stream) if stream is not None else 0))
+    return int(st), int(waited.value)
 
 
 def release():

@@ -1234,6 +1234,15 @@ const char *gk_status_string(int32_t status) {
 
 int32_t gk_abi_version(void) { return GK_ABI_VERSION; }
 
+gk_status gk_check_wait_timeout(int64_t limit_us, int64_t *waited_us, void *stream) {
+    if (limit_us < 1 || limit_us > 10000000) return GK_ERR_INVALID_ARG;
+    int st = kOk;
+    unsigned long long ns = 0;
+    GK_CUDA(run_wait_check((unsigned long long)limit_us * 1000ull, &st, &ns, (cudaStream_t)stream));
+    if (waited_us) *waited_us = (int64_t)(ns / 1000ull);
+    return st == kOk ? GK_OK : GK_ERR_TIMEOUT;
+}
+
 gk_status gk_partition_batched(const gk_instance *inst, int32_t count, const gk_options *opt,
                                gk_result *results, void *stream) {
     return partition_batched(inst, count, opt, results, stream);

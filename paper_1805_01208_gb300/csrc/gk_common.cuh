@@ -57,7 +57,8 @@ static_assert(kGroup == kKThreads, "a group record is written by one CTA of the 
 constexpr int kFixBits = 54;        // |fixed-point value| < 2^54 per point
 constexpr int kStripes = 64;        // striped counters for per-pass statistics
 constexpr int kStripeStride = 16;   // 64-bit words per stripe: each in its own 128-byte line
-constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers
+constexpr long long kSpinLimit = 1ll << 26;  // bounded waits on mbarriers: most polls,
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // and most device time (2 s)
 constexpr int kSkipHist = 64;       // passes of a phase with per-point bounds (then a fresh pass)
 
 // Error codes mirrored from gk.h (device code does not include the C header).
@@ -374,10 +375,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
         : "memory");
     return ok != 0;
 }
-// Returns false if the phase did not complete within kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
-    for (long long it = 0; it < kSpinLimit; ++it)
+// Device time in nanoseconds (the global timer).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Returns false if the phase did not complete within limit_ns of device time (a try_wait
+// may suspend the thread for a time of the hardware's choosing, so a count of polls alone
+// does not bound the wait in seconds) or kSpinLimit polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void fence_mbarrier_init() {

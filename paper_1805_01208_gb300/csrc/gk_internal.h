@@ -53,6 +53,12 @@ cudaError_t run_diameter(const long long *row_ptr, const int *col, long long n, 
                          long long *out_i, double *out_d, int *hbad, long long *hlevels,
                          cudaStream_t s);
 
+// One bounded wait, with limit_ns of device time, on an mbarrier that nothing completes
+// (gk_kmeans.cu); *status = kErrTimeout when it gave up, *waited_ns its device time.
+// Synchronises the stream.
+cudaError_t run_wait_check(unsigned long long limit_ns, int *status,
+                           unsigned long long *waited_ns, cudaStream_t s);
+
 // iteration (gk_kmeans.cu)
 cudaError_t launch_init(const Prob &p, cudaStream_t s);
 cudaError_t launch_load_state(const Prob &p, cudaStream_t s);

@@ -2882,6 +2882,41 @@ cudaError_t launch_assign(const Prob &p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     return cudaLaunchKernel(fn, dim3(assign_grid(p)), dim3(kAWarps * 32), args1, assign_smem_of(p), s);
 }
+// The failure path of the assignment's waits, exercised without a fault: one warp waits,
+// bounded, for phase 0 of an mbarrier that expects one arrival and gets none (no copy is
+// issued on it, so nothing is in flight when the wait gives up).
+__device__ int g_wait_status;
+__device__ unsigned long long g_wait_ns;
+
+__global__ void wait_check_kernel(unsigned long long limit_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+    const bool all = __all_sync(0xffffffffu, ok);
+    if (threadIdx.x == 0) {
+        g_wait_status = all ? kOk : kErrTimeout;
+        g_wait_ns = global_ns() - t0;
+    }
+}
+
+cudaError_t run_wait_check(unsigned long long limit_ns, int *status,
+                           unsigned long long *waited_ns, cudaStream_t s) {
+    wait_check_kernel<<<1, 32, 0, s>>>(limit_ns);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(status, g_wait_status, sizeof(int), 0,
+                                                         cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyFromSymbolAsync(waited_ns, g_wait_ns, sizeof(unsigned long long), 0,
+                                      cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 cudaError_t launch_balance(const Prob &p, int mode, cudaStream_t s) {
     balance_kernel<<<kgrid(p), kKThreads, 0, s>>>(p, mode, 0);
     if (mode != 2) launch_supergroups(p, s);

@@ -30,7 +30,7 @@ def test_header_declares_the_entry_points():
                  "gk_assign", "gk_move_centers", "gk_release", "gk_default_options",
                  "gk_status_string", "gk_abi_version", "gk_partition_batched",
                  "gk_partition_sampled", "gk_partition_quality", "gk_block_diameter",
-                 "gk_set_allocator"):
+                 "gk_set_allocator", "gk_check_wait_timeout"):
         assert want in names
 
 
@@ -49,6 +49,8 @@ def test_host_only_helpers(libgk):
     assert o.hypertiles == 0
     assert gk.status_string(gk.GK_ERR_NOT_BALANCED) == "GK_ERR_NOT_BALANCED"
     assert gk.status_string(99) == "GK_UNKNOWN_STATUS"
+    for bad in (0, -5, 10_000_001):  # the wait limit is checked before any launch
+        assert gk.check_wait_timeout(bad)[0] == gk.GK_ERR_INVALID_ARG
 
 
 def test_struct_layouts_match_header():

@@ -561,6 +561,22 @@ def test_allocation_failure_is_reported(gk):
     assert res["balanced"] == 1
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable(gk):
+    """The form of the assignment's waits, made to run out on an mbarrier that nothing
+    completes: it gives up after its device-time limit with GK_ERR_TIMEOUT (not sooner, and
+    not much later), and a partition afterwards still equals the oracle's."""
+    for limit_us in (2_000, 50_000):
+        st, waited = gk.check_wait_timeout(limit_us)
+        assert st == gk.GK_ERR_TIMEOUT, gk.status_string(st)
+        assert limit_us <= waited < limit_us + 100_000
+    st, _ = gk.check_wait_timeout(0)
+    assert st == gk.GK_ERR_INVALID_ARG
+    x = _points("uniform", 5_000, 2, 73, "f64")
+    block, C, I, res = gk.partition(_dev(x), 8, 0.03)
+    ref = oracle.partition(x, None, 8, 0.03, oracle.default_options(threads=THREADS))
+    assert np.array_equal(_np(block), ref["A"])
+
+
 # ----------------------------------------------------------------------------------------
 # Launch shapes (gk_options.supertile_tiles, assign_ctas_per_sm): the speed changes, the
 # results do not; the tuner picks one of the candidates and reports it.
