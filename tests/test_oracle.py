@@ -146,6 +146,11 @@ def test_quantisation_closed_forms():
     # all points equal: every cell 0, every key 0
     keys, q = oracle.hilbert_keys(np.full((5, 3), 7.25), return_cells=True)
     assert np.all(q == 0) and np.all(keys == 0)
+    # a cell is the floor, not the nearest integer: x = 0.75 + 0.75 * 2^-32 (exact in FP64)
+    # on the unit square scales to 3 * 2^30 + 0.75, in cell 3 * 2^30
+    x = np.array([[0.0, 0.0], [0.75 + 0.75 * 2.0 ** -32, 0.5], [1.0, 1.0]])
+    _, q = oracle.hilbert_keys(x, return_cells=True)
+    assert q[1].tolist() == [3 << 30, 1 << 31]
 
 
 def test_quantisation_fp32_subtracts_in_fp32():
@@ -155,6 +160,12 @@ def test_quantisation_fp32_subtracts_in_fp32():
     _, q = oracle.hilbert_keys(x, return_cells=True)
     assert int(q[1, 0]) == 1 << 9
     assert int(q[2, 1]) == 1 << 31
+    # lo = 2^-30, x = 1 + 2^-23: the exact difference 1 + 2^-23 - 2^-30 is not a float; FP32
+    # rounds it to 1 + 2^-23.  The extent is above 1 -> side 2, cell = floor(v * 2^31):
+    # 2^31 + 2^8 from the FP32 difference (2^31 + 2^8 - 2 from an FP64 one).
+    x = np.array([[2.0 ** -30, 0.0], [1.0 + 2.0 ** -23, 1.0]], dtype=np.float32)
+    _, q = oracle.hilbert_keys(x, return_cells=True)
+    assert q.tolist() == [[0, 0], [(1 << 31) + (1 << 8), 1 << 31]]
 
 
 def test_keys_of_points_follow_cells():
@@ -225,6 +236,8 @@ def test_assign_matches_squared_brute_force():
         assert clear.mean() > 0.99
         assert np.array_equal(A[clear], ref[clear])
         assert np.allclose(best, np.sqrt(sq.min(axis=1)), rtol=1e-13)
+        # the runner-up is the second smallest effective distance (equal to best on a tie)
+        assert np.allclose(second, np.sqrt(np.sort(sq, axis=1)[:, 1]), rtol=1e-13)
 
 
 def test_assign_ties_go_to_lowest_index():
@@ -274,6 +287,21 @@ def test_balance_update_closed_form():
     assert np.allclose(I2, want, rtol=1e-15)
     bal, I3, _ = oracle.balance_update(np.array([50.0, 104.0, 246.0, 0.0]), W, k, 3, eps, I)
     assert I3[1] == pytest.approx(2.0 * (100 / 104) ** (1 / 3), rel=1e-15)
+
+
+def test_balance_target_is_the_mean_and_imbalance_uses_the_ceiling():
+    """W/k not an integer: the target of Eq. 1 is W/k = 2.5 itself, the bound and the
+    imbalance use the ceiling 3 (Section 2)."""
+    k, d, eps, W = 4, 2, 0.0, 10.0
+    S = np.array([3.1, 2.5, 2.4, 2.0])  # 3.1 > 3: unbalanced
+    I = np.array([1.0, 1.0, 2.0, 0.5])
+    bal, I2, imb = oracle.balance_update(S, W, k, d, eps, I)
+    assert not bal and imb == pytest.approx(3.1 / 3.0 - 1.0, rel=1e-15)
+    want = I * np.array([0.95,                  # sqrt(2.5 / 3.1) = 0.898 -> clamp
+                         1.0,                   # at the target: unchanged
+                         math.sqrt(2.5 / 2.4),  # 1.0206, inside the clamp
+                         1.05])                 # sqrt(1.25) = 1.118 -> clamp
+    assert np.allclose(I2, want, rtol=1e-15)
 
 
 @pytest.mark.parametrize("d", [2, 3])

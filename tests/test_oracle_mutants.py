@@ -1,0 +1,140 @@
+"""The oracle's pins catch plausible mistakes (CPU).
+
+Each case below plants one mistake in a copy of ``oracle/gk_oracle.c`` (a flipped
+sign, a dropped term, a wrong index, a step out of order: the kinds of error a
+restatement of Algorithms 1-2 and Eq. 1-3 could contain), builds that copy into a
+library of its own in a temporary directory, and runs the oracle's pin tests
+(``tests/test_oracle.py``, ``tests/test_oracle_trajectory.py``) against it in a
+separate process.  The pins must fail for every planted mistake.  The committed
+oracle is never modified: the copy is loaded in place of it only inside that
+process.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "gk_oracle.c")
+HDR = os.path.join(ROOT, "oracle", "gk_oracle.h")
+PINS = ["tests/test_oracle.py", "tests/test_oracle_trajectory.py"]
+
+# name -> [(text in gk_oracle.c, its replacement), ...]; every text occurs exactly once
+MUTANTS = {
+    # Eq. 1 and the balance test (Section 2, Section 4.2, Algorithm 1)
+    "eq1_gamma_inverted": [("double gamma = target / S[c];", "double gamma = S[c] / target;")],
+    "eq1_no_root": [("factor = sqrt(gamma);", "factor = gamma;")],
+    "eq1_clamp_upper": [("if (factor > 1.05) factor = 1.05;", "if (factor > 1.5) factor = 1.5;")],
+    "eq1_clamp_lower": [("if (factor < 0.95) factor = 0.95;", "if (factor < 0.5) factor = 0.5;")],
+    "eq1_empty_block_kept": [("factor = INFINITY;", "factor = 1.0;")],
+    "eq1_target_ceiling": [("double target = W / (double)k;", "double target = ceil(W / (double)k);")],
+    "bound_no_ceiling": [("return (1.0 + eps) * ceil(W / (double)k);",
+                          "return (1.0 + eps) * (W / (double)k);")],
+    "bound_strict": [("if (max_s <= bound) return 1;", "if (max_s < bound) return 1;")],
+    "imbalance_against_target": [("if (imbalance) *imbalance = max_s / ceil_avg - 1.0;",
+                                  "if (imbalance) *imbalance = max_s / (W / (double)k) - 1.0;")],
+    # effective distance and argmin (Section 4.2)
+    "distance_times_influence": [("double eff = sqrt(ss) / I[c];", "double eff = sqrt(ss) * I[c];")],
+    "distance_squared": [("double eff = sqrt(ss) / I[c];", "double eff = ss / I[c];")],
+    "ties_to_highest_index": [("if (eff < best) {", "if (eff <= best) {")],
+    "runner_up_dropped": [("} else if (eff < second) {", "} else if (0) {")],
+    # block weights (Algorithm 1 localBlockSizes)
+    "block_weights_unweighted": [("S[A[p]] += wp;", "S[A[p]] += 1.0;")],
+    # initial centers (Algorithm 2)
+    "centers_without_offset": [("int64_t idx = i * n / k + n / (2 * (int64_t)k);",
+                                "int64_t idx = i * n / k;")],
+    # movement and beta (Algorithm 2, Eq. 2-3)
+    "mean_by_count": [("C_new[c * d + j] = sx[c * d + j] / sw[c];",
+                       "C_new[c * d + j] = sx[c * d + j] / (double)cnt[c];")],
+    "beta_over_all_blocks": [("*beta = nonempty > 0 ? diam_sum / (double)nonempty : 0.0;",
+                              "*beta = diam_sum / (double)k;")],
+    "beta_squared_diagonal": [("diam_sum += sqrt(diag);", "diam_sum += diag;")],
+    "delta_squared": [("delta[c] = sqrt(dd);", "delta[c] = dd;")],
+    # erosion (Eq. 2-3)
+    "erosion_sign": [("double t = -delta[c] / beta;", "double t = delta[c] / beta;")],
+    "erosion_alpha_form": [("alpha = 2.0 / (1.0 + exp(t)) - 1.0;", "alpha = 1.0 / (1.0 + exp(t));")],
+    "erosion_exponent": [("I[c] = exp((1.0 - alpha) * log(I[c]));", "I[c] = exp(alpha * log(I[c]));")],
+    # the loop's composition (Algorithms 1-2 as read)
+    "erode_the_used_influence": [(
+        "        if (opt->erosion) or_erosion(delta, beta, k, I);\n    }\n    if (!balanced) {",
+        "        if (opt->erosion) {\n"
+        "            memcpy(I, I_used, (size_t)k * sizeof(double));\n"
+        "            or_erosion(delta, beta, k, I);\n"
+        "        }\n    }\n    if (!balanced) {")],
+    "erode_before_convergence_test": [
+        ("        if (max_delta < thr) {\n            res->converged = 1;",
+         "        if (opt->erosion) or_erosion(delta, beta, k, I);\n"
+         "        if (max_delta < thr) {\n            res->converged = 1;"),
+        ("        if (opt->erosion) or_erosion(delta, beta, k, I);\n    }\n    if (!balanced) {",
+         "    }\n    if (!balanced) {")],
+    "move_in_last_phase": [("        if (it == opt->max_iter - 1) break;\n", "")],
+    "used_influence_after_update": [(
+        "            for (int c = 0; c < k; ++c) I_used[c] = I[c];\n"
+        "            balanced = or_balance_update(S, W, k, d, eps, I, &imbalance);\n"
+        "            if (balanced) break;\n        }\n        /* Algorithm 2",
+        "            balanced = or_balance_update(S, W, k, d, eps, I, &imbalance);\n"
+        "            for (int c = 0; c < k; ++c) I_used[c] = I[c];\n"
+        "            if (balanced) break;\n        }\n        /* Algorithm 2")],
+    "no_final_passes": [("    if (!balanced) {\n        for (int fp", "    if (0) {\n        for (int fp")],
+    # Hilbert curve (Section 4.1) and its grid
+    "hilbert_no_mirror": [("flip[0] ^= 1; /* mirror slot 0 */", "/* no mirror */")],
+    "hilbert_no_parity": [("digit = (digit << 1) | (uint64_t)(prefix ^ parity_above);",
+                           "digit = (digit << 1) | (uint64_t)prefix;")],
+    "hilbert_no_exchange": [("                perm[0] = perm[i];\n                perm[i] = tp;\n",
+                             "                (void)tp;\n")],
+    "grid_not_tight": [("return (f == 0.5) ? e - 1 : e;", "return e;")],
+    "quantise_rounds": [("return (uint32_t)floor(scaled);", "return (uint32_t)floor(scaled + 0.5);")],
+    "f32_subtract_in_f64": [("float v = x[p * d + j] - lo[j]; /* one FP32 subtraction */",
+                             "double v = (double)x[p * d + j] - (double)lo[j];")],
+    # sort (Algorithm 2 sortGlobal)
+    "sort_unstable": [("if (keys[a[j]] < keys[a[i]])", "if (keys[a[j]] <= keys[a[i]])")],
+    # random initialization (Section 4.5)
+    "sample_rounds_one_more": [("while (r < 62 && (m0 << r) < n) ++r;",
+                                "while (r < 62 && (m0 << r) <= n) ++r;")],
+    "sample_first_not_100k": [("int64_t m0 = sample0 > 0 ? sample0 : 100 * (int64_t)k;",
+                               "int64_t m0 = sample0 > 0 ? sample0 : 10 * (int64_t)k;")],
+    "sample_round_without_erosion": [(
+        "        if (opt->erosion) or_erosion(delta, beta, k, I);\n    }\n    or_options rest",
+        "    }\n    or_options rest")],
+    "sampled_iterations_not_shared": [("rest.max_iter = opt->max_iter - R;",
+                                       "rest.max_iter = opt->max_iter;")],
+}
+
+
+def _mutant_source(name):
+    text = open(SRC).read()
+    for old, new in MUTANTS[name]:
+        assert text.count(old) == 1, f"{name}: the text to replace occurs {text.count(old)} times"
+        text = text.replace(old, new)
+    return text
+
+
+def test_every_mutant_applies_to_the_current_oracle():
+    for name in MUTANTS:
+        assert _mutant_source(name) != open(SRC).read()
+
+
+_RUNNER = """
+import sys
+import oracle
+oracle._SRC = sys.argv[1]
+oracle._LIB_PATH = sys.argv[2]
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"] + sys.argv[3:]))
+"""
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_planted_mistake(name, tmp_path):
+    src = tmp_path / "gk_oracle.c"
+    src.write_text(_mutant_source(name))
+    shutil.copy(HDR, tmp_path / "gk_oracle.h")
+    lib = tmp_path / "liboracle.so"
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", _RUNNER, str(src), str(lib), *PINS], cwd=ROOT,
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert lib.exists(), r.stdout[-2000:] + r.stderr[-2000:]
+    # exit status 1: tests ran and at least one failed (not a crash, not a collection error)
+    assert r.returncode == 1, f"{name} was not caught:\n{r.stdout[-1500:]}"
