@@ -5,9 +5,10 @@ sign, a dropped term, a wrong index, a step out of order: the kinds of error a
 restatement of Algorithms 1-2 and Eq. 1-3 could contain), builds that copy into a
 library of its own in a temporary directory, and runs the oracle's pin tests
 (``tests/test_oracle.py``, ``tests/test_oracle_trajectory.py``) against it in a
-separate process.  The pins must fail for every planted mistake.  The committed
-oracle is never modified: the copy is loaded in place of it only inside that
-process.
+separate process.  The quality measures of Section 5 (``oracle/quality.py``) get the
+same treatment against the CPU tests of ``tests/test_quality.py``.  The pins must fail
+for every planted mistake.  The committed oracle is never modified: the copy is loaded
+in place of it only inside that process.
 """
 import os
 import shutil
@@ -103,6 +104,39 @@ MUTANTS = {
 }
 
 
+QSRC = os.path.join(ROOT, "oracle", "quality.py")
+QPINS = ["tests/test_quality.py"]
+
+# mistakes in the quality measures (Section 5) and the diameter sweeps as read.  Left out
+# as equivalent (no input tells them apart): counting self-loops (never foreign, never a
+# new vertex), the bound from the last sweep only (every sweep starts at a vertex the one
+# before reached last, so eccentricities do not decrease), and dropping the empty-block
+# case (an empty block is "connected" with bound 0 anyway).
+QMUTANTS = {
+    "edge_cut_not_halved": [('"edge_cut": int(ext.sum() // 2)', '"edge_cut": int(ext.sum())')],
+    "comm_counts_edges": [("pairs = np.unique(np.stack([v[foreign], bu[foreign]], axis=1), axis=0)",
+                           "pairs = np.stack([v[foreign], bu[foreign]], axis=1)")],
+    "comm_credited_to_other_block": [("comm = np.bincount(block[pairs[:, 0]], minlength=k)",
+                                      "comm = np.bincount(pairs[:, 1], minlength=k)")],
+    "comm_includes_own_block": [("pairs = np.unique(np.stack([v[foreign], bu[foreign]], axis=1), axis=0)",
+                                 "pairs = np.unique(np.stack([v, bu], axis=1), axis=0)")],
+    "bfs_leaves_the_block": [("fresh = (block[u] == block[tail]) & (dist[u] < 0)",
+                              "fresh = dist[u] < 0")],
+    "first_start_largest_index": [(
+        "    start = np.full(k, n, dtype=np.int64)\n    np.minimum.at(start, block, ids)",
+        "    start = np.full(k, -1, dtype=np.int64)\n    np.maximum.at(start, block, ids)")],
+    "next_start_largest_index": [(
+        "        start = np.full(k, n, dtype=np.int64)\n        np.minimum.at(start, block[last], last)",
+        "        start = np.full(k, -1, dtype=np.int64)\n        np.maximum.at(start, block[last], last)")],
+    "next_start_not_farthest": [("last = np.nonzero(dist == ecc[block])[0]",
+                                 "last = np.nonzero(dist == 0)[0]")],
+    "harmonic_without_disconnected": [("m = int(big.sum())", "m = int(pos.sum())")],
+    "harmonic_over_single_vertices": [("big = size >= 2", "big = size >= 1")],
+    "arithmetic_mean": [("hm = 0.0 if m == 0 else (np.inf if s == 0.0 else m / s)",
+                         "hm = 0.0 if m == 0 else float(diam[pos].sum()) / m")],
+}
+
+
 def _mutant_source(name):
     text = open(SRC).read()
     for old, new in MUTANTS[name]:
@@ -111,9 +145,19 @@ def _mutant_source(name):
     return text
 
 
+def _qmutant_source(name):
+    text = open(QSRC).read()
+    for old, new in QMUTANTS[name]:
+        assert text.count(old) == 1, f"{name}: the text to replace occurs {text.count(old)} times"
+        text = text.replace(old, new)
+    return text
+
+
 def test_every_mutant_applies_to_the_current_oracle():
     for name in MUTANTS:
         assert _mutant_source(name) != open(SRC).read()
+    for name in QMUTANTS:
+        assert _qmutant_source(name) != open(QSRC).read()
 
 
 _RUNNER = """
@@ -138,3 +182,26 @@ def test_pins_reject_planted_mistake(name, tmp_path):
     assert lib.exists(), r.stdout[-2000:] + r.stderr[-2000:]
     # exit status 1: tests ran and at least one failed (not a crash, not a collection error)
     assert r.returncode == 1, f"{name} was not caught:\n{r.stdout[-1500:]}"
+
+
+_QRUNNER = """
+import importlib.util
+import sys
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.quality", sys.argv[1])
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+sys.modules["oracle.quality"] = mod
+oracle.quality = mod
+import pytest
+sys.exit(pytest.main(["-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"] + sys.argv[2:]))
+"""
+
+
+@pytest.mark.parametrize("name", sorted(QMUTANTS))
+def test_quality_pins_reject_planted_mistake(name, tmp_path):
+    src = tmp_path / "quality.py"
+    src.write_text(_qmutant_source(name))
+    r = subprocess.run([sys.executable, "-c", _QRUNNER, str(src), *QPINS], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"{name} was not caught:\n{r.stdout[-1500:]}{r.stderr[-800:]}"

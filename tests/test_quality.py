@@ -120,6 +120,22 @@ def test_diameter_hand_graphs():
     assert oq.diameter_summary([0, 0], [1, 0])["harmonic_mean"] == 0.0
 
 
+def test_diameter_sweep_starts_follow_the_reading():
+    """The first sweep starts at the block's smallest vertex index, a later one at the
+    smallest index among the vertices the previous sweep reached last."""
+    # path 1-0-2-3-4: from vertex 0 the eccentricity is 3 (from vertex 4 it would be 4)
+    rp, col = _csr(5, [(1, 0), (0, 2), (2, 3), (3, 4)])
+    assert oq.block_diameter_sweeps(rp, col, np.zeros(5, dtype=np.int64), 1, 1).tolist() == [3]
+    # edges 0-1, 0-3, 1-2, 1-4, 2-3: the sweep from 0 reaches {2, 4} last (distance 2); the
+    # sweep from 2 has eccentricity 2 and reaches {0, 4} last, the one from 0 again 2.  (From
+    # 4 the second sweep would find 3, the exact diameter, via 4-1-0-3.)
+    rp, col = _csr(5, [(0, 1), (0, 3), (1, 2), (1, 4), (2, 3)])
+    block = np.zeros(5, dtype=np.int64)
+    for sweeps in (2, 3):
+        assert oq.block_diameter_sweeps(rp, col, block, 1, sweeps).tolist() == [2]
+    assert oq.block_diameter_exact(rp, col, block, 1).tolist() == [3]
+
+
 def test_diameter_sweeps_exact_on_trees():
     """On a tree a sweep from any vertex ends at an end of a longest path, so the second
     sweep already gives the exact diameter."""
