@@ -164,6 +164,8 @@ int32_t gk_abi_version(void);
  *   waited_us (nullable, host memory): the device time the wait took, in microseconds.
  * Returns GK_ERR_TIMEOUT when the wait gave up (the expected result), GK_OK if it
  * completed, GK_ERR_CUDA on a CUDA error.  Waits for its stream before it returns.
+ * Calls whose GPU work overlaps (other streams, other host threads) share one status
+ * word in device memory and race on it.
  */
 gk_status gk_check_wait_timeout(int64_t limit_us, int64_t *waited_us, void *stream);
 
