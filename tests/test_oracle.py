@@ -451,6 +451,22 @@ def test_balanced_kmeans_outputs_are_consistent():
     assert out["result"]["balanced"] == 1
 
 
+def test_default_movement_threshold_is_a_ten_thousandth_of_the_extent():
+    """Reading of the defaults: deltaThreshold = 1e-4 x the largest extent of the points'
+    bounding box unless the caller gives one; the loop stops when every center moved less."""
+    rng = np.random.default_rng(31)
+    x = rng.random((4000, 2)) * np.array([8.0, 2.0]) + np.array([-3.0, 5.0])
+    x[0], x[1] = [-3.0, 5.0], [5.0, 7.0]  # the box is [-3, 5] x [5, 7]: extent 8
+    r = oracle.partition(x, None, 6, 0.03, oracle.default_options(max_iter=3))["result"]
+    assert r["delta_threshold"] == 1e-4 * 8.0
+    r = oracle.partition(x, None, 6, 0.03, oracle.default_options(max_iter=3,
+                                                                  delta_threshold=0.25))["result"]
+    assert r["delta_threshold"] == 0.25
+    # a threshold above every movement stops after the first iteration, converged
+    r = oracle.partition(x, None, 6, 0.03, oracle.default_options(delta_threshold=100.0))["result"]
+    assert r["iterations"] == 1 and r["converged"] == 1
+
+
 def test_invalid_arguments_rejected():
     x = np.zeros((3, 2))
     assert oracle.partition(x, None, 4, 0.03)["result"]["status"] == oracle.OR_INVALID

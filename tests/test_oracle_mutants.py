@@ -22,7 +22,9 @@ SRC = os.path.join(ROOT, "oracle", "gk_oracle.c")
 HDR = os.path.join(ROOT, "oracle", "gk_oracle.h")
 PINS = ["tests/test_oracle.py", "tests/test_oracle_trajectory.py"]
 
-# name -> [(text in gk_oracle.c, its replacement), ...]; every text occurs exactly once
+# name -> [(text in gk_oracle.c, its replacement), ...]; every text occurs exactly once.
+# Left out as equivalent: running the movement loop to it <= maxIter (the body already
+# leaves at the last iteration, so only maxIter = 0 would tell).
 MUTANTS = {
     # Eq. 1 and the balance test (Section 2, Section 4.2, Algorithm 1)
     "eq1_gamma_inverted": [("double gamma = target / S[c];", "double gamma = S[c] / target;")],
@@ -91,7 +93,29 @@ MUTANTS = {
                              "double v = (double)x[p * d + j] - (double)lo[j];")],
     # sort (Algorithm 2 sortGlobal)
     "sort_unstable": [("if (keys[a[j]] < keys[a[i]])", "if (keys[a[j]] <= keys[a[i]])")],
+    # the bootstrap's data movement and the loop bounds (Algorithm 2)
+    "scatter_inverted": [(
+        "    int st = or_balanced_kmeans(xs, ws, n, d, k, eps, opt, C_out, I, I_out, NULL, As, res);\n"
+        "    for (int64_t i = 0; i < n; ++i) A_out[perm[i]] = As[i];",
+        "    int st = or_balanced_kmeans(xs, ws, n, d, k, eps, opt, C_out, I, I_out, NULL, As, res);\n"
+        "    for (int64_t i = 0; i < n; ++i) A_out[i] = As[perm[i]];")],
+    "weights_not_permuted": [("        if (ws) ws[i] = w[perm[i]];\n    }\n    double *I",
+                              "        if (ws) ws[i] = w[i];\n    }\n    double *I")],
+    "centers_from_unsorted_points": [(
+        "    or_sfc_centers(xs, n, d, k, C_out);\n    for (int c = 0; c < k; ++c) I[c] = 1.0;\n    int st",
+        "    or_sfc_centers(xd, n, d, k, C_out);\n    for (int c = 0; c < k; ++c) I[c] = 1.0;\n    int st")],
+    "influence_starts_at_two": [(
+        "    or_sfc_centers(xs, n, d, k, C_out);\n    for (int c = 0; c < k; ++c) I[c] = 1.0;\n    int st",
+        "    or_sfc_centers(xs, n, d, k, C_out);\n    for (int c = 0; c < k; ++c) I[c] = 2.0;\n    int st")],
+    "hilbert_bits_3d": [("return d == 2 ? 32 : 21;", "return d == 2 ? 32 : 20;")],
+    "delta_threshold_scale": [("opt->delta_threshold : 1e-4 * extent;", "opt->delta_threshold : 1e-3 * extent;")],
+    "one_balance_pass_more": [(
+        "        for (int bp = 0; bp < opt->max_balance_iter; ++bp) {\n"
+        "            or_assign(x, n, d, C, I, k, A, NULL, NULL, opt->threads);",
+        "        for (int bp = 0; bp <= opt->max_balance_iter; ++bp) {\n"
+        "            or_assign(x, n, d, C, I, k, A, NULL, NULL, opt->threads);")],
     # random initialization (Section 4.5)
+    "sample_by_input_index": [("mark[rank[order[i]]] = 1;", "mark[order[i]] = 1;")],
     "sample_rounds_one_more": [("while (r < 62 && (m0 << r) < n) ++r;",
                                 "while (r < 62 && (m0 << r) <= n) ++r;")],
     "sample_first_not_100k": [("int64_t m0 = sample0 > 0 ? sample0 : 100 * (int64_t)k;",
