@@ -139,6 +139,10 @@ def test_quantisation_closed_forms():
     x = np.array([[3.0, 0.0], [4.0, 0.5], [5.0, 0.25]])
     _, q = oracle.hilbert_keys(x, return_cells=True)
     assert q.tolist() == [[0, 0], [1 << 31, 1 << 30], [(1 << 32) - 1, 1 << 29]]
+    # the largest extent on the second axis: box [0, 0.5] x [3, 5], extent 2 -> side 2^1
+    x = np.array([[0.0, 3.0], [0.25, 4.0], [0.5, 5.0]])
+    _, q = oracle.hilbert_keys(x, return_cells=True)
+    assert q.tolist() == [[0, 0], [1 << 29, 1 << 31], [1 << 30, (1 << 32) - 1]]
     # 3D, extent 3 -> side 4 = 2^2, b = 21 -> cell = floor((x - lo) * 2^19)
     x = np.array([[0.0, 0.0, 0.0], [3.0, 1.0, 2.0]])
     _, q = oracle.hilbert_keys(x, return_cells=True)
@@ -166,6 +170,12 @@ def test_quantisation_fp32_subtracts_in_fp32():
     x = np.array([[2.0 ** -30, 0.0], [1.0 + 2.0 ** -23, 1.0]], dtype=np.float32)
     _, q = oracle.hilbert_keys(x, return_cells=True)
     assert q.tolist() == [[0, 0], [(1 << 31) + (1 << 8), 1 << 31]]
+    # the extent itself is the FP64 difference of the FP32 bounds: lo = -2^-30, hi = 1 give
+    # 1 + 2^-30 > 1 -> side 2 (an FP32 difference would round it to 1 -> side 1); the point
+    # at hi then has v = fl32(1 + 2^-30) = 1 and cell 2^31
+    x = np.array([[-(2.0 ** -30), 0.0], [1.0, 0.5]], dtype=np.float32)
+    _, q = oracle.hilbert_keys(x, return_cells=True)
+    assert q.tolist() == [[0, 0], [1 << 31, 1 << 30]]
 
 
 def test_keys_of_points_follow_cells():

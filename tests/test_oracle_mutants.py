@@ -91,6 +91,20 @@ MUTANTS = {
     "quantise_rounds": [("return (uint32_t)floor(scaled);", "return (uint32_t)floor(scaled + 0.5);")],
     "f32_subtract_in_f64": [("float v = x[p * d + j] - lo[j]; /* one FP32 subtraction */",
                              "double v = (double)x[p * d + j] - (double)lo[j];")],
+    "extent_of_the_first_axis": [(
+        "    for (int j = 0; j < d; ++j)\n        if (hi[j] - lo[j] > s) s = hi[j] - lo[j];\n"
+        "    int b = hilbert_bits(d);",
+        "    for (int j = 0; j < 1; ++j)\n        if (hi[j] - lo[j] > s) s = hi[j] - lo[j];\n"
+        "    int b = hilbert_bits(d);")],
+    "top_cell_not_clamped": [("if (scaled >= top) return (uint32_t)(top - 1.0);",
+                              "if (scaled > top) return (uint32_t)(top - 1.0);")],
+    "box_starts_at_zero": [(
+        "        lo[j] = INFINITY;\n        hi[j] = -INFINITY;\n    }\n"
+        "    for (int64_t p = 0; p < n; ++p) {\n        for (int j = 0; j < d; ++j) {\n            double v",
+        "        lo[j] = 0.0;\n        hi[j] = 0.0;\n    }\n"
+        "    for (int64_t p = 0; p < n; ++p) {\n        for (int j = 0; j < d; ++j) {\n            double v")],
+    "f32_extent_rounded": [("        double e = (double)hi[j] - (double)lo[j];",
+                            "        double e = (double)(hi[j] - lo[j]);")],
     # sort (Algorithm 2 sortGlobal)
     "sort_unstable": [("if (keys[a[j]] < keys[a[i]])", "if (keys[a[j]] <= keys[a[i]])")],
     # the bootstrap's data movement and the loop bounds (Algorithm 2)
@@ -120,6 +134,7 @@ MUTANTS = {
                                 "while (r < 62 && (m0 << r) <= n) ++r;")],
     "sample_first_not_100k": [("int64_t m0 = sample0 > 0 ? sample0 : 100 * (int64_t)k;",
                                "int64_t m0 = sample0 > 0 ? sample0 : 10 * (int64_t)k;")],
+    "sample_unweighted": [("            if (wr) wr[j] = ws[pos];", "            if (wr) wr[j] = 1.0;")],
     "sample_round_without_erosion": [(
         "        if (opt->erosion) or_erosion(delta, beta, k, I);\n    }\n    or_options rest",
         "    }\n    or_options rest")],
